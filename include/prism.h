@@ -1,0 +1,227 @@
+/* prism.h — C ABI of the GB300 (sm_103a) PRISM filter hot path.
+ *
+ * PRISM (arXiv 2212.02988) filters a dense Gaussian voxel map and a 12-D
+ * agent state from RGB-D frames and IMU readings.  One filter step for
+ * frame t is (Sec. 3.3, App. F):
+ *     prism_predict      state propagation from the IMU window   (App. E.1/E.2)
+ *     prism_localise     MAP pose + Laplace covariance + velocity (App. E.3, Sec. 4.1, Sec. 3.3.2)
+ *     prism_update_map   per-voxel Gaussian map update           (App. D, Eq. mapupdategauss)
+ *     prism_render       render of the map mean = next anchor    (App. B)
+ * (frame 1 only fuses and renders: the first state is given, Eq. 1).
+ * prism_step runs the four in order as one stream of kernels.
+ *
+ * Conventions
+ *   - World frame z up; camera frame +x right, +y down, +z forward.
+ *   - A pose is 7 doubles (t_x, t_y, t_z, q_w, q_x, q_y, q_z): X_w = R(q) X_c + t.
+ *     q need not be normalised; it is normalised before use.
+ *   - Images are row-major, pixel (u, v) at index v * width + u; depth is
+ *     camera z-depth in metres (<= 0 or non-finite = no return); colour is
+ *     3 interleaved floats per pixel.
+ *   - Map arrays exchanged with the caller are linear, z-major, x fastest:
+ *     voxel (i, j, k) at index (k * ny + j) * nx + i; colour 3 interleaved
+ *     floats per voxel.  Voxel (i, j, k) covers [o + i vs, o + (i + 1) vs).
+ *   - "Device pointer" = memory of the handle's CUDA device (e.g. a torch
+ *     tensor's data_ptr()); "host pointer" = ordinary CPU memory.
+ *
+ * Ownership and concurrency
+ *   The library owns the map, the state, the anchor and its scratch buffers
+ *   (allocated in prism_create_map, freed in prism_destroy).  It never frees
+ *   caller memory and keeps no caller pointer after a call returns.  Every
+ *   call enqueues work on the handle's CUDA stream and returns without
+ *   waiting, unless it writes a host output (documented per call), in which
+ *   case it synchronises the stream first.  Device buffers passed in must
+ *   stay valid until the stream has passed the call.  A handle must not be
+ *   used from two host threads at once; distinct handles are independent.
+ *
+ * Errors
+ *   Every call returns a prism_status.  On a negative status the handle's
+ *   state is unchanged where the error is detected on the host, and
+ *   prism_last_error(h) describes it.  Failures found on the device (a
+ *   normal-equation matrix that is not positive definite) leave the state
+ *   unchanged and are reported by the next call that synchronises.  No call
+ *   traps, asserts or aborts on the device.
+ */
+#ifndef PRISM_H
+#define PRISM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PRISM_ABI_VERSION 1
+
+typedef struct prism_ctx* prism_handle;
+
+typedef enum {
+    PRISM_OK = 0,
+    PRISM_EINVAL = -1,    /* bad argument: NULL, size, shape, alignment */
+    PRISM_ENOMEM = -2,    /* device or host allocation failed */
+    PRISM_ECUDA = -3,     /* a CUDA runtime call failed */
+    PRISM_ENOTPD = -4,    /* a normal-equation / covariance matrix was not positive definite */
+    PRISM_ESTATE = -5     /* call out of order (e.g. localise before any anchor) */
+} prism_status;
+
+enum { PRISM_STORAGE_F32 = 0, PRISM_STORAGE_BF16 = 1 };
+
+/* Filter configuration.  prism_config_default() fills the paper's values
+ * (App. F.2, Tbl. transscales) for a cubic grid and an image size. */
+typedef struct {
+    int32_t nx, ny, nz;          /* voxels per axis, each a positive multiple of 8 */
+    int32_t storage;             /* PRISM_STORAGE_F32 or PRISM_STORAGE_BF16 (map means and variances) */
+    int32_t width, height;       /* frame size, pixels (>= 3 each) */
+    int32_t n_gn;                /* Gauss-Newton iterations per frame (>= 1) */
+    int32_t reserved;
+    double voxel;                /* voxel edge length vs, metres */
+    double origin[3];            /* world position of the grid's minimum corner */
+    double fx, fy, cx, cy;       /* pinhole intrinsics, pixel centres at integers */
+    double eps;                  /* ray step (App. F.2: 0.4 vs) */
+    double tau;                  /* hit threshold on occupancy (App. F.2: 0) */
+    double max_depth;            /* longest ray distance, metres; <= 0: the grid bounds the ray */
+    double trunc;                /* truncation distance (App. F.2: 2 vs) */
+    double prior_var;            /* prior variance of every channel (App. B: sigma >> 1; 1e4) */
+    double init_occ;             /* initial occupancy mean (App. F.2: -0.001) */
+    double init_rgb;             /* initial colour mean (App. F.2: 0) */
+    double update_var;           /* sigma_update^2 (App. F.2: 1) */
+    double sigma_vel[2];         /* velocity transition scales, translation / rotation (0.03, 0.03) */
+    double sigma_pose[2];        /* pose transition scales, translation / rotation (0.05, 0.02) */
+    double b_geo, b_rgb;         /* Laplace scales of the objective (0.02 m, 0.1) */
+    double gate_geo, gate_rgb;   /* residual gates (0.45, 0.15) */
+    double floor_geo, floor_rgb; /* IRLS floor on |r| (1e-3 m, 1e-2) */
+    double ema;                  /* Laplace covariance EMA coefficient (0.8) */
+    double disc;                 /* depth discontinuity threshold, metres (0.1) */
+    double gravity;              /* m/s^2 along world -z (9.81) */
+} prism_config;
+
+/* Filter state (host copy).  cov is 12x12 row-major over the error state
+ * (dt, dtheta, dv, dw), the rotation error applied on the left:
+ * R = Exp(dtheta) R_mean; velocities (v linear, w angular) in the world frame. */
+typedef struct {
+    double t[3], q[4], v[3], w[3];
+    double cov[144];
+    int32_t n_localised;         /* frames localised so far (the EMA starts at the first) */
+    int32_t reserved;
+} prism_state;
+
+/* Cumulative counters of the work done by a handle's kernels. */
+typedef struct {
+    int64_t render_rays;         /* rays rendered */
+    int64_t render_samples;      /* ray samples evaluated (8 occupancy corners each) */
+    int64_t render_hits;         /* rays with a valid hit (colour read at 2 x 8 corners) */
+    int64_t fuse_updates;        /* voxels whose occupancy was updated */
+    int64_t fuse_colour_updates; /* voxels whose colour was updated */
+    int64_t track_pixels;        /* pixel evaluations of the localisation objective */
+} prism_stats;
+
+/* Per-phase device time (CUDA events on the handle's stream), in ms,
+ * accumulated since the last prism_timing_reset; enabled by prism_set_timing. */
+typedef struct {
+    double predict_ms, localise_ms, fuse_ms, render_ms, anchor_ms;
+    int64_t predict_n, localise_n, fuse_n, render_n, anchor_n;
+} prism_timing;
+
+/* Paper defaults for an n^3 grid of edge `extent` metres centred on the
+ * origin and a width x height camera with fx = fy = 70 width / 80. */
+void prism_config_default(prism_config* cfg, int32_t n, double extent, int32_t width, int32_t height);
+
+/* Create a filter on the current CUDA device.  Allocates the map (prior
+ * values: occupancy init_occ, colour init_rgb, variances prior_var), the
+ * state (s1, copied; NULL = identity pose, zero velocity, 1e-8 I covariance)
+ * and the scratch buffers.  `stream` is a cudaStream_t (NULL = legacy
+ * default stream) on which every later call of this handle enqueues work.
+ * Returns PRISM_EINVAL for a bad configuration, PRISM_ENOMEM if the device
+ * allocation fails (nothing is leaked).  App. B (prior), Eq. 1 (s_1 given). */
+prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, void* stream,
+                              prism_handle* out);
+
+/* Synchronise the stream and free everything the handle owns. */
+prism_status prism_destroy(prism_handle h);
+
+/* Propagate the state over one frame interval dt > 0 with the IMU samples
+ * of that interval (App. E.1 transition, Eq. statepropagation, App. E.2
+ * split into pose prior and velocity conditional).  imu: HOST pointer to n
+ * rows of 7 doubles (t, acc_x, acc_y, acc_z, gyro_x, gyro_y, gyro_z), specific
+ * force in m/s^2 and angular rate in rad/s in the camera frame; n = 0 means
+ * no controls (constant velocity).  The rows are copied before returning. */
+prism_status prism_predict(prism_handle h, const double* imu, int32_t n, double dt);
+
+/* Localise frame t against the current anchor (App. E.3 objective with the
+ * gates and scales of App. F.2, Gauss-Newton with IRLS weights, FP64 6x6
+ * Cholesky; Sec. 4.1 Laplace covariance with the App. F.2 EMA; Sec. 3.3.2
+ * recombination with the velocity conditional).  Needs a prior from
+ * prism_predict since the last localisation and an anchor (PRISM_ESTATE).
+ * depth: DEVICE pointer, H x W floats; rgb: DEVICE pointer, H x W x 3 floats.
+ * out: HOST pointer or NULL; when given, the stream is synchronised and the
+ * new state written (this also reports PRISM_ENOTPD found on the device). */
+prism_status prism_localise(prism_handle h, const float* depth, const float* rgb, prism_state* out);
+
+/* Fuse a frame into the map at the current state mean (App. D, Eq.
+ * mapupdategauss; frustum and truncation rule of App. F.2).  depth, rgb:
+ * DEVICE pointers as for prism_localise. */
+prism_status prism_update_map(prism_handle h, const float* depth, const float* rgb);
+
+/* Render the map mean at a pose (App. B: ray points d = k eps, trilinear
+ * field, first occupancy above tau, alpha-interpolated depth and colour).
+ * pose7: HOST pointer to a pose, or NULL for the current state mean — in
+ * which case the result also becomes the anchor of the next localisation.
+ * depth (H x W floats, z-depth, 0 = no hit), rgb (H x W x 3 floats),
+ * mask (H x W bytes, 1 = hit), hitk (H x W int32: index k >= 2 of the hit
+ * sample, 0 = none, -1 = hit at the first sample): DEVICE pointers, each
+ * may be NULL (not written). */
+prism_status prism_render(prism_handle h, const double* pose7, float* depth, float* rgb,
+                          uint8_t* mask, int32_t* hitk);
+
+/* One full filter step (R21): predict (skipped on the first step), localise
+ * (skipped on the first step), update_map, render of the new anchor.
+ * Arguments as for the individual calls; out may be NULL. */
+prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
+                        const float* depth, const float* rgb, prism_state* out);
+
+/* Copy the state to HOST memory (synchronises the stream; reports a pending
+ * device-side PRISM_ENOTPD). */
+prism_status prism_get_state(prism_handle h, prism_state* out);
+
+/* Replace the state (HOST pointer); the pending prior is discarded. */
+prism_status prism_set_state(prism_handle h, const prism_state* s);
+
+/* Load / store the whole map in the linear caller layout (see Conventions):
+ * occ (N floats), rgb (3N floats), var_occ (N floats), var_rgb (N floats),
+ * N = nx*ny*nz; DEVICE pointers; for storage BF16 the values are rounded
+ * to nearest-even on load.  prism_map_store may be given NULL for any array. */
+prism_status prism_map_load(prism_handle h, const float* occ, const float* rgb,
+                            const float* var_occ, const float* var_rgb);
+prism_status prism_map_store(prism_handle h, float* occ, float* rgb, float* var_occ, float* var_rgb);
+
+/* Make an externally rendered observation the anchor (as prism_render with
+ * pose7 = NULL does for its own output): pose7 HOST pointer, depth and rgb
+ * DEVICE pointers in the image layout.  The anchor's validity mask (App.
+ * F.3) and normals (App. E.3) are computed from depth. */
+prism_status prism_anchor_load(prism_handle h, const double* pose7, const float* depth,
+                               const float* rgb);
+
+/* One evaluation of the localisation objective at a camera pose against the
+ * current anchor (App. E.3), reduced on the device: out (HOST, 80 doubles)
+ * = H (36, row-major, sum w J^T J), g (6, sum w J^T r), Ht (36, sum J^T J / b^2),
+ * cost (sum |r| / b), kept pixel count; J is the derivative with respect to
+ * a world-frame perturbation t' = t + dt, R' = Exp(dtheta) R.  Synchronises. */
+prism_status prism_normal_equations(prism_handle h, const double* pose7, const float* depth,
+                                    const float* rgb, double* out);
+
+/* Work counters and per-phase timing. */
+prism_status prism_get_stats(prism_handle h, prism_stats* out);
+prism_status prism_set_timing(prism_handle h, int32_t enabled);
+prism_status prism_get_timing(prism_handle h, prism_timing* out);   /* synchronises */
+prism_status prism_timing_reset(prism_handle h);
+
+/* Bytes of device memory the handle owns. */
+int64_t prism_device_bytes(prism_handle h);
+
+/* Human-readable description of the last error on h (never NULL), and of a status. */
+const char* prism_last_error(prism_handle h);
+const char* prism_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRISM_H */

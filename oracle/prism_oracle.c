@@ -147,12 +147,20 @@ static void mat3_inverse(const double A[9], double B[9]) {
 }
 
 /* ------------------------------------------------------------------ rotations */
-/* Rotation matrix of a quaternion (w, x, y, z), normalised first.  This is
- * also the FP64 recipe from which the FP32 decision matrices are rounded,
- * so its operation order is fixed: n = sqrt(((w*w + x*x) + y*y) + z*z). */
+/* A pose with its quaternion normalised: q / sqrt(((w*w + x*x) + y*y) + z*z).
+ * Every entry point normalises the poses it is given, once, with exactly
+ * these operations (the device library does the same at its boundary). */
+static void normalise_pose(const double in[7], double out[7]) {
+    double n = sqrt(((in[3] * in[3] + in[4] * in[4]) + in[5] * in[5]) + in[6] * in[6]);
+    for (int a = 0; a < 3; ++a) out[a] = in[a];
+    for (int a = 0; a < 4; ++a) out[3 + a] = in[3 + a] / n;
+}
+
+/* Rotation matrix of a unit quaternion (w, x, y, z).  This is also the FP64
+ * recipe from which the FP32 decision matrices are rounded, so its operation
+ * order is fixed: products first, then the sums of the standard formula. */
 static void quat_to_R(const double qin[4], double R[9]) {
-    double n = sqrt(((qin[0] * qin[0] + qin[1] * qin[1]) + qin[2] * qin[2]) + qin[3] * qin[3]);
-    double w = qin[0] / n, x = qin[1] / n, y = qin[2] / n, z = qin[3] / n;
+    double w = qin[0], x = qin[1], y = qin[2], z = qin[3];
     double xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
     double wx = w * x, wy = w * y, wz = w * z;
     R[0] = 1.0 - 2.0 * (yy + zz); R[1] = 2.0 * (xy - wz);       R[2] = 2.0 * (xz + wy);
@@ -283,10 +291,11 @@ static double trilinear64(const or_params* P, const double* m, int stride, int c
     return s;
 }
 
-int or_render(const or_params* P, const double* occ, const double* rgb, const double pose[7],
+int or_render(const or_params* P, const double* occ, const double* rgb, const double pose_in[7],
               const int32_t* pix, int32_t npix, double* depth, double* rgb_out, uint8_t* mask,
               int32_t* hitk, int64_t* n_samples) {
-    double R[9];
+    double R[9], pose[7];
+    normalise_pose(pose_in, pose);
     quat_to_R(pose + 3, R);
     /* FP32 ray set-up (decision recipe) */
     float R32[9], c32[3], o32[3];
@@ -438,9 +447,12 @@ void or_anchor_normals(const or_params* P, const float* depth, const uint8_t* ma
  * xi = (dt, dtheta).  kept[p] = 1 iff the pixel passed every validity check
  * and both gates (App. F.2); assoc[2p] = nearest anchor pixel, assoc[2p+1] =
  * the bilinear cell's top-left pixel (-1 when not associated). */
-int or_residuals(const or_params* P, const double anchor_pose[7], const float* a_depth,
-                 const float* a_rgb, const double pose[7], const float* o_depth, const float* o_rgb,
+int or_residuals(const or_params* P, const double anchor_in[7], const float* a_depth,
+                 const float* a_rgb, const double pose_in[7], const float* o_depth, const float* o_rgb,
                  double* r, double* J, int32_t* assoc, uint8_t* kept) {
+    double anchor_pose[7], pose[7];
+    normalise_pose(anchor_in, anchor_pose);
+    normalise_pose(pose_in, pose);
     int W = P->width, H_ = P->height, N = W * H_;
     uint8_t* a_mask = (uint8_t*)malloc(N);
     uint8_t* o_mask = (uint8_t*)malloc(N);
@@ -608,8 +620,11 @@ int or_normal_equations(const or_params* P, const double anchor_pose[7], const f
 int or_predict(const or_params* P, const or_state* s, const double* imu, int32_t n_imu, double dt,
                or_prior* out) {
     if (!(dt > 0.0)) return -1;
-    double R[9];
-    quat_to_R(s->q, R);
+    double R[9], sp[7], spn[7];
+    for (int a = 0; a < 3; ++a) sp[a] = s->t[a];
+    for (int a = 0; a < 4; ++a) sp[3 + a] = s->q[a];
+    normalise_pose(sp, spn);
+    quat_to_R(spn + 3, R);
     double acc[3] = {0, 0, 0}, gyr[3] = {0, 0, 0}, tm = 0.0, tend = -1e300;
     for (int i = 0; i < n_imu; ++i) {
         tm += imu[7 * i] / n_imu;
@@ -726,8 +741,11 @@ int or_predict(const or_params* P, const or_state* s, const double* imu, int32_t
 /* Pose at tangent coordinates xi around the prior mean: t = t_mu + xi_t,
  * R = Exp(xi_theta) R_mu. */
 static void retract(const or_prior* pr, const double xi[6], double pose[7]) {
-    double Rm[9], E[9], Rn[9];
-    quat_to_R(pr->q, Rm);
+    double Rm[9], E[9], Rn[9], pm[7], pmn[7];
+    for (int a = 0; a < 3; ++a) pm[a] = pr->t[a];
+    for (int a = 0; a < 4; ++a) pm[3 + a] = pr->q[a];
+    normalise_pose(pm, pmn);
+    quat_to_R(pmn + 3, Rm);
     so3_exp(xi + 3, E);
     mat3_mul(E, Rm, Rn);
     for (int a = 0; a < 3; ++a) pose[a] = pr->t[a] + xi[a];
@@ -849,7 +867,9 @@ int or_localise(const or_params* P, const or_prior* pr, const or_state* prev,
  * Colour is updated only where |sdf| <= trunc.  Returns the number of voxels
  * whose occupancy was updated. */
 int64_t or_fuse(const or_params* P, double* occ, double* rgb, double* var_occ, double* var_rgb,
-                const double pose[7], const float* depth, const float* rgb_obs) {
+                const double pose_in[7], const float* depth, const float* rgb_obs) {
+    double pose[7];
+    normalise_pose(pose_in, pose);
     int W = P->width, H = P->height;
     uint8_t* mask = (uint8_t*)malloc((size_t)W * H);
     if (!mask) return -2;

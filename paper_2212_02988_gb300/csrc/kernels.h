@@ -1,0 +1,79 @@
+// kernels.h — host-callable launchers of the PRISM kernels (internal to the
+// library; the public boundary is include/prism.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace prism {
+
+struct KParams;
+struct DevState;
+struct DevStats;
+
+// A pose given either by value (host-supplied) or by a device pointer to 7 doubles.
+struct PoseArg {
+    double p[7];
+    const double* dev;
+};
+
+// Which FP32 matrices k_prep derives from an FP64 pose.
+enum PrepKind : int {
+    PREP_STATE = 0,   // c2w and w2c of the state mean
+    PREP_AUX_C2W = 1, // aux = camera-to-world of the pose argument
+    PREP_AUX_REL = 2, // aux = pose argument -> anchor camera
+    PREP_REL = 3      // rel = Gauss-Newton pose -> anchor camera
+};
+
+// The map planes in brick layout (f32 or bf16 elements).
+struct MapPlanes {
+    void* occ;
+    void* r;
+    void* g;
+    void* b;
+    void* var_occ;
+    void* var_rgb;
+};
+
+// render.cu — mats: 12 FP32 values on the device (DevState::c2w or ::aux);
+// anchor_src/anchor_dst: when given, block 0 copies the 7 pose doubles
+// (the anchor's pose) from src to dst.
+cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& M, float* depth, float* rgb,
+                          uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src,
+                          double* anchor_dst, cudaStream_t s);
+cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s);
+cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, const uint8_t* mask,
+                               float4* a0, float4* a1, cudaStream_t s);
+
+// track.cu — normal-equation passes of the localisation.
+enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2 };
+// Evaluate the objective with the relative transform dev->rel (GN, Laplace)
+// or dev->aux (export) against the packed anchor; the last block reduces
+// the per-block partials in a fixed order and runs the mode's FP64 finish.
+cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
+                         const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
+                         DevState* dev, double* partials, unsigned int* counter, int max_blocks,
+                         DevStats* stats, cudaStream_t s);
+int track_grid(const KParams& P, int max_blocks);
+constexpr int TRACK_NV_MAX = 50;   // doubles per block partial
+
+// state.cu — FP64 prediction and GN start; the FP32 matrices of a pose.
+cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt,
+                           cudaStream_t s);
+cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s);
+
+// fuse.cu — the per-voxel map update with the world-to-camera matrices
+// `w2c` (12 FP32 on the device, DevState::w2c).
+cudaError_t launch_fuse(const KParams& P, const MapPlanes& M, const float* w2c, const float* depth,
+                        const float* rgb, const uint8_t* mask, DevStats* stats, cudaStream_t s);
+
+// mapio.cu — fill with the prior, and conversion between the linear caller
+// layout and the brick layout.
+cudaError_t launch_map_fill(const KParams& P, const MapPlanes& M, float occ, float rgb, float var,
+                            cudaStream_t s);
+cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* occ, const float* rgb,
+                            const float* var_occ, const float* var_rgb, cudaStream_t s);
+cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, float* rgb, float* var_occ,
+                             float* var_rgb, cudaStream_t s);
+
+}  // namespace prism

@@ -1,0 +1,255 @@
+// linalg64.cuh — small FP64 linear algebra for the state kernels (6x6 and
+// 12x12 matrices, row-major), run by one thread or spread over a block.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace prism {
+
+__device__ inline void skew3(const double w[3], double K[9]) {
+    K[0] = 0.0; K[1] = -w[2]; K[2] = w[1];
+    K[3] = w[2]; K[4] = 0.0; K[5] = -w[0];
+    K[6] = -w[1]; K[7] = w[0]; K[8] = 0.0;
+}
+
+__device__ inline void mat3mul(const double* A, const double* B, double* C) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+__device__ inline void mat3vec(const double* A, const double* x, double* y) {
+    for (int i = 0; i < 3; ++i) y[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
+}
+
+// Coefficients of Exp and J_l as functions of th^2.  For th < 1/4 they are
+// the Taylor series of sin(th)/th, (1 - cos th)/th^2 and (th - sin th)/th^3
+// (truncation below 1e-17 there), avoiding FP64 sin/cos on the short
+// dependent chains of the filter; larger angles use sin/cos.
+__device__ inline void so3_coeffs(double th2, double& a, double& b, double& c) {
+    if (th2 < 0.0625) {
+        const double x = th2;
+        a = 1.0 + x * (-1.0 / 6 + x * (1.0 / 120 + x * (-1.0 / 5040 + x * (1.0 / 362880 + x * (-1.0 / 39916800)))));
+        b = 0.5 + x * (-1.0 / 24 + x * (1.0 / 720 + x * (-1.0 / 40320 + x * (1.0 / 3628800 + x * (-1.0 / 479001600)))));
+        c = 1.0 / 6 + x * (-1.0 / 120 + x * (1.0 / 5040 + x * (-1.0 / 362880 + x * (1.0 / 39916800 + x * (-1.0 / 6227020800.0)))));
+    } else {
+        const double th = sqrt(th2), sn = sin(th), cs = cos(th);
+        a = sn / th;
+        b = (1.0 - cs) / th2;
+        c = (th - sn) / (th2 * th);
+    }
+}
+
+// Rodrigues: Exp(w) = I + a K + b K^2
+__device__ inline void so3_exp(const double w[3], double R[9]) {
+    double a, b, c;
+    so3_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], a, b, c);
+    double K[9], K2[9];
+    skew3(w, K);
+    mat3mul(K, K, K2);
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+}
+
+// Left Jacobian of SO(3): I + b K + c K^2
+__device__ inline void so3_jl(const double w[3], double J[9]) {
+    double a, b, c;
+    so3_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], a, b, c);
+    double K[9], K2[9];
+    skew3(w, K);
+    mat3mul(K, K, K2);
+    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0 ? 1.0 : 0.0) + b * K[i] + c * K2[i];
+}
+
+// Inverse left Jacobian of SO(3): I - K/2 + c K^2 with
+// c = 1/th^2 - (1 + cos th) / (2 th sin th); for th < 1/4 its Taylor series
+// 1/12 + th^2/720 + th^4/30240 + th^6/1209600 + th^8/47900160.
+__device__ inline void so3_jl_inv(const double w[3], double J[9]) {
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double c;
+    if (th2 < 0.0625) {
+        c = 1.0 / 12 + th2 * (1.0 / 720 + th2 * (1.0 / 30240 + th2 * (1.0 / 1209600 + th2 * (1.0 / 47900160))));
+    } else {
+        const double th = sqrt(th2);
+        c = 1.0 / th2 - (1.0 + cos(th)) / (2.0 * th * sin(th));
+    }
+    double K[9], K2[9];
+    skew3(w, K);
+    mat3mul(K, K, K2);
+    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0 ? 1.0 : 0.0) - 0.5 * K[i] + c * K2[i];
+}
+
+// Unit quaternion of Exp(w): (cos(th/2), sin(th/2)/th w), with the half-angle
+// coefficients from so3_coeffs' series at th/2.
+__device__ inline void quat_exp(const double w[3], double q[4]) {
+    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double ch, sh;
+    if (th2 < 0.25) {   // x = (th/2)^2 < 1/16
+        const double x = 0.25 * th2;
+        ch = 1.0 + x * (-0.5 + x * (1.0 / 24 + x * (-1.0 / 720 + x * (1.0 / 40320 + x * (-1.0 / 3628800)))));
+        sh = 0.5 * (1.0 + x * (-1.0 / 6 + x * (1.0 / 120 + x * (-1.0 / 5040 + x * (1.0 / 362880 + x * (-1.0 / 39916800))))));
+    } else {
+        const double th = sqrt(th2);
+        ch = cos(0.5 * th);
+        sh = sin(0.5 * th) / th;
+    }
+    q[0] = ch; q[1] = sh * w[0]; q[2] = sh * w[1]; q[3] = sh * w[2];
+}
+
+// Hamilton product a (x) b (w first).
+__device__ inline void quat_mul(const double* a, const double* b, double* q) {
+    q[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    q[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    q[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    q[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// Normalised, with w >= 0.
+__device__ inline void quat_normalise(double* q) {
+    double r = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (q[0] < 0.0) r = -r;
+    for (int i = 0; i < 4; ++i) q[i] *= r;
+}
+
+__device__ inline void mat3inv(const double* A, double* B) {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    double id = 1.0 / det;
+    B[0] = c00 * id;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    B[3] = c01 * id;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    B[6] = c02 * id;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+}
+
+// Unit quaternion (w >= 0) of a rotation matrix (Shepperd's method).
+__device__ inline void R_to_quat(const double* R, double* q) {
+    double tr = R[0] + R[4] + R[8], s;
+    if (tr > 0.0) {
+        s = 2.0 * sqrt(tr + 1.0);
+        q[0] = 0.25 * s; q[1] = (R[7] - R[5]) / s; q[2] = (R[2] - R[6]) / s; q[3] = (R[3] - R[1]) / s;
+    } else if (R[0] > R[4] && R[0] > R[8]) {
+        s = 2.0 * sqrt(1.0 + R[0] - R[4] - R[8]);
+        q[0] = (R[7] - R[5]) / s; q[1] = 0.25 * s; q[2] = (R[1] + R[3]) / s; q[3] = (R[2] + R[6]) / s;
+    } else if (R[4] > R[8]) {
+        s = 2.0 * sqrt(1.0 + R[4] - R[0] - R[8]);
+        q[0] = (R[2] - R[6]) / s; q[1] = (R[1] + R[3]) / s; q[2] = 0.25 * s; q[3] = (R[5] + R[7]) / s;
+    } else {
+        s = 2.0 * sqrt(1.0 + R[8] - R[0] - R[4]);
+        q[0] = (R[3] - R[1]) / s; q[1] = (R[2] + R[6]) / s; q[2] = (R[5] + R[7]) / s; q[3] = 0.25 * s;
+    }
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double sg = q[0] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < 4; ++i) q[i] = sg * q[i] / n;
+}
+
+// Rotation of a unit quaternion (value path; not the decision recipe).
+__device__ inline void quat_to_R(const double* q, double* R) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// In-place Cholesky of an n x n SPD matrix into its lower factor, with the
+// reciprocals of the diagonal in rdiag; false if not positive definite.
+__device__ inline bool cholesky(double* A, double* rdiag, int n) {
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0) || !isfinite(s)) return false;
+        const double r = rsqrt(s);
+        A[j * n + j] = s * r;
+        rdiag[j] = r;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = t * r;
+        }
+    }
+    return true;
+}
+
+// Solve L L^T x = b given the factor (lower triangle) and its diagonal reciprocals.
+__device__ inline void chol_solve(const double* L, const double* rdiag, const double* b, double* x, int n) {
+    double y[12];
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        y[i] = s * rdiag[i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s * rdiag[i];
+    }
+}
+
+// Block-cooperative inverse of an SPD matrix (n <= 12) into Ainv (shared or
+// global): thread 0 factors into the shared scratch L/rdiag, then thread j
+// solves for column j; the result is symmetrised.  Every thread of the
+// block must call it.  Returns false (on every thread) if not PD.
+__device__ inline bool spd_inverse_block(const double* A, double* Ainv, int n, double* L, double* rdiag,
+                                         int* ok) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n * n; ++i) L[i] = A[i];
+        *ok = cholesky(L, rdiag, n) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool good = *ok != 0;
+    if (good && threadIdx.x < n) {
+        double e[12], x[12];
+        for (int i = 0; i < n; ++i) e[i] = (i == (int)threadIdx.x) ? 1.0 : 0.0;
+        chol_solve(L, rdiag, e, x, n);
+        for (int i = 0; i < n; ++i) Ainv[i * n + threadIdx.x] = x[i];
+    }
+    __syncthreads();
+    if (good)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            if (i < j) {
+                const double m = 0.5 * (Ainv[i * n + j] + Ainv[j * n + i]);
+                Ainv[i * n + j] = Ainv[j * n + i] = m;
+            }
+        }
+    __syncthreads();
+    return good;
+}
+
+// C = A (n x k) * B (k x m), computed by the threads of a block (element per thread).
+__device__ inline void block_matmul(const double* A, const double* B, double* C, int n, int k, int m) {
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * m + j];
+        C[e] = s;
+    }
+    __syncthreads();
+}
+
+// C = A^T (A: k x n) * B (k x m)
+__device__ inline void block_matmul_tn(const double* A, const double* B, double* C, int n, int k, int m) {
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s += A[l * n + i] * B[l * m + j];
+        C[e] = s;
+    }
+    __syncthreads();
+}
+
+// C = A (n x k) * B^T (B: m x k)
+__device__ inline void block_matmul_nt(const double* A, const double* B, double* C, int n, int k, int m) {
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+        int i = e / m, j = e % m;
+        double s = 0.0;
+        for (int l = 0; l < k; ++l) s += A[i * k + l] * B[j * k + l];
+        C[e] = s;
+    }
+    __syncthreads();
+}
+
+}  // namespace prism

@@ -1,0 +1,87 @@
+// mapio.cu — map initialisation and conversion between the caller's linear
+// layout (z-major, x fastest, colour interleaved) and the padded planes
+// (a ghost border holding copies of the edge voxels, prism_dev.cuh).
+#include "kernels.h"
+#include "prism_dev.cuh"
+
+namespace prism {
+
+template <bool BF16>
+__global__ void k_map_fill(KParams P, MapPlanes M, float occ, float rgb, float var, uint32_t n) {
+    // n = padded elements per plane; ghosts get the same prior values
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        map_store<BF16>(M.occ, i, occ);
+        map_store<BF16>(M.r, i, rgb);
+        map_store<BF16>(M.g, i, rgb);
+        map_store<BF16>(M.b, i, rgb);
+        map_store<BF16>(M.var_occ, i, var);
+        map_store<BF16>(M.var_rgb, i, var);
+    }
+}
+
+// Every padded element (ghosts included) takes the caller's value of the
+// voxel it clamps to.
+template <bool BF16>
+__global__ void k_map_load(KParams P, MapPlanes M, const float* __restrict__ occ, const float* __restrict__ rgb,
+                           const float* __restrict__ vo, const float* __restrict__ vr, uint32_t n) {
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int gx = (int)(e % P.px) - 1, gy = (int)((e / P.px) % P.py) - 1, gz = (int)(e / P.pxy) - 1;
+        const int x = min(max(gx, 0), P.nx - 1), y = min(max(gy, 0), P.ny - 1), z = min(max(gz, 0), P.nz - 1);
+        const size_t i = ((size_t)z * P.ny + y) * P.nx + x;
+        if (occ) map_store<BF16>(M.occ, e, occ[i]);
+        if (rgb) {
+            map_store<BF16>(M.r, e, rgb[3 * i]);
+            map_store<BF16>(M.g, e, rgb[3 * i + 1]);
+            map_store<BF16>(M.b, e, rgb[3 * i + 2]);
+        }
+        if (vo) map_store<BF16>(M.var_occ, e, vo[i]);
+        if (vr) map_store<BF16>(M.var_rgb, e, vr[i]);
+    }
+}
+
+template <bool BF16>
+__global__ void k_map_store(KParams P, MapPlanes M, float* __restrict__ occ, float* __restrict__ rgb,
+                            float* __restrict__ vo, float* __restrict__ vr, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = i % P.nx, y = (i / P.nx) % P.ny, z = i / (P.nx * P.ny);
+        const uint32_t b = pad_index(P, x, y, z);
+        if (occ) occ[i] = map_load_rw<BF16>(M.occ, b);
+        if (rgb) {
+            rgb[3 * (size_t)i] = map_load_rw<BF16>(M.r, b);
+            rgb[3 * (size_t)i + 1] = map_load_rw<BF16>(M.g, b);
+            rgb[3 * (size_t)i + 2] = map_load_rw<BF16>(M.b, b);
+        }
+        if (vo) vo[i] = map_load_rw<BF16>(M.var_occ, b);
+        if (vr) vr[i] = map_load_rw<BF16>(M.var_rgb, b);
+    }
+}
+
+static unsigned int io_grid(uint32_t n) {
+    uint32_t g = (n + 255) / 256;
+    return g > 152u * 64u ? 152u * 64u : (g ? g : 1u);
+}
+
+cudaError_t launch_map_fill(const KParams& P, const MapPlanes& M, float occ, float rgb, float var, cudaStream_t s) {
+    uint32_t n = P.npad;
+    if (P.bf16) k_map_fill<true><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var, n);
+    else k_map_fill<false><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* occ, const float* rgb,
+                            const float* var_occ, const float* var_rgb, cudaStream_t s) {
+    uint32_t n = P.npad;
+    if (P.bf16) k_map_load<true><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
+    else k_map_load<false><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, float* rgb, float* var_occ,
+                             float* var_rgb, cudaStream_t s) {
+    uint32_t n = (uint32_t)P.nx * P.ny * P.nz;
+    if (P.bf16) k_map_store<true><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
+    else k_map_store<false><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
+    return cudaGetLastError();
+}
+
+}  // namespace prism

@@ -1,0 +1,665 @@
+// prism_abi.cu — the C ABI of include/prism.h: handle life cycle, argument
+// checks, the order in which each entry enqueues its kernels on the
+// handle's stream, and host-side state, counter and timing I/O.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "prism.h"
+#include "prism_dev.cuh"
+
+using namespace prism;
+
+namespace {
+
+enum Phase { PH_PREDICT = 0, PH_LOCALISE, PH_FUSE, PH_RENDER, PH_ANCHOR, PH_COUNT };
+
+struct TimedPair {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct prism_ctx {
+    prism_config cfg{};
+    KParams kp{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t nvox = 0;
+    MapPlanes map{};
+    void* map_block = nullptr;
+    float* a_depth = nullptr;
+    float* a_rgb = nullptr;
+    uint8_t* a_mask = nullptr;
+    float4* a0 = nullptr;
+    float4* a1 = nullptr;
+    uint8_t* o_mask = nullptr;
+    DevState* dstate = nullptr;
+    DevStats* dstats = nullptr;
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    int max_blocks = 0;
+    double* d_imu = nullptr;
+    int imu_cap = 0;
+    bool has_anchor = false;
+    bool has_prior = false;
+    int64_t steps = 0;
+    int64_t bytes = 0;
+    std::string err;
+    bool timing = false;
+    std::vector<TimedPair> pending;
+    std::vector<cudaEvent_t> pool;
+    double acc_ms[PH_COUNT] = {0, 0, 0, 0, 0};
+    int64_t acc_n[PH_COUNT] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+thread_local std::string g_err;   // errors without a handle
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+prism_status fail(prism_handle h, prism_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_err = msg;
+    return st;
+}
+
+prism_status cuda_fail(prism_handle h, cudaError_t e, const char* what) {
+    return fail(h, PRISM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+cudaEvent_t take_event(prism_handle h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseTimer {
+    prism_handle h;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(prism_handle h_, int ph) : h(h_), phase(ph) {
+        if (h->timing) {
+            a = take_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~PhaseTimer() {
+        if (a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, h->stream);
+            h->pending.push_back({phase, a, b});
+        }
+    }
+};
+
+void collect_timing(prism_handle h) {
+    for (auto& t : h->pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            h->acc_ms[t.phase] += ms;
+            h->acc_n[t.phase] += 1;
+        }
+        h->pool.push_back(t.a);
+        h->pool.push_back(t.b);
+    }
+    h->pending.clear();
+}
+
+bool valid_config(const prism_config* c, std::string& why) {
+    auto bad = [&](const char* m) { why = m; return false; };
+    if (!c) return bad("config is NULL");
+    if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0 || (c->nx % 8) || (c->ny % 8) || (c->nz % 8))
+        return bad("nx, ny, nz must be positive multiples of 8");
+    if ((double)(c->nx + 2) * (c->ny + 2) * (c->nz + 2) > 2147483648.0) return bad("grid larger than 2^31 voxels");
+    if (c->storage != PRISM_STORAGE_F32 && c->storage != PRISM_STORAGE_BF16) return bad("storage must be 0 or 1");
+    if (c->width < 3 || c->height < 3 || (double)c->width * c->height > 1.0e8) return bad("image size out of range");
+    if (c->n_gn < 1 || c->n_gn > 1000) return bad("n_gn must be in [1, 1000]");
+    if (!(c->voxel > 0) || !(c->eps > 0) || !(c->fx > 0) || !(c->fy > 0)) return bad("voxel, eps, fx, fy must be > 0");
+    if (!(c->prior_var > 0) || !(c->update_var > 0) || !(c->trunc > 0)) return bad("variances and trunc must be > 0");
+    if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
+        return bad("Laplace scales and IRLS floors must be > 0");
+    if (!(c->ema >= 0 && c->ema <= 1)) return bad("ema must be in [0, 1]");
+    for (double x : {c->origin[0], c->origin[1], c->origin[2], c->cx, c->cy, c->tau, c->max_depth})
+        if (!std::isfinite(x)) return bad("non-finite configuration value");
+    return true;
+}
+
+void fill_kparams(const prism_config* c, KParams& k) {
+    std::memset(&k, 0, sizeof(k));
+    k.nx = c->nx; k.ny = c->ny; k.nz = c->nz;
+    k.nbx = c->nx / 8; k.nby = c->ny / 8; k.nbz = c->nz / 8;
+    k.px = (uint32_t)c->nx + 2; k.py = (uint32_t)c->ny + 2; k.pxy = k.px * k.py;
+    k.npad = k.pxy * ((uint32_t)c->nz + 2);
+    k.W = c->width; k.H = c->height;
+    k.bf16 = c->storage == PRISM_STORAGE_BF16;
+    // the march cannot take more than (nx + ny + nz) vs / eps in-grid samples
+    double kcap = 2.0 * (c->nx + c->ny + c->nz) * c->voxel / c->eps + 2.0;
+    double kuser = c->max_depth > 0 ? std::floor(c->max_depth / c->eps) : kcap;
+    double km = kuser < kcap ? kuser : kcap;
+    k.kmax = km > 2.0e9 ? 2000000000 : (int)km;
+    for (int a = 0; a < 3; ++a) { k.o32[a] = (float)c->origin[a]; k.origin[a] = c->origin[a]; }
+    k.vs32 = (float)c->voxel;
+    k.inv_vs32 = (float)(1.0 / c->voxel);
+    k.eps32 = (float)c->eps;
+    k.tau32 = (float)c->tau;
+    k.trunc32 = (float)c->trunc;
+    k.disc32 = (float)c->disc;
+    k.fx32 = (float)c->fx; k.fy32 = (float)c->fy; k.cx32 = (float)c->cx; k.cy32 = (float)c->cy;
+    k.ifx32 = (float)(1.0 / c->fx); k.ify32 = (float)(1.0 / c->fy);
+    k.gate_geo32 = (float)c->gate_geo; k.gate_rgb32 = (float)c->gate_rgb;
+    k.b_geo32 = (float)c->b_geo; k.b_rgb32 = (float)c->b_rgb;
+    k.floor_geo32 = (float)c->floor_geo; k.floor_rgb32 = (float)c->floor_rgb;
+    k.upd_prec32 = (float)(1.0 / c->update_var);
+    k.vs = c->voxel; k.eps = c->eps; k.tau = c->tau; k.trunc = c->trunc;
+    k.fx = c->fx; k.fy = c->fy; k.cx = c->cx; k.cy = c->cy;
+    for (int i = 0; i < 2; ++i) { k.sigma_vel[i] = c->sigma_vel[i]; k.sigma_pose[i] = c->sigma_pose[i]; }
+    k.ema = c->ema; k.gravity = c->gravity; k.update_var = c->update_var;
+}
+
+void free_all(prism_handle h) {
+    void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->o_mask,
+                    h->dstate, h->dstats, h->partials, h->counter, h->d_imu};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : h->pool) cudaEventDestroy(e);
+}
+
+template <class T>
+cudaError_t dalloc(prism_handle h, T** p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) h->bytes += (int64_t)bytes;
+    return e;
+}
+
+// q / sqrt(((w*w + x*x) + y*y) + z*z): every pose given by the caller is
+// normalised once, here, with exactly these FP64 operations (host code is
+// compiled without floating-point contraction).
+void normalise_pose(const double* in, double* out) {
+    const double n = std::sqrt(((in[3] * in[3] + in[4] * in[4]) + in[5] * in[5]) + in[6] * in[6]);
+    for (int a = 0; a < 3; ++a) out[a] = in[a];
+    for (int a = 0; a < 4; ++a) out[3 + a] = in[3 + a] / n;
+}
+
+bool finite_pose(const double* p) {
+    for (int i = 0; i < 7; ++i)
+        if (!std::isfinite(p[i])) return false;
+    double n = p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6];
+    return n > 1e-20;
+}
+
+prism_status check_flags(prism_handle h) {
+    int flags = 0;
+    CK(h, cudaMemcpy(&flags, &h->dstate->flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+    if (flags) {
+        int zero = 0;
+        CK(h, cudaMemcpy(&h->dstate->flags, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear flags");
+        std::string m = "device reported:";
+        if (flags & FLAG_GN_NOTPD) m += " Gauss-Newton system not positive definite;";
+        if (flags & FLAG_LAPLACE_NOTPD) m += " Laplace Hessian not positive definite (state unchanged);";
+        if (flags & FLAG_PRIOR_NOTPD) m += " prior pose covariance not positive definite;";
+        return fail(h, PRISM_ENOTPD, m);
+    }
+    return PRISM_OK;
+}
+
+prism_status read_state(prism_handle h, prism_state* out) {
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    DevState s;
+    CK(h, cudaMemcpy(&s, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost), "read state");
+    std::memset(out, 0, sizeof(*out));
+    std::memcpy(out->t, s.t, sizeof(s.t));
+    std::memcpy(out->q, s.q, sizeof(s.q));
+    std::memcpy(out->v, s.v, sizeof(s.v));
+    std::memcpy(out->w, s.w, sizeof(s.w));
+    std::memcpy(out->cov, s.cov, sizeof(s.cov));
+    out->n_localised = s.n_localised;
+    return check_flags(h);
+}
+
+prism_status write_state(prism_handle h, const prism_state* s) {
+    DevState d;
+    std::memset(&d, 0, sizeof(d));
+    double pin[7], pn[7];
+    std::memcpy(pin, s->t, 3 * sizeof(double));
+    std::memcpy(pin + 3, s->q, 4 * sizeof(double));
+    normalise_pose(pin, pn);
+    std::memcpy(d.t, pn, sizeof(d.t));
+    std::memcpy(d.q, pn + 3, sizeof(d.q));
+    std::memcpy(d.v, s->v, sizeof(d.v));
+    std::memcpy(d.w, s->w, sizeof(d.w));
+    std::memcpy(d.cov, s->cov, sizeof(d.cov));
+    d.n_localised = s->n_localised;
+    // keep the anchor pose already on the device
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    double anchor[7];
+    CK(h, cudaMemcpy(anchor, h->dstate->anchor_pose, sizeof(anchor), cudaMemcpyDeviceToHost), "read anchor pose");
+    std::memcpy(d.anchor_pose, anchor, sizeof(anchor));
+    CK(h, cudaMemcpy(h->dstate, &d, sizeof(d), cudaMemcpyHostToDevice), "write state");
+    PoseArg pa{};
+    CK(h, launch_prep(h->dstate, PREP_STATE, pa, h->stream), "pose matrices");
+    h->has_prior = false;
+    return PRISM_OK;
+}
+
+prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* hitk = nullptr) {
+    {
+        PhaseTimer t(h, PH_RENDER);
+        // t[3] and q[4] are contiguous: the state mean pose becomes the anchor's pose
+        CK(h, launch_render(h->kp, h->dstate->c2w, h->map, h->a_depth, h->a_rgb, mask, hitk, h->dstats,
+                            h->dstate->t, h->dstate->anchor_pose, h->stream),
+           "render");
+    }
+    PhaseTimer t(h, PH_ANCHOR);
+    CK(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
+    CK(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
+    h->has_anchor = true;
+    return PRISM_OK;
+}
+
+prism_status do_localise(prism_handle h, const float* depth, const float* rgb) {
+    PhaseTimer t(h, PH_LOCALISE);
+    CK(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    PoseArg pa{};
+    CK(h, launch_prep(h->dstate, PREP_REL, pa, h->stream), "pose matrices");
+    for (int it = 0; it < h->cfg.n_gn; ++it)
+        CK(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+                           h->counter, h->max_blocks, h->dstats, h->stream),
+           "Gauss-Newton pass");
+    CK(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+                       h->counter, h->max_blocks, h->dstats, h->stream),
+       "Laplace pass");
+    h->has_prior = false;
+    return PRISM_OK;
+}
+
+prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool mask_ready) {
+    PhaseTimer t(h, PH_FUSE);
+    if (!mask_ready) CK(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    CK(h, launch_fuse(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->stream), "fuse");
+    return PRISM_OK;
+}
+
+prism_status do_predict(prism_handle h, const double* imu, int32_t n, double dt) {
+    if (n > h->imu_cap) {
+        if (h->d_imu) {
+            CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+            cudaFree(h->d_imu);
+            h->bytes -= (int64_t)h->imu_cap * 7 * sizeof(double);
+            h->d_imu = nullptr;
+            h->imu_cap = 0;
+        }
+        int cap = n < 256 ? 256 : n;
+        CK(h, dalloc(h, &h->d_imu, (size_t)cap * 7 * sizeof(double)), "IMU buffer");
+        h->imu_cap = cap;
+    }
+    PhaseTimer t(h, PH_PREDICT);
+    if (n > 0)
+        CK(h, cudaMemcpyAsync(h->d_imu, imu, (size_t)n * 7 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+           "IMU upload");
+    CK(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->stream), "predict");
+    h->has_prior = true;
+    return PRISM_OK;
+}
+
+bool imu_ok(const double* imu, int32_t n, double dt, std::string& why) {
+    if (n < 0) { why = "n must be >= 0"; return false; }
+    if (n > 0 && !imu) { why = "imu is NULL with n > 0"; return false; }
+    if (!(dt > 0) || !std::isfinite(dt)) { why = "dt must be finite and > 0"; return false; }
+    for (int i = 0; i < 7 * n; ++i)
+        if (!std::isfinite(imu[i])) { why = "non-finite IMU value"; return false; }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void prism_config_default(prism_config* c, int32_t n, double extent, int32_t width, int32_t height) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->nx = c->ny = c->nz = n;
+    c->storage = PRISM_STORAGE_F32;
+    c->width = width;
+    c->height = height;
+    c->n_gn = 10;
+    c->voxel = extent / n;
+    for (int a = 0; a < 3; ++a) c->origin[a] = -0.5 * extent;
+    c->fx = c->fy = 70.0 * width / 80.0;
+    c->cx = 0.5 * (width - 1);
+    c->cy = 0.5 * (height - 1);
+    c->eps = 0.4 * c->voxel;
+    c->tau = 0.0;
+    c->max_depth = 0.0;
+    c->trunc = 2.0 * c->voxel;
+    c->prior_var = 1e4;
+    c->init_occ = -0.001;
+    c->init_rgb = 0.0;
+    c->update_var = 1.0;
+    c->sigma_vel[0] = 0.03; c->sigma_vel[1] = 0.03;
+    c->sigma_pose[0] = 0.05; c->sigma_pose[1] = 0.02;
+    c->b_geo = 0.02; c->b_rgb = 0.1;
+    c->gate_geo = 0.45; c->gate_rgb = 0.15;
+    c->floor_geo = 1e-3; c->floor_rgb = 1e-2;
+    c->ema = 0.8;
+    c->disc = 0.1;
+    c->gravity = 9.81;
+}
+
+prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, void* stream, prism_handle* out) {
+    std::string why;
+    if (!out) return fail(nullptr, PRISM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!valid_config(cfg, why)) return fail(nullptr, PRISM_EINVAL, "invalid config: " + why);
+    if (s1) {
+        double p[7];
+        std::memcpy(p, s1->t, 3 * sizeof(double));
+        std::memcpy(p + 3, s1->q, 4 * sizeof(double));
+        if (!finite_pose(p)) return fail(nullptr, PRISM_EINVAL, "initial state pose is not finite");
+    }
+    prism_ctx* h = new (std::nothrow) prism_ctx();
+    if (!h) return fail(nullptr, PRISM_ENOMEM, "host allocation failed");
+    h->cfg = *cfg;
+    fill_kparams(cfg, h->kp);
+    h->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->max_blocks = (sms > 0 ? sms : 152) * 4;
+    h->nvox = (size_t)cfg->nx * cfg->ny * cfg->nz;
+    const size_t es = cfg->storage == PRISM_STORAGE_BF16 ? 2 : 4;
+    const size_t plane = (((size_t)h->kp.npad * es + 255) / 256) * 256;   // padded plane, 256-byte aligned
+    const size_t npix = (size_t)cfg->width * cfg->height;
+    auto cleanup = [&](prism_status st, const std::string& m) {
+        free_all(h);
+        delete h;
+        return fail(nullptr, st, m);
+    };
+    if (dalloc(h, &h->map_block, 6 * plane) != cudaSuccess) return cleanup(PRISM_ENOMEM, "map allocation failed");
+    char* base = (char*)h->map_block;
+    h->map.occ = base;
+    h->map.r = base + plane;
+    h->map.g = base + 2 * plane;
+    h->map.b = base + 3 * plane;
+    h->map.var_occ = base + 4 * plane;
+    h->map.var_rgb = base + 5 * plane;
+    if (dalloc(h, &h->a_depth, npix * 4) || dalloc(h, &h->a_rgb, npix * 12) || dalloc(h, &h->a_mask, npix) ||
+        dalloc(h, &h->a0, npix * 16) || dalloc(h, &h->a1, npix * 16) || dalloc(h, &h->o_mask, npix) ||
+        dalloc(h, &h->dstate, sizeof(DevState)) || dalloc(h, &h->dstats, sizeof(DevStats)) ||
+        dalloc(h, &h->partials, (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(double)) ||
+        dalloc(h, &h->counter, sizeof(unsigned int)))
+        return cleanup(PRISM_ENOMEM, "device allocation failed");
+    cudaGetLastError();
+    if ((e = launch_map_fill(h->kp, h->map, (float)cfg->init_occ, (float)cfg->init_rgb, (float)cfg->prior_var,
+                             h->stream)) != cudaSuccess)
+        return cleanup(PRISM_ECUDA, std::string("map fill: ") + cudaGetErrorString(e));
+    if ((e = cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->dstate, 0, sizeof(DevState), h->stream)) != cudaSuccess)
+        return cleanup(PRISM_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
+    prism_state init;
+    if (s1) {
+        init = *s1;
+    } else {
+        std::memset(&init, 0, sizeof(init));
+        init.q[0] = 1.0;
+        for (int i = 0; i < 12; ++i) init.cov[13 * i] = 1e-8;
+    }
+    prism_status st = write_state(h, &init);
+    if (st != PRISM_OK) return cleanup(st, h->err);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cleanup(PRISM_ECUDA, std::string("create: ") + cudaGetErrorString(e));
+    *out = h;
+    return PRISM_OK;
+}
+
+prism_status prism_destroy(prism_handle h) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return PRISM_OK;
+}
+
+prism_status prism_predict(prism_handle h, const double* imu, int32_t n, double dt) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    std::string why;
+    if (!imu_ok(imu, n, dt, why)) return fail(h, PRISM_EINVAL, why);
+    DeviceGuard g(h->device);
+    return do_predict(h, imu, n, dt);
+}
+
+prism_status prism_localise(prism_handle h, const float* depth, const float* rgb, prism_state* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!depth || !rgb) return fail(h, PRISM_EINVAL, "depth or rgb is NULL");
+    if (!h->has_prior) return fail(h, PRISM_ESTATE, "localise needs prism_predict first");
+    if (!h->has_anchor) return fail(h, PRISM_ESTATE, "localise needs an anchor (prism_render or prism_anchor_load)");
+    DeviceGuard g(h->device);
+    prism_status st = do_localise(h, depth, rgb);
+    if (st != PRISM_OK || !out) return st;
+    return read_state(h, out);
+}
+
+prism_status prism_update_map(prism_handle h, const float* depth, const float* rgb) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!depth || !rgb) return fail(h, PRISM_EINVAL, "depth or rgb is NULL");
+    DeviceGuard g(h->device);
+    return do_fuse(h, depth, rgb, false);
+}
+
+prism_status prism_render(prism_handle h, const double* pose7, float* depth, float* rgb, uint8_t* mask,
+                          int32_t* hitk) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (pose7 && !finite_pose(pose7)) return fail(h, PRISM_EINVAL, "pose is not finite or has a zero quaternion");
+    DeviceGuard g(h->device);
+    const size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    if (pose7) {
+        PhaseTimer t(h, PH_RENDER);
+        PoseArg pa{};
+        normalise_pose(pose7, pa.p);
+        CK(h, launch_prep(h->dstate, PREP_AUX_C2W, pa, h->stream), "pose matrices");
+        CK(h, launch_render(h->kp, h->dstate->aux, h->map, depth, rgb, mask, hitk, h->dstats, nullptr, nullptr,
+                            h->stream),
+           "render");
+        return PRISM_OK;
+    }
+    prism_status st = do_render_anchor(h, mask, hitk);
+    if (st != PRISM_OK) return st;
+    if (depth) CK(h, cudaMemcpyAsync(depth, h->a_depth, npix * 4, cudaMemcpyDeviceToDevice, h->stream), "copy depth");
+    if (rgb) CK(h, cudaMemcpyAsync(rgb, h->a_rgb, npix * 12, cudaMemcpyDeviceToDevice, h->stream), "copy rgb");
+    return PRISM_OK;
+}
+
+prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt, const float* depth,
+                        const float* rgb, prism_state* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!depth || !rgb) return fail(h, PRISM_EINVAL, "depth or rgb is NULL");
+    DeviceGuard g(h->device);
+    prism_status st;
+    bool mask_ready = false;
+    if (h->steps > 0) {
+        std::string why;
+        if (!imu_ok(imu, n, dt, why)) return fail(h, PRISM_EINVAL, why);
+        if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
+        if ((st = do_predict(h, imu, n, dt)) != PRISM_OK) return st;
+        if ((st = do_localise(h, depth, rgb)) != PRISM_OK) return st;
+        mask_ready = true;
+    }
+    if ((st = do_fuse(h, depth, rgb, mask_ready)) != PRISM_OK) return st;
+    if ((st = do_render_anchor(h)) != PRISM_OK) return st;
+    h->steps += 1;
+    if (!out) return PRISM_OK;
+    return read_state(h, out);
+}
+
+prism_status prism_get_state(prism_handle h, prism_state* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!out) return fail(h, PRISM_EINVAL, "out is NULL");
+    DeviceGuard g(h->device);
+    return read_state(h, out);
+}
+
+prism_status prism_set_state(prism_handle h, const prism_state* s) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!s) return fail(h, PRISM_EINVAL, "state is NULL");
+    double p[7];
+    std::memcpy(p, s->t, 3 * sizeof(double));
+    std::memcpy(p + 3, s->q, 4 * sizeof(double));
+    if (!finite_pose(p)) return fail(h, PRISM_EINVAL, "state pose is not finite");
+    DeviceGuard g(h->device);
+    return write_state(h, s);
+}
+
+prism_status prism_map_load(prism_handle h, const float* occ, const float* rgb, const float* var_occ,
+                            const float* var_rgb) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!occ || !rgb || !var_occ || !var_rgb) return fail(h, PRISM_EINVAL, "a map array is NULL");
+    DeviceGuard g(h->device);
+    CK(h, launch_map_load(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map load");
+    return PRISM_OK;
+}
+
+prism_status prism_map_store(prism_handle h, float* occ, float* rgb, float* var_occ, float* var_rgb) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    DeviceGuard g(h->device);
+    CK(h, launch_map_store(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map store");
+    return PRISM_OK;
+}
+
+prism_status prism_anchor_load(prism_handle h, const double* pose7, const float* depth, const float* rgb) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!pose7 || !depth || !rgb) return fail(h, PRISM_EINVAL, "pose, depth or rgb is NULL");
+    if (!finite_pose(pose7)) return fail(h, PRISM_EINVAL, "pose is not finite");
+    DeviceGuard g(h->device);
+    const size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    CK(h, cudaMemcpyAsync(h->a_depth, depth, npix * 4, cudaMemcpyDeviceToDevice, h->stream), "copy depth");
+    CK(h, cudaMemcpyAsync(h->a_rgb, rgb, npix * 12, cudaMemcpyDeviceToDevice, h->stream), "copy rgb");
+    double pn[7];
+    normalise_pose(pose7, pn);
+    CK(h, cudaMemcpyAsync(h->dstate->anchor_pose, pn, 7 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
+       "anchor pose");
+    PhaseTimer t(h, PH_ANCHOR);
+    CK(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
+    CK(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
+    h->has_anchor = true;
+    return PRISM_OK;
+}
+
+prism_status prism_normal_equations(prism_handle h, const double* pose7, const float* depth, const float* rgb,
+                                    double* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!pose7 || !depth || !rgb || !out) return fail(h, PRISM_EINVAL, "NULL argument");
+    if (!finite_pose(pose7)) return fail(h, PRISM_EINVAL, "pose is not finite");
+    if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
+    DeviceGuard g(h->device);
+    CK(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    PoseArg pa{};
+    normalise_pose(pose7, pa.p);
+    CK(h, launch_prep(h->dstate, PREP_AUX_REL, pa, h->stream), "pose matrices");
+    CK(h, launch_track(h->kp, TRACK_EXPORT, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+                       h->counter, h->max_blocks, h->dstats, h->stream),
+       "normal equations");
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    CK(h, cudaMemcpy(out, h->dstate->ne_out, 80 * sizeof(double), cudaMemcpyDeviceToHost), "read normal equations");
+    return PRISM_OK;
+}
+
+prism_status prism_get_stats(prism_handle h, prism_stats* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!out) return fail(h, PRISM_EINVAL, "out is NULL");
+    DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    DevStats s;
+    CK(h, cudaMemcpy(&s, h->dstats, sizeof(s), cudaMemcpyDeviceToHost), "read stats");
+    out->render_rays = (int64_t)s.render_rays;
+    out->render_samples = (int64_t)s.render_samples;
+    out->render_hits = (int64_t)s.render_hits;
+    out->fuse_updates = (int64_t)s.fuse_updates;
+    out->fuse_colour_updates = (int64_t)s.fuse_colour_updates;
+    out->track_pixels = (int64_t)s.track_pixels;
+    return PRISM_OK;
+}
+
+prism_status prism_set_timing(prism_handle h, int32_t enabled) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    h->timing = enabled != 0;
+    return PRISM_OK;
+}
+
+prism_status prism_get_timing(prism_handle h, prism_timing* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!out) return fail(h, PRISM_EINVAL, "out is NULL");
+    DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    collect_timing(h);
+    out->predict_ms = h->acc_ms[PH_PREDICT];
+    out->localise_ms = h->acc_ms[PH_LOCALISE];
+    out->fuse_ms = h->acc_ms[PH_FUSE];
+    out->render_ms = h->acc_ms[PH_RENDER];
+    out->anchor_ms = h->acc_ms[PH_ANCHOR];
+    out->predict_n = h->acc_n[PH_PREDICT];
+    out->localise_n = h->acc_n[PH_LOCALISE];
+    out->fuse_n = h->acc_n[PH_FUSE];
+    out->render_n = h->acc_n[PH_RENDER];
+    out->anchor_n = h->acc_n[PH_ANCHOR];
+    return PRISM_OK;
+}
+
+prism_status prism_timing_reset(prism_handle h) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    collect_timing(h);
+    for (int i = 0; i < PH_COUNT; ++i) { h->acc_ms[i] = 0.0; h->acc_n[i] = 0; }
+    return PRISM_OK;
+}
+
+int64_t prism_device_bytes(prism_handle h) { return h ? h->bytes : 0; }
+
+const char* prism_last_error(prism_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+const char* prism_status_string(int32_t st) {
+    switch (st) {
+        case PRISM_OK: return "ok";
+        case PRISM_EINVAL: return "invalid argument";
+        case PRISM_ENOMEM: return "out of memory";
+        case PRISM_ECUDA: return "CUDA error";
+        case PRISM_ENOTPD: return "matrix not positive definite";
+        case PRISM_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

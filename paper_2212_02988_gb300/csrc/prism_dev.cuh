@@ -1,0 +1,208 @@
+// prism_dev.cuh — device-side building blocks shared by the PRISM kernels:
+// the launch parameter block, the map layout, the FP64 pose recipe
+// that produces the FP32 decision matrices, and the FP32 decision recipe
+// (every operation written with an explicit IEEE-rounded intrinsic so that
+// the compiler cannot contract or reorder it).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace prism {
+
+// ----------------------------------------------------------------- parameters
+// Constants every kernel may need, filled once on the host (FP32 copies are
+// single roundings of the FP64 configuration values).
+struct KParams {
+    int nx, ny, nz;            // voxels
+    int nbx, nby, nbz;         // 8^3 tiles per axis (culling and fuse blocks)
+    uint32_t px, py, pxy;      // padded plane: (nx + 2), (ny + 2), (nx + 2) (ny + 2)
+    uint32_t npad;             // elements of a padded plane
+    int W, H;                  // image size
+    int kmax;                  // last ray sample index
+    int bf16;                  // map storage is bf16
+    float o32[3];              // grid origin
+    float vs32, inv_vs32;      // voxel size and its inverse
+    float eps32, tau32, trunc32, disc32;
+    float fx32, fy32, cx32, cy32, ifx32, ify32;
+    float gate_geo32, gate_rgb32;
+    float b_geo32, b_rgb32, floor_geo32, floor_rgb32;
+    float upd_prec32;          // 1 / update_var
+    double vs, origin[3], eps, tau, trunc;
+    double fx, fy, cx, cy;
+    double sigma_vel[2], sigma_pose[2];
+    double ema, gravity, update_var;
+};
+
+// Device-resident filter state (FP64).  One per handle.
+struct DevState {
+    // posterior q_t(s_t)
+    double t[3], q[4], v[3], w[3];
+    double cov[144];
+    // prior from the prediction step
+    double pt[3], pq[4], pv[3], pw[3];
+    double pcov[144], cov_pp[36], prec_pp[36], D[36], cov_vel[36];
+    // Gauss-Newton iterate: xi in the prior's tangent coordinates, and the pose it gives
+    double xi[6];
+    double cur_pose[7];
+    // pose at which the current anchor was rendered
+    double anchor_pose[7];
+    // last exported normal equations: H(36), g(6), Ht(36), cost, count
+    double ne_out[80];
+    // render-adjoint pose gradient (world-frame perturbation)
+    double grad_pose[6];
+    // FP32 decision matrices, each computed once per pose by the FP64 recipe:
+    float c2w[12];             // state mean, camera -> world: R (9), centre (3)
+    float w2c[12];             // state mean, world -> camera: M (9), b (3)
+    float rel[12];             // Gauss-Newton pose -> anchor camera: M (9), b (3)
+    float aux[12];             // a pose given by the host (render or one objective evaluation)
+    int n_localised;
+    int flags;                 // bit 0: GN system not PD; bit 1: Laplace system not PD; bit 2: prior not PD
+    int pad[2];
+};
+
+enum : int { FLAG_GN_NOTPD = 1, FLAG_LAPLACE_NOTPD = 2, FLAG_PRIOR_NOTPD = 4 };
+
+// Work counters (device, accumulated with warp-aggregated atomics).
+struct DevStats {
+    unsigned long long render_rays, render_samples, render_hits;
+    unsigned long long fuse_updates, fuse_colour_updates, track_pixels;
+};
+
+// ------------------------------------------------------------- map layout
+// Each map plane is stored linear (x fastest, then y, then z) with a
+// one-voxel ghost border: voxel (x, y, z), x in [-1, nx], sits at
+// (x + 1) + px ((y + 1) + py (z + 1)), and every ghost holds a copy of the
+// edge voxel it clamps to.  A trilinear cell with lower corner (x0, y0, z0),
+// x0 in [-1, nx - 1], then reads 8 values at fixed offsets {0, 1, px, px + 1,
+// pxy, ...} from one base index, and gets exactly the values that clamping
+// the corner indices to [0, n - 1] would give.
+__device__ __forceinline__ uint32_t pad_index(const KParams& P, int x, int y, int z) {
+    return (uint32_t)(x + 1) + P.px * ((uint32_t)(y + 1) + P.py * (uint32_t)(z + 1));
+}
+
+template <bool BF16>
+__device__ __forceinline__ float map_load(const void* plane, uint32_t i) {
+    if constexpr (BF16) {
+        return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(plane) + i));
+    } else {
+        return __ldg(reinterpret_cast<const float*>(plane) + i);
+    }
+}
+template <bool BF16>
+__device__ __forceinline__ float map_load_rw(const void* plane, uint32_t i) {
+    if constexpr (BF16) {
+        return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(plane)[i]);
+    } else {
+        return reinterpret_cast<const float*>(plane)[i];
+    }
+}
+template <bool BF16>
+__device__ __forceinline__ void map_store(void* plane, uint32_t i, float v) {
+    if constexpr (BF16) {
+        reinterpret_cast<__nv_bfloat16*>(plane)[i] = __float2bfloat16_rn(v);
+    } else {
+        reinterpret_cast<float*>(plane)[i] = v;
+    }
+}
+
+// --------------------------------------------------------- FP32 decision recipe
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) {
+    return __fmaf_rn(t, __fsub_rn(b, a), a);
+}
+
+// Camera-frame point of pixel (u, v) at z-depth z:
+// (z * ((u - cx) * (1/fx)), z * ((v - cy) * (1/fy)), z).
+__device__ __forceinline__ void backproject_rn(const KParams& P, int u, int v, float z, float out[3]) {
+    out[0] = __fmul_rn(z, __fmul_rn(__fsub_rn((float)u, P.cx32), P.ifx32));
+    out[1] = __fmul_rn(z, __fmul_rn(__fsub_rn((float)v, P.cy32), P.ify32));
+    out[2] = z;
+}
+
+// y_r = fma(M_r0, x0, fma(M_r1, x1, fma(M_r2, x2, b_r)))
+__device__ __forceinline__ void affine_rn(const float M[9], const float b[3], const float x[3], float y[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        y[r] = __fmaf_rn(M[3 * r], x[0], __fmaf_rn(M[3 * r + 1], x[1], __fmaf_rn(M[3 * r + 2], x[2], b[r])));
+}
+
+// ----------------------------------------------------------- FP64 pose recipe
+// Rotation of a unit quaternion (w, x, y, z), products formed first.  Poses
+// enter the library normalised (host poses at the C ABI with the FP64
+// operations of normalise_pose there; device poses by the value path), so
+// the recipe itself needs no square root or division.
+__device__ __forceinline__ void quat_to_R_rn(const double* q, double R[9]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    double xx = __dmul_rn(x, x), yy = __dmul_rn(y, y), zz = __dmul_rn(z, z);
+    double xy = __dmul_rn(x, y), xz = __dmul_rn(x, z), yz = __dmul_rn(y, z);
+    double wx = __dmul_rn(w, x), wy = __dmul_rn(w, y), wz = __dmul_rn(w, z);
+    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(yy, zz)));
+    R[1] = __dmul_rn(2.0, __dsub_rn(xy, wz));
+    R[2] = __dmul_rn(2.0, __dadd_rn(xz, wy));
+    R[3] = __dmul_rn(2.0, __dadd_rn(xy, wz));
+    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, zz)));
+    R[5] = __dmul_rn(2.0, __dsub_rn(yz, wx));
+    R[6] = __dmul_rn(2.0, __dsub_rn(xz, wy));
+    R[7] = __dmul_rn(2.0, __dadd_rn(yz, wx));
+    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, yy)));
+}
+
+// (a0*b0 + a1*b1) + a2*b2, each operation rounded
+__device__ __forceinline__ double dot3_rn(double a0, double b0, double a1, double b1, double a2, double b2) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a0, b0), __dmul_rn(a1, b1)), __dmul_rn(a2, b2));
+}
+
+// FP32 camera-to-world rotation and centre of a pose (render set-up):
+// out = (R (9, row-major), t (3)).
+__device__ __forceinline__ void mats_c2w(const double* pose, float* out) {
+    double R[9];
+    quat_to_R_rn(pose + 3, R);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i] = (float)R[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[9 + a] = (float)pose[a];
+}
+
+// FP32 world-to-camera transform of a pose: M = R^T, b = -((R0i t0 + R1i t1) + R2i t2).
+__device__ __forceinline__ void mats_w2c(const double* pose, float* out) {
+    double R[9];
+    quat_to_R_rn(pose + 3, R);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) out[3 * i + j] = (float)R[3 * j + i];
+        out[9 + i] = (float)(-dot3_rn(R[i], pose[0], R[3 + i], pose[1], R[6 + i], pose[2]));
+    }
+}
+
+// FP32 transform from the camera at `pose` to the camera at `anchor`:
+// M = Ra^T R, b = Ra^T (t - ta).
+__device__ __forceinline__ void mats_rel(const double* pose, const double* anchor, float* out) {
+    double R[9], Ra[9], d[3];
+    quat_to_R_rn(pose + 3, R);
+    quat_to_R_rn(anchor + 3, Ra);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            out[3 * i + j] = (float)dot3_rn(Ra[i], R[j], Ra[3 + i], R[3 + j], Ra[6 + i], R[6 + j]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = __dsub_rn(pose[a], anchor[a]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[9 + i] = (float)dot3_rn(Ra[i], d[0], Ra[3 + i], d[1], Ra[6 + i], d[2]);
+}
+
+// --------------------------------------------------------- warp helpers
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace prism

@@ -1,0 +1,208 @@
+"""Python face of the C ABI (include/prism.h): argument marshalling only.
+
+Every method forwards to the prism_* entry of the same name; device arrays
+are torch CUDA tensors (float32, contiguous), host arrays numpy.  All work
+runs in libprism.so's kernels on the stream the filter was created with.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Config, State, Stats, Timing
+
+
+class PrismError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def config(n: int, extent: float, width: int, height: int, **overrides) -> Config:
+    """prism_config_default plus field overrides (origin / sigma_* take sequences)."""
+    c = Config()
+    _lib.load().prism_config_default(C.byref(c), n, extent, width, height)
+    for k, v in overrides.items():
+        if k in ("origin", "sigma_vel", "sigma_pose"):
+            for i, x in enumerate(v):
+                getattr(c, k)[i] = x
+        elif k == "storage" and isinstance(v, str):
+            c.storage = {"f32": _lib.STORAGE_F32, "bf16": _lib.STORAGE_BF16}[v]
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def make_state(pose7, vel6=None, cov=None, n_localised: int = 0) -> State:
+    s = State()
+    pose7 = np.asarray(pose7, dtype=np.float64)
+    vel6 = np.zeros(6) if vel6 is None else np.asarray(vel6, dtype=np.float64)
+    cov = np.eye(12) * 1e-8 if cov is None else np.asarray(cov, dtype=np.float64)
+    for a in range(3):
+        s.t[a], s.v[a], s.w[a] = pose7[a], vel6[a], vel6[3 + a]
+    for a in range(4):
+        s.q[a] = pose7[3 + a]
+    for i in range(144):
+        s.cov[i] = cov.flat[i]
+    s.n_localised = n_localised
+    return s
+
+
+def state_arrays(s: State) -> dict:
+    return {"pose": np.array(list(s.t) + list(s.q)), "vel": np.array(list(s.v) + list(s.w)),
+            "cov": np.array(s.cov[:]).reshape(12, 12), "n_localised": int(s.n_localised)}
+
+
+def _dptr(t: torch.Tensor | None, shape=None, dtype=torch.float32, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Filter:
+    """One PRISM filter (map + state + anchor) on one CUDA device."""
+
+    def __init__(self, cfg: Config, s1: State | None = None, stream: torch.cuda.Stream | None = None,
+                 device: int | None = None):
+        self.L = _lib.load()
+        self.cfg = cfg
+        self.device = torch.cuda.current_device() if device is None else device
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = C.c_void_p()
+            self._check(self.L.prism_create_map(C.byref(cfg), C.byref(s1) if s1 is not None else None,
+                                                C.c_void_p(self.stream.cuda_stream), C.byref(h)), None)
+        self.h = h
+        self.W, self.H = cfg.width, cfg.height
+        self.N = cfg.nx * cfg.ny * cfg.nz
+
+    # ------------------------------------------------------------- plumbing
+    def _check(self, status: int, h):
+        if status != _lib.OK:
+            msg = self.L.prism_last_error(h).decode()
+            raise PrismError(status, msg)
+
+    def _img(self, depth, rgb):
+        return (_dptr(depth, (self.H, self.W), name="depth"), _dptr(rgb, (self.H, self.W, 3), name="rgb"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._check(self.L.prism_destroy(self.h), None)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ the ABI
+    def predict(self, imu: np.ndarray | None, dt: float):
+        imu = np.zeros((0, 7)) if imu is None else np.ascontiguousarray(imu, dtype=np.float64)
+        if imu.ndim != 2 or imu.shape[1] != 7:
+            raise ValueError("imu must be (n, 7)")
+        self._check(self.L.prism_predict(self.h, _hptr(imu) if len(imu) else None, len(imu), dt), self.h)
+
+    def localise(self, depth, rgb, want_state: bool = True):
+        d, c = self._img(depth, rgb)
+        out = State() if want_state else None
+        self._check(self.L.prism_localise(self.h, d, c, C.byref(out) if out is not None else None), self.h)
+        return out
+
+    def update_map(self, depth, rgb):
+        d, c = self._img(depth, rgb)
+        self._check(self.L.prism_update_map(self.h, d, c), self.h)
+
+    def render(self, pose7=None, depth=None, rgb=None, mask=None, hitk=None, alloc: bool = True):
+        """Render at pose7 (None: the state mean, which also sets the anchor).
+        Missing outputs are allocated when alloc is True."""
+        dev = torch.device("cuda", self.device)
+        if alloc:
+            depth = torch.empty((self.H, self.W), device=dev) if depth is None else depth
+            rgb = torch.empty((self.H, self.W, 3), device=dev) if rgb is None else rgb
+            mask = torch.empty((self.H, self.W), dtype=torch.uint8, device=dev) if mask is None else mask
+            hitk = torch.empty((self.H, self.W), dtype=torch.int32, device=dev) if hitk is None else hitk
+        p = None if pose7 is None else np.ascontiguousarray(pose7, dtype=np.float64)
+        self._check(self.L.prism_render(self.h, _hptr(p), _dptr(depth, (self.H, self.W), name="depth"),
+                                        _dptr(rgb, (self.H, self.W, 3), name="rgb"),
+                                        _dptr(mask, (self.H, self.W), torch.uint8, "mask"),
+                                        _dptr(hitk, (self.H, self.W), torch.int32, "hitk")), self.h)
+        return {"depth": depth, "rgb": rgb, "mask": mask, "hitk": hitk}
+
+    def step(self, imu, dt, depth, rgb, want_state: bool = False):
+        imu = np.zeros((0, 7)) if imu is None else np.ascontiguousarray(imu, dtype=np.float64)
+        d, c = self._img(depth, rgb)
+        out = State() if want_state else None
+        self._check(self.L.prism_step(self.h, _hptr(imu) if len(imu) else None, len(imu), dt, d, c,
+                                      C.byref(out) if out is not None else None), self.h)
+        return out
+
+    def get_state(self) -> State:
+        s = State()
+        self._check(self.L.prism_get_state(self.h, C.byref(s)), self.h)
+        return s
+
+    def set_state(self, s: State):
+        self._check(self.L.prism_set_state(self.h, C.byref(s)), self.h)
+
+    def map_load(self, occ, rgb, var_occ, var_rgb):
+        N = self.N
+        self._check(self.L.prism_map_load(self.h, _dptr(occ.reshape(-1), (N,), name="occ"),
+                                          _dptr(rgb.reshape(-1), (3 * N,), name="rgb"),
+                                          _dptr(var_occ.reshape(-1), (N,), name="var_occ"),
+                                          _dptr(var_rgb.reshape(-1), (N,), name="var_rgb")), self.h)
+
+    def map_store(self) -> dict:
+        dev = torch.device("cuda", self.device)
+        n = (self.cfg.nz, self.cfg.ny, self.cfg.nx)
+        out = {"occ": torch.empty(n, device=dev), "rgb": torch.empty(n + (3,), device=dev),
+               "var_occ": torch.empty(n, device=dev), "var_rgb": torch.empty(n, device=dev)}
+        self._check(self.L.prism_map_store(self.h, *(C.c_void_p(out[k].data_ptr())
+                                                      for k in ("occ", "rgb", "var_occ", "var_rgb"))),
+                    self.h)
+        return out
+
+    def anchor_load(self, pose7, depth, rgb):
+        p = np.ascontiguousarray(pose7, dtype=np.float64)
+        d, c = self._img(depth, rgb)
+        self._check(self.L.prism_anchor_load(self.h, _hptr(p), d, c), self.h)
+
+    def normal_equations(self, pose7, depth, rgb) -> dict:
+        p = np.ascontiguousarray(pose7, dtype=np.float64)
+        d, c = self._img(depth, rgb)
+        out = np.zeros(80)
+        self._check(self.L.prism_normal_equations(self.h, _hptr(p), d, c, _hptr(out)), self.h)
+        return {"H": out[:36].reshape(6, 6), "g": out[36:42], "Ht": out[42:78].reshape(6, 6),
+                "cost": out[78], "count": out[79]}
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.L.prism_get_stats(self.h, C.byref(s)), self.h)
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_timing(self, enabled: bool = True):
+        self._check(self.L.prism_set_timing(self.h, int(enabled)), self.h)
+
+    def timing(self) -> dict:
+        t = Timing()
+        self._check(self.L.prism_get_timing(self.h, C.byref(t)), self.h)
+        return {k: getattr(t, k) for k, _ in Timing._fields_}
+
+    def timing_reset(self):
+        self._check(self.L.prism_timing_reset(self.h), self.h)
+
+    def device_bytes(self) -> int:
+        return int(self.L.prism_device_bytes(self.h))

@@ -1,0 +1,91 @@
+"""CPU-side checks of the C ABI: libprism.so loads and exports every
+function include/prism.h declares, the ctypes mirrors match the C struct
+layouts, and prism_config_default carries the paper's constants."""
+import ctypes as C
+import json
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2212_02988_gb300 import build as B
+    B.build()
+    from paper_2212_02988_gb300 import _lib
+    return _lib
+
+
+def test_exports_every_declared_function(lib):
+    names = lib.header_functions()
+    assert len(names) >= 20
+    L = lib.load()
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    src = tmp_path / "probe.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "prism.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(prism_config), sizeof(prism_state), sizeof(prism_stats), sizeof(prism_timing));
+  printf("%zu %zu %zu\\n", offsetof(prism_config, voxel), offsetof(prism_config, gravity), offsetof(prism_state, n_localised));
+  return 0;
+}
+""")
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    a, b = subprocess.check_output([str(exe)], text=True).split("\n")[:2]
+    sizes = [int(x) for x in a.split()]
+    offs = [int(x) for x in b.split()]
+    assert sizes == [C.sizeof(lib.Config), C.sizeof(lib.State), C.sizeof(lib.Stats), C.sizeof(lib.Timing)]
+    assert offs == [lib.Config.voxel.offset, lib.Config.gravity.offset, lib.State.n_localised.offset]
+
+
+def test_config_default_is_the_paper(lib):
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    c = lib.Config()
+    lib.load().prism_config_default(C.byref(c), 256, 6.4, 640, 480)
+    assert c.voxel == pytest.approx(0.025)
+    assert c.eps == pytest.approx(gold["eps_over_voxel"]["value"] * c.voxel)
+    assert c.trunc == pytest.approx(gold["trunc_over_voxel"]["value"] * c.voxel)
+    assert c.tau == gold["tau"]["value"]
+    assert c.update_var == gold["sigma_update"]["value"] ** 2
+    assert (c.init_occ, c.init_rgb) == (gold["init_occ"]["value"], gold["init_rgb"]["value"])
+    assert list(c.sigma_vel) == [gold["sigma_vel_translation"]["value"], gold["sigma_vel_rotation"]["value"]]
+    assert list(c.sigma_pose) == [gold["sigma_pose_translation"]["value"], gold["sigma_pose_rotation"]["value"]]
+    assert (c.gate_geo, c.gate_rgb, c.b_geo, c.b_rgb, c.ema) == (
+        gold["gate_geo"]["value"], gold["gate_rgb"]["value"], gold["b_geo"]["value"], gold["b_rgb"]["value"],
+        gold["ema"]["value"])
+    assert c.fx == 560.0 and c.cx == 319.5 and c.cy == 239.5
+
+
+def test_invalid_config_rejected_without_gpu_work(lib):
+    L = lib.load()
+    c = lib.Config()
+    L.prism_config_default(C.byref(c), 64, 4.0, 80, 60)
+    c.nx = 60                                   # not a multiple of 8
+    h = C.c_void_p()
+    assert L.prism_create_map(C.byref(c), None, None, C.byref(h)) == lib.EINVAL
+    assert b"multiples of 8" in L.prism_last_error(None)
+    assert L.prism_destroy(None) == lib.EINVAL
+    assert L.prism_status_string(lib.ENOTPD) == b"matrix not positive definite"
+
+
+def test_product_path_does_not_touch_the_oracle():
+    """The package and its C sources never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_2212_02988_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text, f
