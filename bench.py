@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput of the PRISM filter hot path (arXiv 2212.02988) on GB300.
+
+One step is one full filter step through the C ABI (prism_step): predict
+from the frame's IMU window, localise (10 Gauss-Newton passes and the
+Laplace pass), fuse the frame into the map, render the next anchor — on
+one 640x480 RGB-D frame against a 256^3 map (the workload's defaults).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is frames/s of the whole job with the frames
+already on the device; `e2e` is the same metric through the same public
+call with each frame copied from pinned host memory and the state read back
+every step.  Under torchrun each rank runs an independent filter replica on
+its own GPU (the filter does not shard); the max elapsed time over ranks is
+used.  `--impl reference` times the FP64 CPU oracle on the host instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filter frames/s & p50/p99 step latency; render Mrays/s and % of HBM peak"
+UNIT = "frames/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="room256_640x480")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--reference-budget-s", type=float, default=150.0)
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ ranks
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def combine_over_ranks(elapsed_s: float, units: float, group=None):
+    """(max elapsed over ranks, sum of units over ranks); identity without a
+    process group."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return elapsed_s, units
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "50", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- roofline
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def render_source_hash():
+    h = hashlib.sha256()
+    for f in ("render.cu", "prism_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2212_02988_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per render launch from the committed ncu summary, if it
+    was taken on the current render source; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_render_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != render_source_hash():
+        return None
+    try:
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2212_02988_gb300 import Filter, config, make_state
+    from synth.gpu_frames import raycast_frames
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.PRESETS[args.workload]
+    K, W = args.steps, max(args.warmup, 0)
+    n_frames = 1 + W + K
+    seq = synth.Sequence(w, n_frames=n_frames, seed=w.seed + 100 * rank)
+    occ, rgb, vo, vr = seq.settled_map()
+    maps = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (occ, rgb, vo, vr)]
+    D, C = [], []
+    for c0 in range(0, n_frames, 64):
+        d, c = raycast_frames(seq, range(c0, min(n_frames, c0 + 64)), dev)
+        D.append(d)
+        C.append(c)
+    D, C = torch.cat(D), torch.cat(C)
+    imus = [None] + [seq.imu_window(i) for i in range(1, n_frames)]
+    storage = "bf16" if w.storage == "bf16" else "f32"
+    cfg = config(w.n, w.extent, w.width, w.height, storage=storage)
+    s1 = make_state(seq.pose7(0), seq.velocity(0))
+
+    # ---- device-resident run ----
+    F = Filter(cfg, s1, device=local_rank)
+    F.map_load(*maps)
+    F.step(None, w.dt, D[0], C[0])
+    F.set_detail_counters(True)
+    st_w0 = F.stats()
+    for i in range(1, 1 + W):
+        F.step(imus[i], w.dt, D[i], C[i])
+    st_w1 = F.stats()
+    F.set_detail_counters(False)
+    F.set_timing(True)
+    F.timing_reset()
+    st0 = F.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e_start.record()
+    for j in range(K):
+        i = 1 + W + j
+        ev[j][0].record()
+        F.step(imus[i], w.dt, D[i], C[i])
+        ev[j][1].record()
+    e_end.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    total_ms = e_start.elapsed_time(e_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st1 = F.stats()
+    tm = F.timing()
+    elapsed, frames = combine_over_ranks(total_ms / 1000.0, float(K))
+    F.close()
+
+    d_st = {k: st1[k] - st0[k] for k in st1}
+    rays_per = d_st["render_rays"] / max(tm["render_n"], 1)
+    samp_per = d_st["render_samples"] / max(tm["render_n"], 1)
+    hits_per = d_st["render_hits"] / max(tm["render_n"], 1)
+    render_ms = tm["render_ms"] / max(tm["render_n"], 1)
+    b = 2 if storage == "bf16" else 4
+    G = samp_per * 8 * b + hits_per * 2 * 8 * 3 * b              # logical gathered voxel bytes
+    warm = {k: st_w1[k] - st_w0[k] for k in st_w1}
+    u_ratio = warm["render_unique_corners"] / max(warm["render_samples"] * 8, 1)
+    U = samp_per * 8 * b * u_ratio + hits_per * 8 * 3 * b         # per-ray unique bytes (estimate, see DESIGN)
+    peak, peak_kind = measured_peaks()
+    achieved_G = G / (render_ms * 1e-3) / 1e9
+    achieved = U / (render_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.workload)
+    # localisation passes: per pass the observed frame (depth 4 B + mask 1 B + colour 12 B per
+    # pixel) and the packed anchor (2 x 16 B per pixel) are the bytes the method must read
+    npx = w.width * w.height
+    loc_bytes = (cfg.n_gn + 1) * npx * (4 + 1 + 12 + 32)
+    loc_ms = tm["localise_ms"] / max(tm["localise_n"], 1)
+
+    # ---- end to end through the same public call ----
+    e2e = None
+    if not args.no_e2e:
+        Dh = D.cpu().pin_memory()
+        Ch = C.cpu().pin_memory()
+        d_buf, c_buf = torch.empty_like(D[0]), torch.empty_like(C[0])
+        F2 = Filter(cfg, s1, device=local_rank)
+        F2.map_load(*maps)
+        F2.step(None, w.dt, D[0], C[0])
+        for i in range(1, 1 + W):
+            F2.step(imus[i], w.dt, D[i], C[i])
+        torch.cuda.synchronize()
+        barrier()
+        lat = []
+        t0 = time.perf_counter()
+        for j in range(K):
+            i = 1 + W + j
+            ts = time.perf_counter()
+            d_buf.copy_(Dh[i], non_blocking=True)
+            c_buf.copy_(Ch[i], non_blocking=True)
+            F2.step(imus[i], w.dt, d_buf, c_buf, want_state=True)   # state read back to the host
+            lat.append((time.perf_counter() - ts) * 1e3)
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        e2e_elapsed, e2e_frames = combine_over_ranks(e2e_s, float(K))
+        F2.close()
+        imu_bytes = sum(imus[1 + W + j].nbytes for j in range(K)) / K
+        from paper_2212_02988_gb300._lib import State
+        import ctypes
+        e2e = {"value": e2e_frames / e2e_elapsed, "unit": UNIT,
+               "h2d_bytes_per_step": int(d_buf.numel() * 4 + c_buf.numel() * 4 + imu_bytes),
+               "d2h_bytes_per_step": ctypes.sizeof(State),
+               "p50_step_ms": statistics.median(lat), "p99_step_ms": float(np.percentile(lat, 99))}
+
+    res = {
+        "metric": METRIC, "value": frames / elapsed, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 6x6 solve and state covariance)" if storage == "f32" else "bf16 map, f32 math",
+        "data": "synthetic (seeded analytic scene; RGB-D frames ray-cast on the GPU, IMU from the trajectory)",
+        "config": {"workload": w.name, "map": f"{w.n}^3 @ {w.voxel * 100:.2f} cm, {storage}",
+                   "frames": f"{w.width}x{w.height} RGB-D at {w.rate:g} Hz, IMU {w.imu_rate:g} Hz",
+                   "gauss_newton_iterations": cfg.n_gn,
+                   "l2": "no flush; working set larger than L2 (map planes 6 x %.0f MB)" % (
+                       (w.n + 2) ** 3 * b / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+        "render_mrays_per_s": rays_per / (render_ms * 1e-3) / 1e6,
+        "render_pct_hbm_peak": 100.0 * achieved_G / peak,
+        "phase_ms_per_step": {k[:-3]: tm[k] / max(tm[k[:-3] + "_n"], 1) for k in
+                              ("predict_ms", "localise_ms", "fuse_ms", "render_ms", "anchor_ms")},
+        "roofline": {"kernel": "k_render", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": traffic,
+                     "algorithmic_bytes": "U = distinct occupancy corners per ray x %d B + hits x 8 x 3 x %d B "
+                                          "colour corners, per launch" % (b, b),
+                     "bytes_per_launch": U, "samples_per_launch": samp_per,
+                     "gathered_bytes_per_launch": G, "frac_gathered": achieved_G / peak,
+                     "ms_per_launch": render_ms},
+        "roofline_localise": {"kernels": "k_track (Gauss-Newton x %d, Laplace) + mask + pose matrices" % cfg.n_gn,
+                              "bound": "latency (FP64 tail of each pass)",
+                              "achieved": loc_bytes / (loc_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": loc_bytes / (loc_ms * 1e-3) / 1e9 / peak, "bytes_per_step": loc_bytes,
+                              "ms_per_step": loc_ms},
+        "e2e": e2e,
+        "gpu_launches": int(d_st["kernel_launches"]),
+        "clocks": clocks,
+    }
+    return res
+
+
+def cpu_baseline(args):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    full filter steps of the same configuration on the host."""
+    import synth
+    from oracle import oracle as O
+    w = synth.PRESETS[args.workload]
+    n = max(1, args.cpu_sample_steps)
+    seq = synth.Sequence(w, n_frames=n + 2)
+    p = O.params(w)
+    frames = [seq.frame(i) for i in range(n + 1)]
+    F = O.Filter(p, seq.settled_map(), O.make_state(seq.pose7(0), seq.velocity(0)))
+    F.step(frames[0]["depth"], frames[0]["rgb"])
+    t0 = time.perf_counter()
+    for i in range(1, n + 1):
+        F.step(frames[i]["depth"], frames[i]["rgb"], seq.imu_window(i), w.dt)
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full filter steps (frames 1-{n}) of {w.name}, single-threaded FP64 C"}
+
+
+def run_reference(args, rank):
+    """Reference arm: the oracle timed on the host cores, on our config and metric."""
+    import synth
+    from oracle import oracle as O
+    w = synth.PRESETS[args.workload]
+    K, W = args.steps, max(args.warmup, 0)
+    seq = synth.Sequence(w, n_frames=min(1 + W + K, w.n_frames))
+    p = O.params(w)
+    F = O.Filter(p, seq.settled_map(), O.make_state(seq.pose7(0), seq.velocity(0)))
+    f0 = seq.frame(0)
+    F.step(f0["depth"], f0["rgb"])
+    # warm-up: one step (the oracle has no caches to warm beyond the first)
+    t_w = time.perf_counter()
+    for i in range(1, 1 + min(W, 1)):
+        f = seq.frame(i)
+        F.step(f["depth"], f["rgb"], seq.imu_window(i), w.dt)
+    per_step = time.perf_counter() - t_w if W else 5.0
+    n_run = max(1, min(K, int(args.reference_budget_s / max(per_step, 1e-3))))
+    frames = [seq.frame(i) for i in range(2, 2 + n_run)]
+    t0 = time.perf_counter()
+    for j, f in enumerate(frames):
+        F.step(f["depth"], f["rgb"], seq.imu_window(2 + j), w.dt)
+    el = time.perf_counter() - t0
+    v = n_run / el
+    sample = (f"{n_run} of {K} requested full filter steps of {w.name} (frames 2-{1 + n_run}), "
+              f"single-threaded FP64 C oracle, time-bounded at {args.reference_budget_s:.0f} s")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": n_run,
+            "warmup": min(W, 1), "ms_per_step": 1e3 * el / n_run, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name}, "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                                              "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank)))
+        return 0
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(args)
+        else:
+            res["cpu_baseline"] = None
+        print(json.dumps(res))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

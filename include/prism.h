@@ -112,6 +112,9 @@ typedef struct {
     int64_t fuse_updates;        /* voxels whose occupancy was updated */
     int64_t fuse_colour_updates; /* voxels whose colour was updated */
     int64_t track_pixels;        /* pixel evaluations of the localisation objective */
+    int64_t render_unique_corners; /* distinct occupancy corners per ray, summed (only while
+                                      detail counters are on; see prism_set_detail_counters) */
+    int64_t kernel_launches;     /* CUDA kernels this handle has launched */
 } prism_stats;
 
 /* Per-phase device time (CUDA events on the handle's stream), in ms,
@@ -208,9 +211,12 @@ prism_status prism_anchor_load(prism_handle h, const double* pose7, const float*
 prism_status prism_normal_equations(prism_handle h, const double* pose7, const float* depth,
                                     const float* rgb, double* out);
 
-/* Work counters and per-phase timing. */
+/* Work counters and per-phase timing.  Detail counters (off by default)
+ * make the render also count the distinct trilinear corners each ray
+ * reads, at a few instructions per sample. */
 prism_status prism_get_stats(prism_handle h, prism_stats* out);
 prism_status prism_set_timing(prism_handle h, int32_t enabled);
+prism_status prism_set_detail_counters(prism_handle h, int32_t enabled);
 prism_status prism_get_timing(prism_handle h, prism_timing* out);   /* synchronises */
 prism_status prism_timing_reset(prism_handle h);
 

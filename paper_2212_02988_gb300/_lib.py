@@ -39,7 +39,8 @@ class State(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("render_rays", "render_samples", "render_hits",
-                                         "fuse_updates", "fuse_colour_updates", "track_pixels")]
+                                         "fuse_updates", "fuse_colour_updates", "track_pixels",
+                                         "render_unique_corners", "kernel_launches")]
 
 
 class Timing(C.Structure):
@@ -86,6 +87,7 @@ def load() -> C.CDLL:
         "prism_normal_equations": (st, [H, dp, fp, fp, dp]),
         "prism_get_stats": (st, [H, P(Stats)]),
         "prism_set_timing": (st, [H, C.c_int32]),
+        "prism_set_detail_counters": (st, [H, C.c_int32]),
         "prism_get_timing": (st, [H, P(Timing)]),
         "prism_timing_reset": (st, [H]),
         "prism_device_bytes": (C.c_int64, [H]),

@@ -40,7 +40,7 @@ struct MapPlanes {
 // (the anchor's pose) from src to dst.
 cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& M, float* depth, float* rgb,
                           uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src,
-                          double* anchor_dst, cudaStream_t s);
+                          double* anchor_dst, bool detail, cudaStream_t s);
 cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s);
 cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, const uint8_t* mask,
                                float4* a0, float4* a1, cudaStream_t s);

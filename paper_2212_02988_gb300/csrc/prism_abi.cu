@@ -52,6 +52,8 @@ struct prism_ctx {
     int64_t bytes = 0;
     std::string err;
     bool timing = false;
+    bool detail = false;
+    int64_t launches = 0;
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> pool;
     double acc_ms[PH_COUNT] = {0, 0, 0, 0, 0};
@@ -85,6 +87,14 @@ prism_status cuda_fail(prism_handle h, cudaError_t e, const char* what) {
 
 #define CK(h, call, what)                                  \
     do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+// A kernel launch: counted (prism_stats.kernel_launches), then checked.
+#define LAUNCH(h, call, what)                              \
+    do {                                                   \
+        ++(h)->launches;                                   \
         cudaError_t e_ = (call);                           \
         if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
     } while (0)
@@ -264,7 +274,7 @@ prism_status write_state(prism_handle h, const prism_state* s) {
     std::memcpy(d.anchor_pose, anchor, sizeof(anchor));
     CK(h, cudaMemcpy(h->dstate, &d, sizeof(d), cudaMemcpyHostToDevice), "write state");
     PoseArg pa{};
-    CK(h, launch_prep(h->dstate, PREP_STATE, pa, h->stream), "pose matrices");
+    LAUNCH(h, launch_prep(h->dstate, PREP_STATE, pa, h->stream), "pose matrices");
     h->has_prior = false;
     return PRISM_OK;
 }
@@ -273,27 +283,27 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
     {
         PhaseTimer t(h, PH_RENDER);
         // t[3] and q[4] are contiguous: the state mean pose becomes the anchor's pose
-        CK(h, launch_render(h->kp, h->dstate->c2w, h->map, h->a_depth, h->a_rgb, mask, hitk, h->dstats,
-                            h->dstate->t, h->dstate->anchor_pose, h->stream),
-           "render");
+        LAUNCH(h, launch_render(h->kp, h->dstate->c2w, h->map, h->a_depth, h->a_rgb, mask, hitk, h->dstats,
+                                h->dstate->t, h->dstate->anchor_pose, h->detail, h->stream),
+               "render");
     }
     PhaseTimer t(h, PH_ANCHOR);
-    CK(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
-    CK(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
+    LAUNCH(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
+    LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
     h->has_anchor = true;
     return PRISM_OK;
 }
 
 prism_status do_localise(prism_handle h, const float* depth, const float* rgb) {
     PhaseTimer t(h, PH_LOCALISE);
-    CK(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
     PoseArg pa{};
-    CK(h, launch_prep(h->dstate, PREP_REL, pa, h->stream), "pose matrices");
+    LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream), "pose matrices");
     for (int it = 0; it < h->cfg.n_gn; ++it)
-        CK(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+        LAUNCH(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                            h->counter, h->max_blocks, h->dstats, h->stream),
            "Gauss-Newton pass");
-    CK(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+    LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                        h->counter, h->max_blocks, h->dstats, h->stream),
        "Laplace pass");
     h->has_prior = false;
@@ -302,8 +312,8 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb) {
 
 prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool mask_ready) {
     PhaseTimer t(h, PH_FUSE);
-    if (!mask_ready) CK(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
-    CK(h, launch_fuse(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->stream), "fuse");
+    if (!mask_ready) LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    LAUNCH(h, launch_fuse(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->stream), "fuse");
     return PRISM_OK;
 }
 
@@ -324,7 +334,7 @@ prism_status do_predict(prism_handle h, const double* imu, int32_t n, double dt)
     if (n > 0)
         CK(h, cudaMemcpyAsync(h->d_imu, imu, (size_t)n * 7 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
            "IMU upload");
-    CK(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->stream), "predict");
+    LAUNCH(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->stream), "predict");
     h->has_prior = true;
     return PRISM_OK;
 }
@@ -489,9 +499,9 @@ prism_status prism_render(prism_handle h, const double* pose7, float* depth, flo
         PhaseTimer t(h, PH_RENDER);
         PoseArg pa{};
         normalise_pose(pose7, pa.p);
-        CK(h, launch_prep(h->dstate, PREP_AUX_C2W, pa, h->stream), "pose matrices");
-        CK(h, launch_render(h->kp, h->dstate->aux, h->map, depth, rgb, mask, hitk, h->dstats, nullptr, nullptr,
-                            h->stream),
+        LAUNCH(h, launch_prep(h->dstate, PREP_AUX_C2W, pa, h->stream), "pose matrices");
+        LAUNCH(h, launch_render(h->kp, h->dstate->aux, h->map, depth, rgb, mask, hitk, h->dstats, nullptr, nullptr,
+                            h->detail, h->stream),
            "render");
         return PRISM_OK;
     }
@@ -547,14 +557,14 @@ prism_status prism_map_load(prism_handle h, const float* occ, const float* rgb, 
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     if (!occ || !rgb || !var_occ || !var_rgb) return fail(h, PRISM_EINVAL, "a map array is NULL");
     DeviceGuard g(h->device);
-    CK(h, launch_map_load(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map load");
+    LAUNCH(h, launch_map_load(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map load");
     return PRISM_OK;
 }
 
 prism_status prism_map_store(prism_handle h, float* occ, float* rgb, float* var_occ, float* var_rgb) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     DeviceGuard g(h->device);
-    CK(h, launch_map_store(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map store");
+    LAUNCH(h, launch_map_store(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map store");
     return PRISM_OK;
 }
 
@@ -571,8 +581,8 @@ prism_status prism_anchor_load(prism_handle h, const double* pose7, const float*
     CK(h, cudaMemcpyAsync(h->dstate->anchor_pose, pn, 7 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
        "anchor pose");
     PhaseTimer t(h, PH_ANCHOR);
-    CK(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
-    CK(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
+    LAUNCH(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
+    LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
     h->has_anchor = true;
     return PRISM_OK;
 }
@@ -584,11 +594,11 @@ prism_status prism_normal_equations(prism_handle h, const double* pose7, const f
     if (!finite_pose(pose7)) return fail(h, PRISM_EINVAL, "pose is not finite");
     if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
     DeviceGuard g(h->device);
-    CK(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
     PoseArg pa{};
     normalise_pose(pose7, pa.p);
-    CK(h, launch_prep(h->dstate, PREP_AUX_REL, pa, h->stream), "pose matrices");
-    CK(h, launch_track(h->kp, TRACK_EXPORT, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+    LAUNCH(h, launch_prep(h->dstate, PREP_AUX_REL, pa, h->stream), "pose matrices");
+    LAUNCH(h, launch_track(h->kp, TRACK_EXPORT, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                        h->counter, h->max_blocks, h->dstats, h->stream),
        "normal equations");
     CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
@@ -609,12 +619,20 @@ prism_status prism_get_stats(prism_handle h, prism_stats* out) {
     out->fuse_updates = (int64_t)s.fuse_updates;
     out->fuse_colour_updates = (int64_t)s.fuse_colour_updates;
     out->track_pixels = (int64_t)s.track_pixels;
+    out->render_unique_corners = (int64_t)s.render_unique_corners;
+    out->kernel_launches = h->launches;
     return PRISM_OK;
 }
 
 prism_status prism_set_timing(prism_handle h, int32_t enabled) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     h->timing = enabled != 0;
+    return PRISM_OK;
+}
+
+prism_status prism_set_detail_counters(prism_handle h, int32_t enabled) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    h->detail = enabled != 0;
     return PRISM_OK;
 }
 

@@ -67,6 +67,7 @@ enum : int { FLAG_GN_NOTPD = 1, FLAG_LAPLACE_NOTPD = 2, FLAG_PRIOR_NOTPD = 4 };
 // Work counters (device, accumulated with warp-aggregated atomics).
 struct DevStats {
     unsigned long long render_rays, render_samples, render_hits;
+    unsigned long long render_unique_corners;   // only with detail counters on
     unsigned long long fuse_updates, fuse_colour_updates, track_pixels;
 };
 

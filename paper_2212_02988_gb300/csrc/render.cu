@@ -58,7 +58,7 @@ __device__ __forceinline__ Sample cell_of(const KParams& P, float gx, float gy, 
 
 }  // namespace
 
-template <bool BF16>
+template <bool BF16, bool DETAIL>
 __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
                                                 float* __restrict__ depth, float* __restrict__ rgb,
                                                 uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
     const bool active = u < P.W && v < P.H;
 
     int nsamp = 0, hk = 0;
+    unsigned int uniq = 0;   // distinct occupancy corners of this ray (DETAIL only)
     float out_d = 0.0f, out_r = 0.0f, out_g = 0.0f, out_b = 0.0f;
     if (active) {
         // ray set-up (FP32 recipe)
@@ -98,11 +99,18 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
         int k = 1;
         bool hit = false;
         Sample cur;
+        float pfx = -2.0f, pfy = -2.0f, pfz = -2.0f;
         for (; k <= P.kmax; ++k) {
             const float d = __fmul_rn((float)k, P.eps32);
             const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
             if (!(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
             ++nsamp;
+            if (DETAIL) {   // consecutive cells share 8 >> (axes changed) corners (steps below one voxel)
+                const float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
+                const int ch = (flx != pfx) + (fly != pfy) + (flz != pfz);
+                uniq += nsamp == 1 ? 8u : 8u - (8u >> ch);
+                pfx = flx; pfy = fly; pfz = flz;
+            }
             cur = cell_of(P, gx, gy, gz);
             f = trilinear<BF16>(M.occ, cur.base, P.px, P.pxy, cur.fx, cur.fy, cur.fz);
             if (f > P.tau32) { hit = true; break; }
@@ -138,6 +146,10 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
         unsigned long long s = warp_sum_u64((unsigned long long)nsamp);
         unsigned int hits = __popc(__ballot_sync(0xffffffffu, hk >= 2));
         unsigned int rays = __popc(__ballot_sync(0xffffffffu, active));
+        if (DETAIL) {
+            const unsigned long long q = warp_sum_u64((unsigned long long)uniq);
+            if (lane == 0) atomicAdd(&stats->render_unique_corners, q);
+        }
         if (lane == 0) {
             atomicAdd(&stats->render_samples, s);
             atomicAdd(&stats->render_hits, (unsigned long long)hits);
@@ -205,12 +217,15 @@ __global__ void k_anchor_pack(KParams P, const float* __restrict__ depth, const 
 // ----------------------------------------------------------------- launchers
 cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& M, float* depth, float* rgb,
                           uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src,
-                          double* anchor_dst, cudaStream_t s) {
+                          double* anchor_dst, bool detail, cudaStream_t s) {
     dim3 grid((P.W + 15) / 16, (P.H + 7) / 8), block(128);
-    if (P.bf16)
-        k_render<true><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
-    else
-        k_render<false><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+    if (P.bf16) {
+        if (detail) k_render<true, true><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+        else k_render<true, false><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+    } else {
+        if (detail) k_render<false, true><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+        else k_render<false, false><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+    }
     return cudaGetLastError();
 }
 

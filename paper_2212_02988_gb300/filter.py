@@ -196,6 +196,9 @@ class Filter:
     def set_timing(self, enabled: bool = True):
         self._check(self.L.prism_set_timing(self.h, int(enabled)), self.h)
 
+    def set_detail_counters(self, enabled: bool = True):
+        self._check(self.L.prism_set_detail_counters(self.h, int(enabled)), self.h)
+
     def timing(self) -> dict:
         t = Timing()
         self._check(self.L.prism_get_timing(self.h, C.byref(t)), self.h)

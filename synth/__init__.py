@@ -28,14 +28,16 @@ class Sequence:
     """All seeded inputs of one workload.  Frame i is taken at time i / rate.
 
     The trajectory, scene and IMU stream depend only on the workload and the
-    seed; `n_frames` only bounds which frames the caller intends to use."""
+    seed; `n_frames` only bounds which frames the caller intends to use (a
+    value above the workload's own frame count extends the trajectory, which
+    then differs from the default one)."""
 
     def __init__(self, w: Workload, n_frames: int | None = None, seed: int | None = None):
         self.w = w
         self.seed = w.seed if seed is None else seed
-        self.n_frames = w.n_frames if n_frames is None else min(n_frames, w.n_frames)
+        self.n_frames = w.n_frames if n_frames is None else n_frames
         rng = np.random.default_rng(self.seed)
-        duration = (w.n_frames + 1) / w.rate
+        duration = (max(w.n_frames, self.n_frames) + 1) / w.rate
         margin = 3.0 * w.voxel
         self.traj = make_trajectory(w, rng, duration, margin)
         keep = self.traj.position(np.linspace(0, duration, max(200, int(duration * 40))))
