@@ -211,6 +211,37 @@ prism_status prism_anchor_load(prism_handle h, const double* pose7, const float*
 prism_status prism_normal_equations(prism_handle h, const double* pose7, const float* depth,
                                     const float* rgb, double* out);
 
+/* ---- Allocation-free evaluation of the normal equations ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory (code that must not call cudaMalloc, or a
+ * process whose device footprint is fixed after start-up).  It computes
+ * what prism_anchor_load followed by prism_normal_equations computes, without
+ * a handle: anchor_pose7 and pose7 are HOST poses, anchor_depth / anchor_rgb
+ * (the rendered anchor) and depth / rgb (the observation) are DEVICE pointers
+ * in the image layout, `stream` a cudaStream_t (NULL = legacy default), out
+ * a HOST array of 80 doubles laid out as for prism_normal_equations.  Only
+ * cfg's image size, intrinsics, gates, scales, floors and disc are used.
+ *
+ * All scratch (packed anchor, validity masks, per-block partial sums, ticket
+ * counter, device state) lives in one static device array of
+ * PRISM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * until the process exits; the call allocates and frees nothing.  Images
+ * larger than PRISM_NOALLOC_MAX_PIXELS are rejected with PRISM_EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before any stream capture.  Calls share the array and it keeps
+ * the last call's contents: two calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and give wrong results; serialise them.
+ * The call synchronises `stream` before returning.  Errors: as elsewhere,
+ * with the message in prism_noalloc_last_error(). */
+#define PRISM_NOALLOC_MAX_PIXELS (640 * 480)
+#define PRISM_NOALLOC_SCRATCH_BYTES (10u * 1024u * 1024u + 256u * 1024u)
+prism_status prism_normal_equations_noalloc(const prism_config* cfg, const double* anchor_pose7,
+                                            const float* anchor_depth, const float* anchor_rgb,
+                                            const double* pose7, const float* depth, const float* rgb,
+                                            void* stream, double* out);
+const char* prism_noalloc_last_error(void);
+
 /* Work counters and per-phase timing.  Detail counters (off by default)
  * make the render also count the distinct trilinear corners each ray
  * reads, at a few instructions per sample. */

@@ -3,6 +3,6 @@
 The compute path is libprism.so (CUDA kernels behind the C ABI of
 include/prism.h); this package is its thin Python binding.
 """
-from .filter import Filter, PrismError, config, make_state, state_arrays
+from .filter import Filter, PrismError, config, make_state, normal_equations_noalloc, state_arrays
 
-__all__ = ["Filter", "PrismError", "config", "make_state", "state_arrays"]
+__all__ = ["Filter", "PrismError", "config", "make_state", "normal_equations_noalloc", "state_arrays"]

@@ -72,6 +72,27 @@ def _hptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def normal_equations_noalloc(cfg: Config, anchor_pose7, anchor_depth, anchor_rgb, pose7, depth, rgb,
+                             stream: torch.cuda.Stream | None = None) -> dict:
+    """prism_normal_equations_noalloc: the normal equations of one pose with
+    no device allocation (scratch in the library's static device array; see
+    include/prism.h).  Device arrays are CUDA tensors on the current device."""
+    L = _lib.load()
+    H, W = cfg.height, cfg.width
+    ap = np.ascontiguousarray(anchor_pose7, dtype=np.float64)
+    p = np.ascontiguousarray(pose7, dtype=np.float64)
+    out = np.zeros(80)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = L.prism_normal_equations_noalloc(C.byref(cfg), _hptr(ap), _dptr(anchor_depth, (H, W), name="anchor_depth"),
+                                          _dptr(anchor_rgb, (H, W, 3), name="anchor_rgb"), _hptr(p),
+                                          _dptr(depth, (H, W), name="depth"), _dptr(rgb, (H, W, 3), name="rgb"),
+                                          C.c_void_p(s.cuda_stream), _hptr(out))
+    if st != _lib.OK:
+        raise PrismError(st, L.prism_noalloc_last_error().decode())
+    return {"H": out[:36].reshape(6, 6), "g": out[36:42], "Ht": out[42:78].reshape(6, 6),
+            "cost": out[78], "count": out[79]}
+
+
 class Filter:
     """One PRISM filter (map + state + anchor) on one CUDA device."""
 
