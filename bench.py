@@ -220,6 +220,30 @@ def run_ours(args, rank, world, local_rank):
     st1 = F.stats()
     tm = F.timing()
     elapsed, frames = combine_over_ranks(total_ms / 1000.0, float(K))
+    # render adjoint (config with the differentiation path): timed separately,
+    # at the final state's pose, with resident upstream gradients
+    adj = None
+    n_adj = min(K, 50)
+    if n_adj > 0:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        gD = torch.randn((w.height, w.width), generator=gen, device=dev)
+        gC = torch.randn((w.height, w.width, 3), generator=gen, device=dev)
+        go = torch.zeros(maps[0].shape, device=dev)
+        gr = torch.zeros(maps[1].shape, device=dev)
+        from paper_2212_02988_gb300 import state_arrays
+        pose_last = state_arrays(F.get_state())["pose"]
+        F.render_backward(pose_last, gD, gC, go, gr)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(n_adj):   # device-side gradients only: no host read-back per call
+            F.render_backward_async(pose_last, gD, gC, go, gr)
+        a1.record()
+        torch.cuda.synchronize()
+        adj_ms = a0.elapsed_time(a1) / n_adj
+        adj = {"ms_per_call": adj_ms, "calls": n_adj, "mrays_per_s": w.width * w.height / (adj_ms * 1e-3) / 1e6,
+               "note": "prism_render_backward (pose + per-voxel gradients, FP32 atomics), not part of the step"}
     F.close()
 
     d_st = {k: st1[k] - st0[k] for k in st1}
@@ -306,6 +330,7 @@ def run_ours(args, rank, world, local_rank):
                               "frac": loc_bytes / (loc_ms * 1e-3) / 1e9 / peak, "bytes_per_step": loc_bytes,
                               "ms_per_step": loc_ms},
         "e2e": e2e,
+        "render_adjoint": adj,
         "gpu_launches": int(d_st["kernel_launches"]),
         "clocks": clocks,
     }

@@ -191,7 +191,8 @@ prism_status prism_set_state(prism_handle h, const prism_state* s);
 /* Load / store the whole map in the linear caller layout (see Conventions):
  * occ (N floats), rgb (3N floats), var_occ (N floats), var_rgb (N floats),
  * N = nx*ny*nz; DEVICE pointers; for storage BF16 the values are rounded
- * to nearest-even on load.  prism_map_store may be given NULL for any array. */
+ * to nearest-even on load.  Either call may be given NULL for any array,
+ * which is then left unchanged (load) or not written (store). */
 prism_status prism_map_load(prism_handle h, const float* occ, const float* rgb,
                             const float* var_occ, const float* var_rgb);
 prism_status prism_map_store(prism_handle h, float* occ, float* rgb, float* var_occ, float* var_rgb);
@@ -241,6 +242,22 @@ prism_status prism_normal_equations_noalloc(const prism_config* cfg, const doubl
                                             const double* pose7, const float* depth, const float* rgb,
                                             void* stream, double* out);
 const char* prism_noalloc_last_error(void);
+
+/* Adjoint of prism_render at pose7 (App. B: the emission is
+ * differentiable): gradients of L = sum grad_depth * depth + sum grad_rgb .
+ * rgb for the render of the current map at pose7.  grad_depth (H x W) and
+ * grad_rgb (H x W x 3): DEVICE pointers, either may be NULL (zero).  Each
+ * ray is re-marched (nothing is stored by the forward) and the hit sample
+ * held fixed.  grad_occ (N floats) and grad_rgb_map (3N floats): DEVICE
+ * pointers in the linear map layout, ACCUMULATED into (zero them first;
+ * atomics, so the summation order varies), either may be NULL.
+ * grad_pose6: HOST, 6 doubles (dL/dt, dL/dtheta for the world-frame left
+ * perturbation t' = t + dt, R' = Exp(dtheta) R) or NULL; grad_pose7: HOST,
+ * 7 doubles, the same gradient with respect to (t, q) of pose7 as given
+ * (before normalisation), or NULL.  Either host output synchronises. */
+prism_status prism_render_backward(prism_handle h, const double* pose7, const float* grad_depth,
+                                   const float* grad_rgb, float* grad_occ, float* grad_rgb_map,
+                                   double* grad_pose6, double* grad_pose7);
 
 /* Work counters and per-phase timing.  Detail counters (off by default)
  * make the render also count the distinct trilinear corners each ray

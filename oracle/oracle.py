@@ -77,6 +77,7 @@ def lib():
             dp, fp, u8p, i32p, i64p = (P(C.c_double), P(C.c_float), P(C.c_uint8), P(C.c_int32),
                                        P(C.c_int64))
             L.or_render.argtypes = [P(Params), dp, dp, dp, i32p, C.c_int32, dp, dp, u8p, i32p, i64p]
+            L.or_render_backward.argtypes = [P(Params), dp, dp, dp, dp, dp, dp, dp, dp]
             L.or_depth_mask.argtypes = [P(Params), fp, u8p]
             L.or_anchor_normals.argtypes = [P(Params), fp, u8p, dp, fp, u8p]
             L.or_residuals.argtypes = [P(Params), dp, fp, fp, dp, fp, fp, dp, dp, i32p, u8p]
@@ -163,6 +164,22 @@ def render(p: Params, occ, rgb, pose7, pix=None):
         out = {k: (v.reshape((p.height, p.width) + v.shape[1:]) if isinstance(v, np.ndarray) else v)
                for k, v in out.items()}
     return out
+
+
+def render_backward(p: Params, occ, rgb, pose7, g_depth=None, g_rgb=None):
+    """Gradients of sum(g_depth * depth) + sum(g_rgb * rgb) for the render at
+    pose7: dict of occ (like occ), rgb (like rgb), pose (6: d/dt, d/dtheta for
+    a world-frame left perturbation)."""
+    occ, rgb, pose = _f64(occ), _f64(rgb), _f64(pose7)
+    gd = None if g_depth is None else _f64(g_depth)
+    gc = None if g_rgb is None else _f64(g_rgb)
+    go = np.zeros_like(occ)
+    gr = np.zeros_like(rgb)
+    gp = np.zeros(6)
+    lib().or_render_backward(C.byref(p), _p(occ, C.c_double), _p(rgb, C.c_double), _p(pose, C.c_double),
+                             _p(gd, C.c_double), _p(gc, C.c_double), _p(go, C.c_double), _p(gr, C.c_double),
+                             _p(gp, C.c_double))
+    return {"occ": go, "rgb": gr, "pose": gp}
 
 
 def depth_mask(p: Params, depth):

@@ -11,6 +11,9 @@
  *   or_render            App. B, ray points p = c + d r, d in {eps, 2 eps, ...};
  *                        trilinear field f_M; first point with f_occ > tau;
  *                        d* = alpha d_k + (1 - alpha) d_{k-1}; colour "analogously".
+ *   or_render_backward   its adjoint (App. B: the emission is differentiable):
+ *                        gradients of a weighted sum of the rendered depth and
+ *                        colour with respect to the map means and the pose.
  *   or_depth_mask        App. F.3, ignore invalid and strongly discontinuous depth.
  *   or_anchor_normals    App. E.3, "normal of the rendered depth image".
  *   or_residuals         App. E.3, Eq. pointtoplanelaplace: point-to-plane and
@@ -351,6 +354,129 @@ int or_render(const or_params* P, const double* occ, const double* rgb, const do
         if (hitk) hitk[n] = hk;
     }
     if (n_samples) *n_samples = nsamp;
+    return 0;
+}
+
+/* ============================================================ render adjoint */
+/* Gradient of  L = sum_pixels gD * depth + sum_pixels,c gC_c * rgb_c  with
+ * respect to the occupancy and colour means and to a world-frame
+ * perturbation of the camera pose (t' = t + dt, R' = Exp(dtheta) R), for
+ * the render of App. B.  With the hit between samples k-1 and k:
+ *   alpha = (tau - f0) / (f1 - f0),  depth = (alpha d_k + (1 - alpha) d_{k-1}) / |dir_c|,
+ *   rgb_c = alpha C_c(p_k) + (1 - alpha) C_c(p_{k-1}),
+ *   dL/dalpha = gD eps / |dir_c| + sum_c gC_c (C_c(p_k) - C_c(p_{k-1})),
+ *   dL/df0 = dL/dalpha (alpha - 1) / (f1 - f0),  dL/df1 = -dL/dalpha alpha / (f1 - f0);
+ * each trilinear value passes its gradient to its 8 corners with the
+ * trilinear weights, and to its sample position p with grad_p = grad_g / vs;
+ * p_k = c + d_k r gives dL/dt += gp_k and dL/dtheta += d_k (r x gp_k).  The
+ * hit index is held fixed (it is piecewise constant in the inputs). */
+static void trilinear64_grad(const or_params* P, const double* m, int stride, int ch, const cell_t* c,
+                             double g[3]) {
+    double fx = c->fx, fy = c->fy, fz = c->fz;
+    int xs[2] = {c->x0, c->x1}, ys[2] = {c->y0, c->y1}, zs[2] = {c->z0, c->z1};
+    g[0] = g[1] = g[2] = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e) {
+                double v = m[vidx(P, xs[a], ys[b], zs[e]) * stride + ch];
+                double wx = a ? fx : 1.0 - fx, wy = b ? fy : 1.0 - fy, wz = e ? fz : 1.0 - fz;
+                g[0] += (a ? 1.0 : -1.0) * wy * wz * v;
+                g[1] += wx * (b ? 1.0 : -1.0) * wz * v;
+                g[2] += wx * wy * (e ? 1.0 : -1.0) * v;
+            }
+}
+
+static void scatter64(const or_params* P, double* gm, int stride, int ch, const cell_t* c, double gval) {
+    double fx = c->fx, fy = c->fy, fz = c->fz;
+    int xs[2] = {c->x0, c->x1}, ys[2] = {c->y0, c->y1}, zs[2] = {c->z0, c->z1};
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e) {
+                double w = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy) * (e ? fz : 1.0 - fz);
+                gm[vidx(P, xs[a], ys[b], zs[e]) * stride + ch] += gval * w;
+            }
+}
+
+int or_render_backward(const or_params* P, const double* occ, const double* rgb, const double pose_in[7],
+                       const double* gD, const double* gC, double* g_occ, double* g_rgb, double g_pose[6]) {
+    double R[9], pose[7];
+    normalise_pose(pose_in, pose);
+    quat_to_R(pose + 3, R);
+    float R32[9], c32[3], o32[3];
+    for (int i = 0; i < 9; ++i) R32[i] = (float)R[i];
+    for (int a = 0; a < 3; ++a) { c32[a] = (float)pose[a]; o32[a] = (float)P->origin[a]; }
+    float inv_vs = (float)(1.0 / P->voxel), eps32 = (float)P->eps, tau32 = (float)P->tau;
+    float cx = (float)P->cx, cy = (float)P->cy;
+    float ifx = (float)(1.0 / P->fx), ify = (float)(1.0 / P->fy);
+    long kmax = P->max_depth > 0 ? (long)floor(P->max_depth / P->eps) : 0x7fffffffL;
+    for (int i = 0; i < 6; ++i) g_pose[i] = 0.0;
+    for (int p = 0; p < P->width * P->height; ++p) {
+        int u = p % P->width, v = p / P->width;
+        double gd = gD ? gD[p] : 0.0, gc[3] = {0, 0, 0};
+        if (gC) for (int c = 0; c < 3; ++c) gc[c] = gC[3 * p + c];
+        if (gd == 0.0 && gc[0] == 0.0 && gc[1] == 0.0 && gc[2] == 0.0) continue;
+        /* march (same decisions as or_render) */
+        float dx = ((float)u - cx) * ifx, dy = ((float)v - cy) * ify;
+        float w[3], cg[3], rg[3];
+        for (int a = 0; a < 3; ++a) w[a] = fmaf(R32[3 * a], dx, fmaf(R32[3 * a + 1], dy, R32[3 * a + 2]));
+        float inv_n = 1.0f / sqrtf(fmaf(w[0], w[0], fmaf(w[1], w[1], w[2] * w[2])));
+        for (int a = 0; a < 3; ++a) {
+            cg[a] = fmaf(c32[a] - o32[a], inv_vs, -0.5f);
+            rg[a] = (w[a] * inv_n) * inv_vs;
+        }
+        cell_t prev, cur;
+        int k = 1, hit = 0;
+        for (; k <= kmax; ++k) {
+            if (!sample_cell(P, cg, rg, eps32, k, &cur)) break;
+            if (trilinear32(P, occ, 1, 0, &cur) > tau32) { hit = 1; break; }
+            prev = cur;
+        }
+        if (!hit || k < 2) continue;
+        /* values and gradients in FP64 */
+        double f0 = trilinear64(P, occ, 1, 0, &prev), f1 = trilinear64(P, occ, 1, 0, &cur);
+        double alpha = (P->tau - f0) / (f1 - f0);
+        double dcx = (u - P->cx) / P->fx, dcy = (v - P->cy) / P->fy;
+        double ndir = sqrt(dcx * dcx + dcy * dcy + 1.0);
+        double C0[3], C1[3];
+        for (int c = 0; c < 3; ++c) {
+            C0[c] = trilinear64(P, rgb, 3, c, &prev);
+            C1[c] = trilinear64(P, rgb, 3, c, &cur);
+        }
+        double gA = gd * P->eps / ndir;
+        for (int c = 0; c < 3; ++c) gA += gc[c] * (C1[c] - C0[c]);
+        double gf0 = gA * (alpha - 1.0) / (f1 - f0), gf1 = -gA * alpha / (f1 - f0);
+        if (g_occ) {
+            scatter64(P, g_occ, 1, 0, &prev, gf0);
+            scatter64(P, g_occ, 1, 0, &cur, gf1);
+        }
+        if (g_rgb)
+            for (int c = 0; c < 3; ++c) {
+                scatter64(P, g_rgb, 3, c, &prev, gc[c] * (1.0 - alpha));
+                scatter64(P, g_rgb, 3, c, &cur, gc[c] * alpha);
+            }
+        /* pose: positions of samples k-1 and k */
+        double dirw[3], r[3];
+        double dc[3] = {dcx, dcy, 1.0};
+        mat3_vec(R, dc, dirw);
+        for (int a = 0; a < 3; ++a) r[a] = dirw[a] / ndir;
+        const cell_t* cells[2] = {&prev, &cur};
+        double gfs[2] = {gf0, gf1}, wa[2] = {1.0 - alpha, alpha}, ds[2] = {(k - 1) * P->eps, k * P->eps};
+        for (int s = 0; s < 2; ++s) {
+            double gp[3], tmp[3], rx[3];
+            trilinear64_grad(P, occ, 1, 0, cells[s], gp);
+            for (int a = 0; a < 3; ++a) gp[a] *= gfs[s];
+            for (int c = 0; c < 3; ++c) {
+                trilinear64_grad(P, rgb, 3, c, cells[s], tmp);
+                for (int a = 0; a < 3; ++a) gp[a] += gc[c] * wa[s] * tmp[a];
+            }
+            for (int a = 0; a < 3; ++a) gp[a] /= P->voxel;
+            cross3(r, gp, rx);
+            for (int a = 0; a < 3; ++a) {
+                g_pose[a] += gp[a];
+                g_pose[3 + a] += ds[s] * rx[a];
+            }
+        }
+    }
     return 0;
 }
 

@@ -78,6 +78,8 @@ int or_render(const or_params* P, const double* occ, const double* rgb,
               const double pose[7], const int32_t* pix, int32_t npix,
               double* depth, double* rgb_out, uint8_t* mask, int32_t* hitk,
               int64_t* n_samples);
+int or_render_backward(const or_params* P, const double* occ, const double* rgb, const double pose[7],
+                       const double* gD, const double* gC, double* g_occ, double* g_rgb, double g_pose[6]);
 void or_depth_mask(const or_params* P, const float* depth, uint8_t* mask);
 void or_anchor_normals(const or_params* P, const float* depth, const uint8_t* mask,
                        double* n64, float* n32, uint8_t* nvalid);

@@ -93,6 +93,7 @@ def load() -> C.CDLL:
         "prism_device_bytes": (C.c_int64, [H]),
         "prism_last_error": (C.c_char_p, [H]),
         "prism_status_string": (C.c_char_p, [C.c_int32]),
+        "prism_render_backward": (st, [H, dp, fp, fp, fp, fp, dp, dp]),
         "prism_normal_equations_noalloc": (st, [P(Config), dp, fp, fp, dp, fp, fp, vp, dp]),
         "prism_noalloc_last_error": (C.c_char_p, []),
     }

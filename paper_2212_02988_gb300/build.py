@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
-SOURCES = ["render.cu", "track.cu", "state.cu", "fuse.cu", "mapio.cu", "prism_abi.cu", "noalloc.cu"]
+SOURCES = ["render.cu", "track.cu", "state.cu", "fuse.cu", "mapio.cu", "prism_abi.cu", "noalloc.cu",
+           "render_bwd.cu"]
 HEADERS = ["prism_dev.cuh", "linalg64.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",

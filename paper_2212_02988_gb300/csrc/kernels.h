@@ -76,4 +76,10 @@ cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* o
 cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, float* rgb, float* var_occ,
                              float* var_rgb, cudaStream_t s);
 
+// render_bwd.cu — adjoint of the render at the pose whose matrices are in
+// `mats` (DevState::aux); adds the pose gradient to dev->grad_pose.
+cudaError_t launch_render_bwd(const KParams& P, const float* mats, const MapPlanes& M, const float* grad_depth,
+                              const float* grad_rgb, float* grad_occ, float* grad_rgb_map, DevState* dev,
+                              cudaStream_t s);
+
 }  // namespace prism

@@ -555,9 +555,46 @@ prism_status prism_set_state(prism_handle h, const prism_state* s) {
 prism_status prism_map_load(prism_handle h, const float* occ, const float* rgb, const float* var_occ,
                             const float* var_rgb) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
-    if (!occ || !rgb || !var_occ || !var_rgb) return fail(h, PRISM_EINVAL, "a map array is NULL");
     DeviceGuard g(h->device);
     LAUNCH(h, launch_map_load(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map load");
+    return PRISM_OK;
+}
+
+prism_status prism_render_backward(prism_handle h, const double* pose7, const float* grad_depth,
+                                   const float* grad_rgb, float* grad_occ, float* grad_rgb_map,
+                                   double* grad_pose6, double* grad_pose7) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!pose7) return fail(h, PRISM_EINVAL, "pose is NULL");
+    if (!finite_pose(pose7)) return fail(h, PRISM_EINVAL, "pose is not finite or has a zero quaternion");
+    DeviceGuard g(h->device);
+    PoseArg pa{};
+    normalise_pose(pose7, pa.p);
+    LAUNCH(h, launch_prep(h->dstate, PREP_AUX_C2W, pa, h->stream), "pose matrices");
+    CK(h, cudaMemsetAsync(h->dstate->grad_pose, 0, 6 * sizeof(double), h->stream), "clear pose gradient");
+    LAUNCH(h, launch_render_bwd(h->kp, h->dstate->aux, h->map, grad_depth, grad_rgb, grad_occ, grad_rgb_map,
+                                h->dstate, h->stream),
+           "render adjoint");
+    if (!grad_pose6 && !grad_pose7) return PRISM_OK;
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    double g6[6];
+    CK(h, cudaMemcpy(g6, h->dstate->grad_pose, sizeof(g6), cudaMemcpyDeviceToHost), "read pose gradient");
+    if (grad_pose6) std::memcpy(grad_pose6, g6, sizeof(g6));
+    if (grad_pose7) {
+        // d/dt as is.  For q (given unnormalised, |q| = n, q^ = q / n), a change dq
+        // rotates by dtheta = 2 vec(dq^ (x) conj(q^)) with dq^ = (dq - q^ (q^ . dq)) / n,
+        // so dL/dq = G / n with G = 2 (-g . q^_v, q^_w g - q^_v x g); G . q^ = 0.
+        const double* gt = g6;
+        const double* gth = g6 + 3;
+        const double n = std::sqrt(((pose7[3] * pose7[3] + pose7[4] * pose7[4]) + pose7[5] * pose7[5]) +
+                                   pose7[6] * pose7[6]);
+        const double w = pa.p[3], x = pa.p[4], y = pa.p[5], z = pa.p[6];
+        const double cx = y * gth[2] - z * gth[1], cy = z * gth[0] - x * gth[2], cz = x * gth[1] - y * gth[0];
+        for (int a = 0; a < 3; ++a) grad_pose7[a] = gt[a];
+        grad_pose7[3] = 2.0 * -(gth[0] * x + gth[1] * y + gth[2] * z) / n;
+        grad_pose7[4] = 2.0 * (w * gth[0] - cx) / n;
+        grad_pose7[5] = 2.0 * (w * gth[1] - cy) / n;
+        grad_pose7[6] = 2.0 * (w * gth[2] - cz) / n;
+    }
     return PRISM_OK;
 }
 

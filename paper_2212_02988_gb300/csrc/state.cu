@@ -19,7 +19,7 @@ namespace prism {
 
 __global__ void __launch_bounds__(256) k_predict(KParams P, DevState* dev, const double* __restrict__ imu, int n,
                                                  double dt) {
-    __shared__ double R[9], A[36], B[36], F[144], T1[144], Sig[144], Svp[36], Spv[36], Dm[36], Spp[36];
+    __shared__ double R[9], B[36], F[144], T1[144], Sig[144], Svp[36], Spv[36], Dm[36], Spp[36];
     __shared__ double Rw[9], Jl[9], vnew[6], Lch[36], rdg[6];
     __shared__ int ok;
     __shared__ double sums[8];   // mean t, acc (3), gyro (3), then t_end
@@ -108,7 +108,6 @@ __global__ void __launch_bounds__(256) k_predict(KParams P, DevState* dev, const
         double f = 0.0;
         if (i < 6 && j < 6) {
             f = (i < 3 && j < 3) ? (i == j ? 1.0 : 0.0) : ((i >= 3 && j >= 3) ? Rw[3 * (i - 3) + j - 3] : 0.0);
-            A[6 * i + j] = f;
         } else if (i < 6 && j >= 6) {
             int jj = j - 6;
             f = (i < 3 && jj < 3) ? (i == jj ? dt : 0.0)

@@ -179,12 +179,37 @@ class Filter:
     def set_state(self, s: State):
         self._check(self.L.prism_set_state(self.h, C.byref(s)), self.h)
 
-    def map_load(self, occ, rgb, var_occ, var_rgb):
+    def map_load(self, occ, rgb, var_occ=None, var_rgb=None):
+        """Load map arrays (None leaves that part of the map unchanged)."""
         N = self.N
-        self._check(self.L.prism_map_load(self.h, _dptr(occ.reshape(-1), (N,), name="occ"),
-                                          _dptr(rgb.reshape(-1), (3 * N,), name="rgb"),
-                                          _dptr(var_occ.reshape(-1), (N,), name="var_occ"),
-                                          _dptr(var_rgb.reshape(-1), (N,), name="var_rgb")), self.h)
+        f = lambda a, n, name: None if a is None else _dptr(a.reshape(-1), (n,), name=name)
+        self._check(self.L.prism_map_load(self.h, f(occ, N, "occ"), f(rgb, 3 * N, "rgb"),
+                                          f(var_occ, N, "var_occ"), f(var_rgb, N, "var_rgb")), self.h)
+
+    def render_backward(self, pose7, grad_depth=None, grad_rgb=None, grad_occ=None, grad_rgb_map=None):
+        """Adjoint of render(pose7); map gradients are accumulated into the given
+        tensors (shapes of the map arrays).  Returns (grad_pose6, grad_pose7)."""
+        p = np.ascontiguousarray(pose7, dtype=np.float64)
+        g6, g7 = np.zeros(6), np.zeros(7)
+        N = self.N
+        self._check(self.L.prism_render_backward(
+            self.h, _hptr(p), _dptr(grad_depth, (self.H, self.W), name="grad_depth"),
+            _dptr(grad_rgb, (self.H, self.W, 3), name="grad_rgb"),
+            None if grad_occ is None else _dptr(grad_occ.view(-1), (N,), name="grad_occ"),
+            None if grad_rgb_map is None else _dptr(grad_rgb_map.view(-1), (3 * N,), name="grad_rgb_map"),
+            _hptr(g6), _hptr(g7)), self.h)
+        return g6, g7
+
+    def render_backward_async(self, pose7, grad_depth=None, grad_rgb=None, grad_occ=None, grad_rgb_map=None):
+        """render_backward without the host pose gradient (no synchronisation)."""
+        p = np.ascontiguousarray(pose7, dtype=np.float64)
+        N = self.N
+        self._check(self.L.prism_render_backward(
+            self.h, _hptr(p), _dptr(grad_depth, (self.H, self.W), name="grad_depth"),
+            _dptr(grad_rgb, (self.H, self.W, 3), name="grad_rgb"),
+            None if grad_occ is None else _dptr(grad_occ.view(-1), (N,), name="grad_occ"),
+            None if grad_rgb_map is None else _dptr(grad_rgb_map.view(-1), (3 * N,), name="grad_rgb_map"),
+            None, None), self.h)
 
     def map_store(self) -> dict:
         dev = torch.device("cuda", self.device)
