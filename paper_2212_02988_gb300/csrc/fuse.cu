@@ -45,6 +45,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(256) k_fuse(KParams P, MapPlanes M, const float* __restrict__ w2c,
                                               const float* __restrict__ depth, const float* __restrict__ rgb,
                                               const uint8_t* __restrict__ mask, DevStats* __restrict__ stats) {
+    pdl_enter();
     __shared__ float sM[9], sb[3];
     __shared__ int s_skip;
     const uint32_t tile = blockIdx.x;
@@ -156,9 +157,9 @@ cudaError_t launch_fuse(const KParams& P, const MapPlanes& M, const float* w2c, 
                         const float* rgb, const uint8_t* mask, DevStats* stats, cudaStream_t s) {
     const unsigned int tiles = (unsigned int)(P.nbx * P.nby * P.nbz);
     if (P.bf16)
-        k_fuse<true><<<tiles, 256, 0, s>>>(P, M, w2c, depth, rgb, mask, stats);
+        launch_pdl(k_fuse<true>, tiles, 256, s, P, M, w2c, depth, rgb, mask, stats);
     else
-        k_fuse<false><<<tiles, 256, 0, s>>>(P, M, w2c, depth, rgb, mask, stats);
+        launch_pdl(k_fuse<false>, tiles, 256, s, P, M, w2c, depth, rgb, mask, stats);
     return cudaGetLastError();
 }
 

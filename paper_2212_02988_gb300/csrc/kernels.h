@@ -25,7 +25,7 @@ enum PrepKind : int {
     PREP_REL = 3      // rel = Gauss-Newton pose -> anchor camera
 };
 
-// The map planes in brick layout (f32 or bf16 elements).
+// The six map planes (f32 or bf16 elements), each linear with a ghost border.
 struct MapPlanes {
     void* occ;
     void* r;
@@ -52,10 +52,10 @@ enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2 };
 // the per-block partials in a fixed order and runs the mode's FP64 finish.
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
-                         DevState* dev, double* partials, unsigned int* counter, int max_blocks,
+                         DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s);
 int track_grid(const KParams& P, int max_blocks);
-constexpr int TRACK_NV_MAX = 50;   // doubles per block partial
+constexpr int TRACK_NV_MAX = 50;   // FP32 values per block partial
 
 // state.cu — FP64 prediction and GN start; the FP32 matrices of a pose.
 cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt,
@@ -67,8 +67,8 @@ cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream
 cudaError_t launch_fuse(const KParams& P, const MapPlanes& M, const float* w2c, const float* depth,
                         const float* rgb, const uint8_t* mask, DevStats* stats, cudaStream_t s);
 
-// mapio.cu — fill with the prior, and conversion between the linear caller
-// layout and the brick layout.
+// mapio.cu — fill with the prior, and conversion between the caller's dense
+// layout and the padded (ghost-bordered) device layout.
 cudaError_t launch_map_fill(const KParams& P, const MapPlanes& M, float occ, float rgb, float var,
                             cudaStream_t s);
 cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* occ, const float* rgb,

@@ -8,6 +8,7 @@ namespace prism {
 
 template <bool BF16>
 __global__ void k_map_fill(KParams P, MapPlanes M, float occ, float rgb, float var, uint32_t n) {
+    pdl_enter();
     // n = padded elements per plane; ghosts get the same prior values
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         map_store<BF16>(M.occ, i, occ);
@@ -24,6 +25,7 @@ __global__ void k_map_fill(KParams P, MapPlanes M, float occ, float rgb, float v
 template <bool BF16>
 __global__ void k_map_load(KParams P, MapPlanes M, const float* __restrict__ occ, const float* __restrict__ rgb,
                            const float* __restrict__ vo, const float* __restrict__ vr, uint32_t n) {
+    pdl_enter();
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int gx = (int)(e % P.px) - 1, gy = (int)((e / P.px) % P.py) - 1, gz = (int)(e / P.pxy) - 1;
         const int x = min(max(gx, 0), P.nx - 1), y = min(max(gy, 0), P.ny - 1), z = min(max(gz, 0), P.nz - 1);
@@ -42,6 +44,7 @@ __global__ void k_map_load(KParams P, MapPlanes M, const float* __restrict__ occ
 template <bool BF16>
 __global__ void k_map_store(KParams P, MapPlanes M, float* __restrict__ occ, float* __restrict__ rgb,
                             float* __restrict__ vo, float* __restrict__ vr, uint32_t n) {
+    pdl_enter();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x = i % P.nx, y = (i / P.nx) % P.ny, z = i / (P.nx * P.ny);
         const uint32_t b = pad_index(P, x, y, z);
@@ -63,24 +66,24 @@ static unsigned int io_grid(uint32_t n) {
 
 cudaError_t launch_map_fill(const KParams& P, const MapPlanes& M, float occ, float rgb, float var, cudaStream_t s) {
     uint32_t n = P.npad;
-    if (P.bf16) k_map_fill<true><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var, n);
-    else k_map_fill<false><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var, n);
+    if (P.bf16) launch_pdl(k_map_fill<true>, io_grid(n), 256, s, P, M, occ, rgb, var, n);
+    else launch_pdl(k_map_fill<false>, io_grid(n), 256, s, P, M, occ, rgb, var, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* occ, const float* rgb,
                             const float* var_occ, const float* var_rgb, cudaStream_t s) {
     uint32_t n = P.npad;
-    if (P.bf16) k_map_load<true><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
-    else k_map_load<false><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
+    if (P.bf16) launch_pdl(k_map_load<true>, io_grid(n), 256, s, P, M, occ, rgb, var_occ, var_rgb, n);
+    else launch_pdl(k_map_load<false>, io_grid(n), 256, s, P, M, occ, rgb, var_occ, var_rgb, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, float* rgb, float* var_occ,
                              float* var_rgb, cudaStream_t s) {
     uint32_t n = (uint32_t)P.nx * P.ny * P.nz;
-    if (P.bf16) k_map_store<true><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
-    else k_map_store<false><<<io_grid(n), 256, 0, s>>>(P, M, occ, rgb, var_occ, var_rgb, n);
+    if (P.bf16) launch_pdl(k_map_store<true>, io_grid(n), 256, s, P, M, occ, rgb, var_occ, var_rgb, n);
+    else launch_pdl(k_map_store<false>, io_grid(n), 256, s, P, M, occ, rgb, var_occ, var_rgb, n);
     return cudaGetLastError();
 }
 

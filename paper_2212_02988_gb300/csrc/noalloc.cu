@@ -37,7 +37,7 @@ constexpr size_t kPix = PRISM_NOALLOC_MAX_PIXELS;
 constexpr size_t kOffState = 0;
 constexpr size_t kOffCounter = align_up(kOffState + sizeof(DevState));
 constexpr size_t kOffPartials = align_up(kOffCounter + sizeof(unsigned int));
-constexpr size_t kOffA0 = align_up(kOffPartials + sizeof(double) * TRACK_NV_MAX * kMaxBlocks);
+constexpr size_t kOffA0 = align_up(kOffPartials + sizeof(float) * TRACK_NV_MAX * kMaxBlocks);
 constexpr size_t kOffA1 = align_up(kOffA0 + 16 * kPix);
 constexpr size_t kOffAMask = align_up(kOffA1 + 16 * kPix);
 constexpr size_t kOffOMask = align_up(kOffAMask + kPix);
@@ -132,7 +132,7 @@ prism_status prism_normal_equations_noalloc(const prism_config* cfg, const doubl
     fill_params(cfg, P);
     DevState* ds = (DevState*)(base + kOffState);
     unsigned int* counter = (unsigned int*)(base + kOffCounter);
-    double* partials = (double*)(base + kOffPartials);
+    float* partials = (float*)(base + kOffPartials);
     float4* a0 = (float4*)(base + kOffA0);
     float4* a1 = (float4*)(base + kOffA1);
     uint8_t* a_mask = base + kOffAMask;

@@ -41,7 +41,7 @@ struct prism_ctx {
     uint8_t* o_mask = nullptr;
     DevState* dstate = nullptr;
     DevStats* dstats = nullptr;
-    double* partials = nullptr;
+    float* partials = nullptr;
     unsigned int* counter = nullptr;
     int max_blocks = 0;
     double* d_imu = nullptr;
@@ -427,7 +427,7 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
     if (dalloc(h, &h->a_depth, npix * 4) || dalloc(h, &h->a_rgb, npix * 12) || dalloc(h, &h->a_mask, npix) ||
         dalloc(h, &h->a0, npix * 16) || dalloc(h, &h->a1, npix * 16) || dalloc(h, &h->o_mask, npix) ||
         dalloc(h, &h->dstate, sizeof(DevState)) || dalloc(h, &h->dstats, sizeof(DevStats)) ||
-        dalloc(h, &h->partials, (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(double)) ||
+        dalloc(h, &h->partials, (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(float)) ||
         dalloc(h, &h->counter, sizeof(unsigned int)))
         return cleanup(PRISM_ENOMEM, "device allocation failed");
     cudaGetLastError();

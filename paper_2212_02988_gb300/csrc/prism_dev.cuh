@@ -9,7 +9,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace prism {
+
+// ------------------------------------------------ programmatic dependent launch
+// Every kernel of the library starts with pdl_enter(): it waits until the
+// grid before it in the stream has completed and its memory is visible
+// (griddepcontrol.wait; a no-op when launched without the attribute), then
+// lets the next grid be scheduled.  Launched through launch_pdl, a kernel's
+// launch and block scheduling therefore overlap the tail of the kernel before
+// it instead of following its completion.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ----------------------------------------------------------------- parameters
 // Constants every kernel may need, filled once on the host (FP32 copies are

@@ -21,15 +21,28 @@ namespace prism {
 namespace {
 
 // Trilinear value at a cell given by its padded base index and in-cell
-// weights: lerps along x, then y, then z (the FP32 recipe).
-template <bool BF16>
-__device__ __forceinline__ float trilinear(const void* plane, uint32_t base, uint32_t px, uint32_t pxy, float fx,
-                                           float fy, float fz) {
-    const uint32_t b1 = base + px, b2 = base + pxy, b3 = b2 + px;
-    const float v000 = map_load<BF16>(plane, base), v100 = map_load<BF16>(plane, base + 1);
-    const float v010 = map_load<BF16>(plane, b1), v110 = map_load<BF16>(plane, b1 + 1);
-    const float v001 = map_load<BF16>(plane, b2), v101 = map_load<BF16>(plane, b2 + 1);
-    const float v011 = map_load<BF16>(plane, b3), v111 = map_load<BF16>(plane, b3 + 1);
+// weights: lerps along x, then y, then z (the FP32 recipe).  With PX > 0 the
+// plane strides are compile-time constants (cubic grids of PX - 2 voxels a
+// side), so the 8 loads are immediate offsets from one address.
+template <bool BF16, int PX>
+__device__ __forceinline__ float trilinear(const void* plane, uint32_t base, uint32_t px_rt, uint32_t pxy_rt,
+                                           float fx, float fy, float fz) {
+    const uint32_t px = PX > 0 ? (uint32_t)PX : px_rt;
+    const uint32_t pxy = PX > 0 ? (uint32_t)(PX * PX) : pxy_rt;
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if constexpr (BF16) {
+        const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(plane) + base;
+        v000 = __bfloat162float(__ldg(q)); v100 = __bfloat162float(__ldg(q + 1));
+        v010 = __bfloat162float(__ldg(q + px)); v110 = __bfloat162float(__ldg(q + px + 1));
+        v001 = __bfloat162float(__ldg(q + pxy)); v101 = __bfloat162float(__ldg(q + pxy + 1));
+        v011 = __bfloat162float(__ldg(q + pxy + px)); v111 = __bfloat162float(__ldg(q + pxy + px + 1));
+    } else {
+        const float* q = reinterpret_cast<const float*>(plane) + base;
+        v000 = __ldg(q); v100 = __ldg(q + 1);
+        v010 = __ldg(q + px); v110 = __ldg(q + px + 1);
+        v001 = __ldg(q + pxy); v101 = __ldg(q + pxy + 1);
+        v011 = __ldg(q + pxy + px); v111 = __ldg(q + pxy + px + 1);
+    }
     const float c00 = lerp_rn(v000, v100, fx);
     const float c10 = lerp_rn(v010, v110, fx);
     const float c01 = lerp_rn(v001, v101, fx);
@@ -46,35 +59,48 @@ struct Sample {
     float fx, fy, fz;
 };
 
-__device__ __forceinline__ Sample cell_of(const KParams& P, float gx, float gy, float gz) {
-    const float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
+// floor(g) for |g| < 2^22 without a conversion instruction: adding
+// 1.5 * 2^23 with rounding toward -inf leaves floor(g) in the low mantissa
+// bits (the sum's ulp is 1), and subtracting it back is exact.
+constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr uint32_t kFloorMagicBits = 0x4B400000u;
+
+__device__ __forceinline__ Sample cell_of(uint32_t px, uint32_t pxy, float gx, float gy, float gz) {
+    const float tx = __fadd_rd(gx, kFloorMagic), ty = __fadd_rd(gy, kFloorMagic), tz = __fadd_rd(gz, kFloorMagic);
     Sample s;
-    s.fx = __fsub_rn(gx, flx);
-    s.fy = __fsub_rn(gy, fly);
-    s.fz = __fsub_rn(gz, flz);
-    s.base = pad_index(P, (int)flx, (int)fly, (int)flz);
+    s.fx = __fsub_rn(gx, __fsub_rn(tx, kFloorMagic));
+    s.fy = __fsub_rn(gy, __fsub_rn(ty, kFloorMagic));
+    s.fz = __fsub_rn(gz, __fsub_rn(tz, kFloorMagic));
+    // (x0 + 1) + px ((y0 + 1) + py (z0 + 1)) with x0 = bits(tx) - magic, ...
+    // in wrapping 32-bit arithmetic; the constant folds the offsets.
+    const uint32_t c = (1u - kFloorMagicBits) * (1u + px + pxy);
+    s.base = __float_as_uint(tx) + px * __float_as_uint(ty) + pxy * __float_as_uint(tz) + c;
     return s;
 }
 
 }  // namespace
 
-template <bool BF16, bool DETAIL>
-__global__ void __launch_bounds__(128) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
-                                                float* __restrict__ depth, float* __restrict__ rgb,
-                                                uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
-                                                DevStats* __restrict__ stats, const double* __restrict__ anchor_src,
-                                                double* __restrict__ anchor_dst) {
-    __shared__ float sR[9], sc[3];
-    if (threadIdx.x < 12) {
-        if (threadIdx.x < 9) sR[threadIdx.x] = mats[threadIdx.x];
-        else sc[threadIdx.x - 9] = mats[threadIdx.x];
-    }
-    if (anchor_dst && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 7) anchor_dst[threadIdx.x] = anchor_src[threadIdx.x];
-    __syncthreads();
+// One 16x8-pixel tile (128 threads; warp w covers the 8x4 pixels at
+// ((w & 1) 8, (w >> 1) 4) of the tile).  sR / sc: camera-to-world rotation
+// and centre in shared memory.  anchor_src / anchor_dst: when given, the
+// tile at (0, 0) copies the 7 pose doubles.
+//
+// The march runs in two loops with the same body: samples 1..k_safe, which
+// a conservative FP32 bound (one voxel of margin, far above the rounding of
+// the bound and of the sample positions) shows to lie inside the grid, skip
+// the grid test; the samples after them are tested one by one.  The samples,
+// corner indices and hit index are those of the one-loop march.
+template <bool BF16, bool DETAIL, int PX>
+__device__ __forceinline__ void render_tile(const KParams& P, const float* sR, const float* sc, const MapPlanes& M,
+                                            float* __restrict__ depth, float* __restrict__ rgb,
+                                            uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
+                                            DevStats* __restrict__ stats, int tile_x, int tile_y) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int v = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    const int u = tile_x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int v = tile_y * 8 + (warp >> 1) * 4 + (lane >> 3);
     const bool active = u < P.W && v < P.H;
+    const uint32_t px = PX > 0 ? (uint32_t)PX : P.px;
+    const uint32_t pxy = PX > 0 ? (uint32_t)(PX * PX) : P.pxy;
 
     int nsamp = 0, hk = 0;
     unsigned int uniq = 0;   // distinct occupancy corners of this ray (DETAIL only)
@@ -95,15 +121,28 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
         float cgz = __fmaf_rn(__fsub_rn(sc[2], P.o32[2]), P.inv_vs32, -0.5f);
         const float hx = (float)P.nx - 0.5f, hy = (float)P.ny - 0.5f, hz = (float)P.nz - 0.5f;
 
+        // k_safe: every sample k <= k_safe stays one voxel inside the grid
+        int k_safe = 0;
+        if (cgx >= 0.5f && cgx <= hx - 1.0f && cgy >= 0.5f && cgy <= hy - 1.0f && cgz >= 0.5f &&
+            cgz <= hz - 1.0f) {
+            float ks = (float)P.kmax;
+            const float rg3[3] = {rgx, rgy, rgz}, cg3[3] = {cgx, cgy, cgz}, h3[3] = {hx, hy, hz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (rg3[a] > 0.0f) ks = fminf(ks, (h3[a] - 1.0f - cg3[a]) / (rg3[a] * P.eps32));
+                else if (rg3[a] < 0.0f) ks = fminf(ks, (0.5f - cg3[a]) / (rg3[a] * P.eps32));
+            }
+            k_safe = ks > 0.0f ? (int)ks : 0;
+            k_safe = k_safe < P.kmax ? k_safe : P.kmax;
+        }
+
         float f = 0.0f, f_prev = 0.0f;
         int k = 1;
+        float kf = 1.0f;   // (float)k, exact below 2^24
         bool hit = false;
         Sample cur;
         float pfx = -2.0f, pfy = -2.0f, pfz = -2.0f;
-        for (; k <= P.kmax; ++k) {
-            const float d = __fmul_rn((float)k, P.eps32);
-            const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
-            if (!(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
+        auto step = [&](float gx, float gy, float gz) -> bool {
             ++nsamp;
             if (DETAIL) {   // consecutive cells share 8 >> (axes changed) corners (steps below one voxel)
                 const float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
@@ -111,29 +150,43 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
                 uniq += nsamp == 1 ? 8u : 8u - (8u >> ch);
                 pfx = flx; pfy = fly; pfz = flz;
             }
-            cur = cell_of(P, gx, gy, gz);
-            f = trilinear<BF16>(M.occ, cur.base, P.px, P.pxy, cur.fx, cur.fy, cur.fz);
-            if (f > P.tau32) { hit = true; break; }
+            cur = cell_of(px, pxy, gx, gy, gz);
+            f = trilinear<BF16, PX>(M.occ, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+            if (f > P.tau32) return true;
             f_prev = f;
+            return false;
+        };
+        for (; k <= k_safe; ++k, kf += 1.0f) {
+            const float d = __fmul_rn(kf, P.eps32);
+            if (step(__fmaf_rn(d, rgx, cgx), __fmaf_rn(d, rgy, cgy), __fmaf_rn(d, rgz, cgz))) { hit = true; break; }
+        }
+        if (!hit) {
+            for (; k <= P.kmax; ++k, kf += 1.0f) {
+                const float d = __fmul_rn(kf, P.eps32);
+                const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
+                if (!(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
+                if (step(gx, gy, gz)) { hit = true; break; }
+            }
         }
         if (hit && k == 1) hk = -1;
         if (hit && k >= 2) {
             hk = k;
             // sample k - 1, recomputed exactly (same recipe) instead of carried along
             const float d1 = __fmul_rn((float)(k - 1), P.eps32);
-            const Sample prev = cell_of(P, __fmaf_rn(d1, rgx, cgx), __fmaf_rn(d1, rgy, cgy), __fmaf_rn(d1, rgz, cgz));
+            const Sample prev = cell_of(px, pxy, __fmaf_rn(d1, rgx, cgx), __fmaf_rn(d1, rgy, cgy),
+                                        __fmaf_rn(d1, rgz, cgz));
             const float alpha = __fdiv_rn(P.tau32 - f_prev, f - f_prev);
             const float dk = __fmul_rn((float)k, P.eps32);
             const float dstar = fmaf(alpha, dk - d1, d1);
             out_d = dstar * inv_n;
-            float a1 = trilinear<BF16>(M.r, cur.base, P.px, P.pxy, cur.fx, cur.fy, cur.fz);
-            float a0 = trilinear<BF16>(M.r, prev.base, P.px, P.pxy, prev.fx, prev.fy, prev.fz);
+            float a1 = trilinear<BF16, PX>(M.r, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+            float a0 = trilinear<BF16, PX>(M.r, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
             out_r = fmaf(alpha, a1 - a0, a0);
-            a1 = trilinear<BF16>(M.g, cur.base, P.px, P.pxy, cur.fx, cur.fy, cur.fz);
-            a0 = trilinear<BF16>(M.g, prev.base, P.px, P.pxy, prev.fx, prev.fy, prev.fz);
+            a1 = trilinear<BF16, PX>(M.g, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+            a0 = trilinear<BF16, PX>(M.g, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
             out_g = fmaf(alpha, a1 - a0, a0);
-            a1 = trilinear<BF16>(M.b, cur.base, P.px, P.pxy, cur.fx, cur.fy, cur.fz);
-            a0 = trilinear<BF16>(M.b, prev.base, P.px, P.pxy, prev.fx, prev.fy, prev.fz);
+            a1 = trilinear<BF16, PX>(M.b, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+            a0 = trilinear<BF16, PX>(M.b, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
             out_b = fmaf(alpha, a1 - a0, a0);
         }
         const int p = v * P.W + u;
@@ -158,9 +211,27 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
     }
 }
 
+template <bool BF16, bool DETAIL, int PX>
+__global__ void __launch_bounds__(128) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
+                                                float* __restrict__ depth, float* __restrict__ rgb,
+                                                uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
+                                                DevStats* __restrict__ stats, const double* __restrict__ anchor_src,
+                                                double* __restrict__ anchor_dst) {
+    pdl_enter();
+    __shared__ float sR[9], sc[3];
+    if (threadIdx.x < 12) {
+        if (threadIdx.x < 9) sR[threadIdx.x] = mats[threadIdx.x];
+        else sc[threadIdx.x - 9] = mats[threadIdx.x];
+    }
+    if (anchor_dst && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 7) anchor_dst[threadIdx.x] = anchor_src[threadIdx.x];
+    __syncthreads();
+    render_tile<BF16, DETAIL, PX>(P, sR, sc, M, depth, rgb, mask, hitk, stats, blockIdx.x, blockIdx.y);
+}
+
 // Depth validity (App. F.3, reading R19): valid iff d > 0, finite, and every
 // in-image 4-neighbour dn has |d - dn| <= disc (FP32).
 __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t* __restrict__ mask) {
+    pdl_enter();
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P.W * P.H) return;
     int u = p % P.W, v = p / P.W;
@@ -180,6 +251,7 @@ __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t
 __global__ void k_anchor_pack(KParams P, const float* __restrict__ depth, const float* __restrict__ rgb,
                               const uint8_t* __restrict__ mask, float4* __restrict__ a0,
                               float4* __restrict__ a1) {
+    pdl_enter();
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P.W * P.H) return;
     int u = p % P.W, v = p / P.W, W = P.W;
@@ -215,30 +287,49 @@ __global__ void k_anchor_pack(KParams P, const float* __restrict__ depth, const 
 }
 
 // ----------------------------------------------------------------- launchers
+// The compile-time padded stride for cubic grids of 64, 128 and 256 voxels a
+// side, else 0 (runtime strides).
+int render_px_specialisation(const KParams& P) {
+    if (P.nx != P.ny || P.px != P.py) return 0;
+    return (P.nx == 64 || P.nx == 128 || P.nx == 256) ? (int)P.px : 0;
+}
+
+template <bool BF16, bool DETAIL>
+static void render_px(const KParams& P, dim3 grid, const float* mats, const MapPlanes& M, float* depth, float* rgb,
+                      uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src, double* anchor_dst,
+                      cudaStream_t s) {
+    switch (render_px_specialisation(P)) {
+        case 66: launch_pdl(k_render<BF16, DETAIL, 66>, grid, 128, s, P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst); break;
+        case 130: launch_pdl(k_render<BF16, DETAIL, 130>, grid, 128, s, P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst); break;
+        case 258: launch_pdl(k_render<BF16, DETAIL, 258>, grid, 128, s, P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst); break;
+        default: launch_pdl(k_render<BF16, DETAIL, 0>, grid, 128, s, P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+    }
+}
+
 cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& M, float* depth, float* rgb,
                           uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src,
                           double* anchor_dst, bool detail, cudaStream_t s) {
-    dim3 grid((P.W + 15) / 16, (P.H + 7) / 8), block(128);
+    dim3 grid((P.W + 15) / 16, (P.H + 7) / 8);
     if (P.bf16) {
-        if (detail) k_render<true, true><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
-        else k_render<true, false><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+        if (detail) render_px<true, true>(P, grid, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst, s);
+        else render_px<true, false>(P, grid, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst, s);
     } else {
-        if (detail) k_render<false, true><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
-        else k_render<false, false><<<grid, block, 0, s>>>(P, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst);
+        if (detail) render_px<false, true>(P, grid, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst, s);
+        else render_px<false, false>(P, grid, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst, s);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s) {
     int n = P.W * P.H;
-    k_depth_mask<<<(n + 255) / 256, 256, 0, s>>>(P, depth, mask);
+    launch_pdl(k_depth_mask, (n + 255) / 256, 256, s, P, depth, mask);
     return cudaGetLastError();
 }
 
 cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, const uint8_t* mask,
                                float4* a0, float4* a1, cudaStream_t s) {
     int n = P.W * P.H;
-    k_anchor_pack<<<(n + 255) / 256, 256, 0, s>>>(P, depth, rgb, mask, a0, a1);
+    launch_pdl(k_anchor_pack, (n + 255) / 256, 256, s, P, depth, rgb, mask, a0, a1);
     return cudaGetLastError();
 }
 

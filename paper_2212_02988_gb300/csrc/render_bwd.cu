@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(128) k_render_bwd(KParams P, const float* __re
                                                     const float* __restrict__ gD, const float* __restrict__ gC,
                                                     float* __restrict__ g_occ, float* __restrict__ g_rgb,
                                                     DevState* __restrict__ dev) {
+    pdl_enter();
     __shared__ float sR[9], sc[3];
     __shared__ float sred[4][6];
     if (threadIdx.x < 12) {
@@ -188,9 +189,9 @@ cudaError_t launch_render_bwd(const KParams& P, const float* mats, const MapPlan
                               cudaStream_t s) {
     dim3 grid((P.W + 15) / 16, (P.H + 7) / 8), block(128);
     if (P.bf16)
-        k_render_bwd<true><<<grid, block, 0, s>>>(P, mats, M, grad_depth, grad_rgb, grad_occ, grad_rgb_map, dev);
+        launch_pdl(k_render_bwd<true>, grid, block, s, P, mats, M, grad_depth, grad_rgb, grad_occ, grad_rgb_map, dev);
     else
-        k_render_bwd<false><<<grid, block, 0, s>>>(P, mats, M, grad_depth, grad_rgb, grad_occ, grad_rgb_map, dev);
+        launch_pdl(k_render_bwd<false>, grid, block, s, P, mats, M, grad_depth, grad_rgb, grad_occ, grad_rgb_map, dev);
     return cudaGetLastError();
 }
 

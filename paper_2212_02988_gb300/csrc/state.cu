@@ -19,6 +19,7 @@ namespace prism {
 
 __global__ void __launch_bounds__(256) k_predict(KParams P, DevState* dev, const double* __restrict__ imu, int n,
                                                  double dt) {
+    pdl_enter();
     __shared__ double R[9], B[36], F[144], T1[144], Sig[144], Svp[36], Spv[36], Dm[36], Spp[36];
     __shared__ double Rw[9], Jl[9], vnew[6], Lch[36], rdg[6];
     __shared__ int ok;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(256) k_predict(KParams P, DevState* dev, const
 // FP32 decision matrices of a pose (see PrepKind), computed once per pose by
 // the FP64 recipe so that no kernel block repeats the FP64 chain.
 __global__ void k_prep(DevState* dev, int kind, PoseArg pose) {
+    pdl_enter();
     if (threadIdx.x != 0) return;
     switch (kind) {
         case PREP_STATE:
@@ -194,12 +196,12 @@ __global__ void k_prep(DevState* dev, int kind, PoseArg pose) {
 }
 
 cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s) {
-    k_prep<<<1, 32, 0, s>>>(dev, kind, pose);
+    launch_pdl(k_prep, 1, 32, s, dev, kind, pose);
     return cudaGetLastError();
 }
 
 cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt, cudaStream_t s) {
-    k_predict<<<1, 256, 0, s>>>(P, dev, imu, n, dt);
+    launch_pdl(k_predict, 1, 256, s, P, dev, imu, n, dt);
     return cudaGetLastError();
 }
 

@@ -93,13 +93,14 @@ __global__ void __launch_bounds__(kThreads) k_track(KParams P, const float* __re
                                                     const uint8_t* __restrict__ om,
                                                     const float4* __restrict__ a0,
                                                     const float4* __restrict__ a1, DevState* dev,
-                                                    double* __restrict__ partials, int pstride,
+                                                    float* __restrict__ partials, int pstride,
                                                     unsigned int* __restrict__ counter,
                                                     DevStats* __restrict__ stats) {
+    pdl_enter();
     constexpr int N = NV<MODE>::value;
     using L = Layout<MODE>;
     __shared__ float sM[9], sb[3];
-    __shared__ double swarp[kWarps][N];
+    __shared__ float swarp[kWarps][N];
     __shared__ double S[64];
     __shared__ double sm[8][36];
     __shared__ double sx[8][36];
@@ -189,15 +190,15 @@ __global__ void __launch_bounds__(kThreads) k_track(KParams P, const float* __re
         acc[L::oCount] += 1.0f;
     }
 
-    // ---- block reduction: FP32 within the warp, FP64 across warps ----
+    // ---- block reduction: FP32, in a fixed order (warp shuffles, then warps 0..7) ----
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         float s = warp_sum(acc[i]);
-        if (lane == 0) swarp[warp][i] = (double)s;
+        if (lane == 0) swarp[warp][i] = s;
     }
     __syncthreads();
     if (tid < N) {   // partials are stored value-major: partials[v * pstride + block]
-        double s = swarp[0][tid];
+        float s = swarp[0][tid];
         for (int w = 1; w < kWarps; ++w) s += swarp[w][tid];
         partials[(size_t)tid * pstride + blockIdx.x] = s;
     }
@@ -228,28 +229,32 @@ __global__ void __launch_bounds__(kThreads) k_track(KParams P, const float* __re
     // is fully unrolled; G <= 32 * kMaxPerLane is checked at launch).
     // Warp w sums rows v = w, w + 8, ... (at most kRows); the loads of all its
     // rows are issued before the first add.
+    // The sums stay FP32 (a GB300 SM retires about two FP64 adds per clock,
+    // so ~9,000 of them would dominate this block's tail; FP32 keeps the
+    // sums to ~1e-6 relative, far inside what a Gauss-Newton step or the
+    // Laplace covariance needs) and are widened to FP64 for the finish.
     const int G = gridDim.x;
     constexpr int kRows = (N + kWarps - 1) / kWarps;
-    double x[kRows][kMaxPerLane];
+    float x[kRows][kMaxPerLane];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
         const int v = warp + kWarps * q;
-        const double* row = partials + (size_t)(v < N ? v : 0) * pstride;
+        const float* row = partials + (size_t)(v < N ? v : 0) * pstride;
 #pragma unroll
         for (int j = 0; j < kMaxPerLane; ++j) {
             const int b = lane + 32 * j;
-            x[q][j] = (v < N && b < G) ? __ldcg(row + b) : 0.0;
+            x[q][j] = (v < N && b < G) ? __ldcg(row + b) : 0.0f;
         }
     }
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
-        double s = x[q][0];
+        float s = x[q][0];
 #pragma unroll
         for (int j = 1; j < kMaxPerLane; ++j) s += x[q][j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const int v = warp + kWarps * q;
-        if (lane == 0 && v < N) S[v] = s;
+        if (lane == 0 && v < N) S[v] = (double)s;
     }
     __syncthreads();
     if (tid == 0) {
@@ -534,7 +539,7 @@ int track_grid(const KParams& P, int max_blocks) {
 
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
-                         DevState* dev, double* partials, unsigned int* counter, int max_blocks,
+                         DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s) {
     int grid = track_grid(P, max_blocks);
     const int wave = mode == TRACK_GN ? wave_blocks<TRACK_GN>()
@@ -542,15 +547,15 @@ cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
     if (grid > wave) grid = wave;
     switch (mode) {
         case TRACK_GN:
-            k_track<TRACK_GN><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+            launch_pdl(k_track<TRACK_GN>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                                                         max_blocks, counter, stats);
             break;
         case TRACK_LAPLACE:
-            k_track<TRACK_LAPLACE><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev,
+            launch_pdl(k_track<TRACK_LAPLACE>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
                                                              partials, max_blocks, counter, stats);
             break;
         default:
-            k_track<TRACK_EXPORT><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev,
+            launch_pdl(k_track<TRACK_EXPORT>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
                                                             partials, max_blocks, counter, stats);
     }
     return cudaGetLastError();
