@@ -45,6 +45,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
     ap.add_argument("--reference-budget-s", type=float, default=150.0)
+    ap.add_argument("--serve", action="store_true",
+                    help="run only the multi-stream serving workload (32 streams) and print its JSON line")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="length of the serving run (default 120 with --serve, 12 inside the default run)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default bench")
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     return ap.parse_args(argv)
 
 
@@ -337,6 +343,211 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+# ---------------------------------------------------------------- serving
+def prepare_serving(duration_s: float, frames_per_cycle: int, dev, seed: int = 4000):
+    """The stream mix and, per stream, its pre-rendered frame cycle in pinned
+    host memory, IMU windows, first state and request arrival times."""
+    import numpy as np
+    import synth
+    from paper_2212_02988_gb300 import config, make_state
+    from synth.gpu_frames import raycast_frames
+    from synth.serving import request_times, serving_plan
+    plans = serving_plan(32, duration_s, seed, frames_per_cycle)
+    rng = np.random.default_rng(seed + 1)
+    streams = []
+    for p in plans:
+        w = p.workload
+        seq = synth.Sequence(w)
+        P = w.n_frames
+        d, c = raycast_frames(seq, range(P), dev, seed=p.index)
+        streams.append({"plan": p, "w": w, "D": d.cpu().pin_memory(), "C": c.cpu().pin_memory(),
+                        "imus": [None] + [seq.imu_window(i) for i in range(1, P + 1)],
+                        "cfg": config(w.n, w.extent, w.width, w.height),
+                        "s1": make_state(seq.pose7(0), seq.velocity(0)),
+                        "times": request_times(p, rng, duration_s)})
+    return streams
+
+
+def _frame_of(st, k):
+    P = st["w"].n_frames
+    imu = None if k == 0 else st["imus"][((k - 1) % P) + 1]
+    return imu, st["D"][k % P], st["C"][k % P]
+
+
+def _events(streams):
+    ev = []
+    for i, st in enumerate(streams):
+        ts = st["times"]
+        if len(ts) == 0:
+            continue
+        ev.append((ts[0], 0, i, -1))                       # open
+        ev += [(t, 1, i, k) for k, t in enumerate(ts)]       # requests
+        ev.append((ts[-1], 2, i, -1))                        # close after its last request
+    return sorted(ev)
+
+
+def _lat_stats(lat, frames, span):
+    import numpy as np
+    lat = np.asarray(lat)
+    return {"frames": int(frames), "frames_per_s": frames / span if span > 0 else None,
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "max_ms": float(lat.max()) if lat.size else None}
+
+
+def serve_batched(streams, budget_bytes, device):
+    """The arrival schedule through the multi-stream server (bf16 maps)."""
+    from paper_2212_02988_gb300.serve import Server
+    srv = Server(budget_bytes, max_slots=64, storage="bf16", device=device)
+    ev = _events(streams)
+    ids, lat, results = {}, [], []
+    t0 = time.perf_counter()
+    for t, kind, i, k in ev:
+        while True:
+            now = time.perf_counter() - t0
+            if now >= t:
+                break
+            results += srv.poll(256, timeout_ms=0)
+            time.sleep(min(2e-4, t - now))
+        st = streams[i]
+        if kind == 0:
+            ids[i] = srv.open(st["cfg"], st["s1"])
+        elif kind == 1:
+            imu, d, c = _frame_of(st, k)
+            srv.submit(ids[i], imu, st["w"].dt, d, c, tag=(i, k))
+        else:
+            srv.close(ids[i])
+    srv.drain(600000)
+    results += srv.poll(1 << 16, timeout_ms=0)
+    stats = srv.stats()
+    srv.destroy()
+    lat = [r["latency_ms"] for r in results]
+    span = max(r["done_s"] for r in results) - min(r["submit_s"] for r in results)
+    out = _lat_stats(lat, len(results), span)
+    out.update({"batches": stats["batches"], "mean_batch": len(results) / max(stats["batches"], 1),
+                "max_batch": stats["max_batch"], "bytes_peak": stats["bytes_peak"], "budget": stats["budget"],
+                "kernel_launches": stats["kernel_launches"], "graph_launches": stats["graph_launches"],
+                "not_pd_steps": sum(1 for r in results if r["status"] != 0)})
+    return out
+
+
+def serve_plain(streams, device):
+    """The same schedule served one request at a time, in arrival order, by
+    one single-stream f32 filter per stream (host copy in, state out)."""
+    import torch
+    from paper_2212_02988_gb300 import Filter
+    ev = _events(streams)
+    F, bufs, lat = {}, {}, []
+    t0 = time.perf_counter()
+    t_first = t_last = None
+    for t, kind, i, k in ev:
+        now = time.perf_counter() - t0
+        if now < t:
+            time.sleep(t - now)
+        st = streams[i]
+        if kind == 0:
+            F[i] = Filter(st["cfg"], st["s1"], device=device)
+            bufs[i] = (torch.empty_like(st["D"][0], device="cuda"), torch.empty_like(st["C"][0], device="cuda"))
+        elif kind == 1:
+            imu, d, c = _frame_of(st, k)
+            db, cb = bufs[i]
+            db.copy_(d, non_blocking=True)
+            cb.copy_(c, non_blocking=True)
+            F[i].step(imu, st["w"].dt, db, cb, want_state=True)
+            done = time.perf_counter() - t0
+            lat.append(1e3 * (done - t))
+            t_first = t if t_first is None else t_first
+            t_last = done
+        else:
+            F.pop(i).close()
+            bufs.pop(i)
+    for f in F.values():
+        f.close()
+    return _lat_stats(lat, len(lat), (t_last or 0) - (t_first or 0))
+
+
+def serve_saturation(streams, seconds, budget_bytes, device):
+    """Closed loop over the first 32 streams (no churn): frames/s when every
+    stream always has two requests waiting (server) or when the streams are
+    stepped round-robin as fast as possible (plain f32 filters)."""
+    import torch
+    from paper_2212_02988_gb300 import Filter
+    from paper_2212_02988_gb300.serve import Server
+    pool = streams[:32]
+    srv = Server(budget_bytes, max_slots=64, storage="bf16", device=device)
+    ids = [srv.open(st["cfg"], st["s1"]) for st in pool]
+    nxt = [0] * len(pool)
+    sid_to = {sid: j for j, sid in enumerate(ids)}
+
+    def sub(j):
+        imu, d, c = _frame_of(pool[j], nxt[j])
+        srv.submit(ids[j], imu, pool[j]["w"].dt, d, c)
+        nxt[j] += 1
+
+    for j in range(len(pool)):
+        sub(j)
+        sub(j)
+    for _ in range(3):                      # warm-up: let every stream finish its first steps
+        for r in srv.poll(512, timeout_ms=2000):
+            sub(sid_to[r["stream"]])
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for r in srv.poll(512, timeout_ms=50):
+            done += 1
+            sub(sid_to[r["stream"]])
+    el = time.perf_counter() - t0
+    st = srv.stats()
+    srv.destroy()
+    batched = {"frames_per_s": done / el, "mean_batch": None if not st["batches"] else st["frames"] / st["batches"]}
+    filters = [Filter(st_["cfg"], st_["s1"], device=device) for st_ in pool]
+    bufs = [(torch.empty_like(st_["D"][0], device="cuda"), torch.empty_like(st_["C"][0], device="cuda"))
+            for st_ in pool]
+    k = [0] * len(pool)
+
+    def step(j):
+        imu, d, c = _frame_of(pool[j], k[j])
+        bufs[j][0].copy_(d, non_blocking=True)
+        bufs[j][1].copy_(c, non_blocking=True)
+        filters[j].step(imu, pool[j]["w"].dt, bufs[j][0], bufs[j][1], want_state=True)
+        k[j] += 1
+
+    for j in range(len(pool)):
+        step(j)
+        step(j)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        step(n % len(pool))
+        n += 1
+    el = time.perf_counter() - t0
+    for f in filters:
+        f.close()
+    return {"batched_bf16": batched, "plain_f32": {"frames_per_s": n / el}, "streams": len(pool),
+            "seconds": seconds}
+
+
+def run_serving(args, local_rank, seconds, frames_per_cycle):
+    import torch
+    dev = torch.device("cuda", local_rank)
+    t_prep = time.perf_counter()
+    streams = prepare_serving(seconds, frames_per_cycle, dev)
+    prep_s = time.perf_counter() - t_prep
+    budget = int(args.serve_budget_gb * (1 << 30))
+    sizes = {}
+    for st in streams:
+        key = f"{st['w'].n}^3/{st['w'].width}x{st['w'].height}"
+        sizes[key] = sizes.get(key, 0) + 1
+    batched = serve_batched(streams, budget, local_rank)
+    plain = serve_plain(streams, local_rank)
+    sat = serve_saturation(streams, min(8.0, max(3.0, seconds / 4)), budget, local_rank)
+    return {"workload": "32 concurrent streams, maps {64,128,256}^3, frames {160x120,320x240,640x480}, "
+                        "10-30 Hz Poisson arrivals, streams arriving and retiring",
+            "seconds": seconds, "streams_total": len(streams), "requests": int(sum(len(s["times"]) for s in streams)),
+            "stream_mix": sizes, "frames_per_cycle": frames_per_cycle, "prepare_s": prep_s,
+            "batched_bf16": batched, "plain_f32": plain, "saturation": sat}
+
+
 def cpu_baseline(args):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     full filter steps of the same configuration on the host."""
@@ -404,12 +615,28 @@ def main(argv=None):
     if world > 1 and not dist.is_initialized():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.serve:
+        if rank == 0:
+            secs = args.serve_seconds if args.serve_seconds is not None else 120.0
+            torch.cuda.set_device(local_rank)
+            srv = run_serving(args, local_rank, secs, 32)
+            b = srv["batched_bf16"]
+            line = {"metric": "serving: p50/p99 step latency and aggregate frames/s, 32 concurrent streams",
+                    "value": b["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": b["frames"],
+                    "warmup": 0, "ms_per_step": b["p50_ms"], "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "bf16 map, f32 math", "data": "synthetic",
+                    "config": {"workload": "serving_32_streams"}, "serving": srv}
+            print(json.dumps(line))
+        return 0
     res = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(args)
         else:
             res["cpu_baseline"] = None
+        if world == 1 and not args.no_serve:
+            secs = args.serve_seconds if args.serve_seconds is not None else 12.0
+            res["serving"] = run_serving(args, local_rank, secs, 16)
         print(json.dumps(res))
     if world > 1:
         dist.destroy_process_group()

@@ -1,4 +1,5 @@
-"""ctypes declarations of include/prism.h and the loader of libprism.so.
+"""ctypes declarations of include/prism.h and include/prism_serve.h, and the
+loader of libprism.so.
 
 The library is built in-tree by paper_2212_02988_gb300.build; if it is
 missing this module raises at load time — there is no fallback path.
@@ -12,6 +13,7 @@ import re
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libprism.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "prism.h")
+HEADERS = [HEADER, os.path.join(os.path.dirname(PKG), "include", "prism_serve.h")]
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTPD, ESTATE = 0, -1, -2, -3, -4, -5
 STORAGE_F32, STORAGE_BF16 = 0, 1
@@ -49,14 +51,35 @@ class Timing(C.Structure):
                [(n, C.c_int64) for n in ("predict_n", "localise_n", "fuse_n", "render_n", "anchor_n")]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_slots", C.c_int32), ("storage", C.c_int32),
+                ("n_gn", C.c_int32), ("max_inflight", C.c_int32), ("use_graph", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("stream_id", C.c_int32), ("status", C.c_int32), ("tag", C.c_int64), ("batch", C.c_int64),
+                ("batch_size", C.c_int32), ("reserved", C.c_int32), ("submit_s", C.c_double),
+                ("done_s", C.c_double), ("latency_ms", C.c_double), ("state", State)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("batches", "frames", "max_batch", "bytes_in_use", "bytes_peak",
+                                         "budget")] + \
+               [(n, C.c_int32) for n in ("streams_resident", "streams_queued", "streams_open", "reserved")] + \
+               [(n, C.c_int64) for n in ("kernel_launches", "graph_launches")]
+
+
 _lib = None
 
 
 def header_functions() -> list[str]:
-    """Names of the functions include/prism.h declares."""
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(prism_[a-z0-9_]+)\s*\(", text)))
+    """Names of the functions include/prism.h and include/prism_serve.h declare."""
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(prism_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def load() -> C.CDLL:
@@ -96,6 +119,18 @@ def load() -> C.CDLL:
         "prism_render_backward": (st, [H, dp, fp, fp, fp, fp, dp, dp]),
         "prism_normal_equations_noalloc": (st, [P(Config), dp, fp, fp, dp, fp, fp, vp, dp]),
         "prism_noalloc_last_error": (C.c_char_p, []),
+        "prism_serve_config_default": (None, [P(ServeConfig)]),
+        "prism_serve_stream_bytes": (C.c_int64, [P(Config), C.c_int32]),
+        "prism_serve_create": (st, [P(ServeConfig), P(H)]),
+        "prism_serve_destroy": (st, [H]),
+        "prism_serve_open": (st, [H, P(Config), P(State), fp, fp, fp, fp, P(C.c_int32)]),
+        "prism_serve_submit": (st, [H, C.c_int32, dp, C.c_int32, C.c_double, fp, fp, C.c_int64]),
+        "prism_serve_close": (st, [H, C.c_int32]),
+        "prism_serve_poll": (st, [H, P(ServeResult), C.c_int32, C.c_int32, P(C.c_int32)]),
+        "prism_serve_drain": (st, [H, C.c_int32]),
+        "prism_serve_get_stats": (st, [H, P(ServeStats)]),
+        "prism_serve_map_store": (st, [H, C.c_int32, fp, fp, fp, fp]),
+        "prism_serve_last_error": (C.c_char_p, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -17,8 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
 SOURCES = ["render.cu", "track.cu", "state.cu", "fuse.cu", "mapio.cu", "prism_abi.cu", "noalloc.cu",
-           "render_bwd.cu"]
-HEADERS = ["prism_dev.cuh", "linalg64.cuh", "kernels.h"]
+           "render_bwd.cu", "serve_kernels.cu", "serve.cu"]
+HEADERS = ["prism_dev.cuh", "linalg64.cuh", "kernels.h", "render_dev.cuh", "track_dev.cuh", "fuse_dev.cuh",
+           "state_dev.cuh", "serve.h", "host_util.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -32,7 +33,8 @@ def nvcc() -> str:
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "prism.h")]
+    files = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h)
+                                                        for h in ("prism.h", "prism_serve.h")]
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -42,6 +42,8 @@ cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& 
                           uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src,
                           double* anchor_dst, bool detail, cudaStream_t s);
 cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s);
+// The render's compile-time plane-stride specialisation for P (0: none).
+int render_px_specialisation(const KParams& P);
 cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, const uint8_t* mask,
                                float4* a0, float4* a1, cudaStream_t s);
 
@@ -55,6 +57,8 @@ cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s);
 int track_grid(const KParams& P, int max_blocks);
+// The grid launch_track uses for `mode` (one wave of the device at most).
+int track_launch_grid(const KParams& P, int mode, int max_blocks);
 constexpr int TRACK_NV_MAX = 50;   // FP32 values per block partial
 
 // state.cu — FP64 prediction and GN start; the FP32 matrices of a pose.

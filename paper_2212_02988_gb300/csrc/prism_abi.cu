@@ -11,8 +11,81 @@
 #include "kernels.h"
 #include "prism.h"
 #include "prism_dev.cuh"
+#include "host_util.h"
 
 using namespace prism;
+
+namespace prism {
+
+bool valid_config(const prism_config* c, std::string& why) {
+    auto bad = [&](const char* m) { why = m; return false; };
+    if (!c) return bad("config is NULL");
+    if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0 || (c->nx % 8) || (c->ny % 8) || (c->nz % 8))
+        return bad("nx, ny, nz must be positive multiples of 8");
+    if ((double)(c->nx + 2) * (c->ny + 2) * (c->nz + 2) > 2147483648.0) return bad("grid larger than 2^31 voxels");
+    if (c->storage != PRISM_STORAGE_F32 && c->storage != PRISM_STORAGE_BF16) return bad("storage must be 0 or 1");
+    if (c->width < 3 || c->height < 3 || (double)c->width * c->height > 1.0e8) return bad("image size out of range");
+    if (c->n_gn < 1 || c->n_gn > 1000) return bad("n_gn must be in [1, 1000]");
+    if (!(c->voxel > 0) || !(c->eps > 0) || !(c->fx > 0) || !(c->fy > 0)) return bad("voxel, eps, fx, fy must be > 0");
+    if (!(c->prior_var > 0) || !(c->update_var > 0) || !(c->trunc > 0)) return bad("variances and trunc must be > 0");
+    if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
+        return bad("Laplace scales and IRLS floors must be > 0");
+    if (!(c->ema >= 0 && c->ema <= 1)) return bad("ema must be in [0, 1]");
+    for (double x : {c->origin[0], c->origin[1], c->origin[2], c->cx, c->cy, c->tau, c->max_depth})
+        if (!std::isfinite(x)) return bad("non-finite configuration value");
+    return true;
+}
+
+void fill_kparams(const prism_config* c, KParams& k) {
+    std::memset(&k, 0, sizeof(k));
+    k.nx = c->nx; k.ny = c->ny; k.nz = c->nz;
+    k.nbx = c->nx / 8; k.nby = c->ny / 8; k.nbz = c->nz / 8;
+    k.px = (uint32_t)c->nx + 2; k.py = (uint32_t)c->ny + 2; k.pxy = k.px * k.py;
+    k.npad = k.pxy * ((uint32_t)c->nz + 2);
+    k.W = c->width; k.H = c->height;
+    k.bf16 = c->storage == PRISM_STORAGE_BF16;
+    // the march cannot take more than (nx + ny + nz) vs / eps in-grid samples
+    double kcap = 2.0 * (c->nx + c->ny + c->nz) * c->voxel / c->eps + 2.0;
+    double kuser = c->max_depth > 0 ? std::floor(c->max_depth / c->eps) : kcap;
+    double km = kuser < kcap ? kuser : kcap;
+    k.kmax = km > 2.0e9 ? 2000000000 : (int)km;
+    for (int a = 0; a < 3; ++a) { k.o32[a] = (float)c->origin[a]; k.origin[a] = c->origin[a]; }
+    k.vs32 = (float)c->voxel;
+    k.inv_vs32 = (float)(1.0 / c->voxel);
+    k.eps32 = (float)c->eps;
+    k.tau32 = (float)c->tau;
+    k.trunc32 = (float)c->trunc;
+    k.disc32 = (float)c->disc;
+    k.fx32 = (float)c->fx; k.fy32 = (float)c->fy; k.cx32 = (float)c->cx; k.cy32 = (float)c->cy;
+    k.ifx32 = (float)(1.0 / c->fx); k.ify32 = (float)(1.0 / c->fy);
+    k.gate_geo32 = (float)c->gate_geo; k.gate_rgb32 = (float)c->gate_rgb;
+    k.b_geo32 = (float)c->b_geo; k.b_rgb32 = (float)c->b_rgb;
+    k.floor_geo32 = (float)c->floor_geo; k.floor_rgb32 = (float)c->floor_rgb;
+    k.upd_prec32 = (float)(1.0 / c->update_var);
+    k.vs = c->voxel; k.eps = c->eps; k.tau = c->tau; k.trunc = c->trunc;
+    k.fx = c->fx; k.fy = c->fy; k.cx = c->cx; k.cy = c->cy;
+    for (int i = 0; i < 2; ++i) { k.sigma_vel[i] = c->sigma_vel[i]; k.sigma_pose[i] = c->sigma_pose[i]; }
+    k.ema = c->ema; k.gravity = c->gravity; k.update_var = c->update_var;
+}
+
+// q / sqrt(((w*w + x*x) + y*y) + z*z): every pose given by the caller is
+// normalised once, here, with exactly these FP64 operations (host code is
+// compiled without floating-point contraction).
+void normalise_pose(const double* in, double* out) {
+    const double n = std::sqrt(((in[3] * in[3] + in[4] * in[4]) + in[5] * in[5]) + in[6] * in[6]);
+    for (int a = 0; a < 3; ++a) out[a] = in[a];
+    for (int a = 0; a < 4; ++a) out[3 + a] = in[3 + a] / n;
+}
+
+bool finite_pose(const double* p) {
+    for (int i = 0; i < 7; ++i)
+        if (!std::isfinite(p[i])) return false;
+    double n = p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6];
+    return n > 1e-20;
+}
+
+}  // namespace prism
+
 
 namespace {
 
@@ -142,57 +215,6 @@ void collect_timing(prism_handle h) {
     h->pending.clear();
 }
 
-bool valid_config(const prism_config* c, std::string& why) {
-    auto bad = [&](const char* m) { why = m; return false; };
-    if (!c) return bad("config is NULL");
-    if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0 || (c->nx % 8) || (c->ny % 8) || (c->nz % 8))
-        return bad("nx, ny, nz must be positive multiples of 8");
-    if ((double)(c->nx + 2) * (c->ny + 2) * (c->nz + 2) > 2147483648.0) return bad("grid larger than 2^31 voxels");
-    if (c->storage != PRISM_STORAGE_F32 && c->storage != PRISM_STORAGE_BF16) return bad("storage must be 0 or 1");
-    if (c->width < 3 || c->height < 3 || (double)c->width * c->height > 1.0e8) return bad("image size out of range");
-    if (c->n_gn < 1 || c->n_gn > 1000) return bad("n_gn must be in [1, 1000]");
-    if (!(c->voxel > 0) || !(c->eps > 0) || !(c->fx > 0) || !(c->fy > 0)) return bad("voxel, eps, fx, fy must be > 0");
-    if (!(c->prior_var > 0) || !(c->update_var > 0) || !(c->trunc > 0)) return bad("variances and trunc must be > 0");
-    if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
-        return bad("Laplace scales and IRLS floors must be > 0");
-    if (!(c->ema >= 0 && c->ema <= 1)) return bad("ema must be in [0, 1]");
-    for (double x : {c->origin[0], c->origin[1], c->origin[2], c->cx, c->cy, c->tau, c->max_depth})
-        if (!std::isfinite(x)) return bad("non-finite configuration value");
-    return true;
-}
-
-void fill_kparams(const prism_config* c, KParams& k) {
-    std::memset(&k, 0, sizeof(k));
-    k.nx = c->nx; k.ny = c->ny; k.nz = c->nz;
-    k.nbx = c->nx / 8; k.nby = c->ny / 8; k.nbz = c->nz / 8;
-    k.px = (uint32_t)c->nx + 2; k.py = (uint32_t)c->ny + 2; k.pxy = k.px * k.py;
-    k.npad = k.pxy * ((uint32_t)c->nz + 2);
-    k.W = c->width; k.H = c->height;
-    k.bf16 = c->storage == PRISM_STORAGE_BF16;
-    // the march cannot take more than (nx + ny + nz) vs / eps in-grid samples
-    double kcap = 2.0 * (c->nx + c->ny + c->nz) * c->voxel / c->eps + 2.0;
-    double kuser = c->max_depth > 0 ? std::floor(c->max_depth / c->eps) : kcap;
-    double km = kuser < kcap ? kuser : kcap;
-    k.kmax = km > 2.0e9 ? 2000000000 : (int)km;
-    for (int a = 0; a < 3; ++a) { k.o32[a] = (float)c->origin[a]; k.origin[a] = c->origin[a]; }
-    k.vs32 = (float)c->voxel;
-    k.inv_vs32 = (float)(1.0 / c->voxel);
-    k.eps32 = (float)c->eps;
-    k.tau32 = (float)c->tau;
-    k.trunc32 = (float)c->trunc;
-    k.disc32 = (float)c->disc;
-    k.fx32 = (float)c->fx; k.fy32 = (float)c->fy; k.cx32 = (float)c->cx; k.cy32 = (float)c->cy;
-    k.ifx32 = (float)(1.0 / c->fx); k.ify32 = (float)(1.0 / c->fy);
-    k.gate_geo32 = (float)c->gate_geo; k.gate_rgb32 = (float)c->gate_rgb;
-    k.b_geo32 = (float)c->b_geo; k.b_rgb32 = (float)c->b_rgb;
-    k.floor_geo32 = (float)c->floor_geo; k.floor_rgb32 = (float)c->floor_rgb;
-    k.upd_prec32 = (float)(1.0 / c->update_var);
-    k.vs = c->voxel; k.eps = c->eps; k.tau = c->tau; k.trunc = c->trunc;
-    k.fx = c->fx; k.fy = c->fy; k.cx = c->cx; k.cy = c->cy;
-    for (int i = 0; i < 2; ++i) { k.sigma_vel[i] = c->sigma_vel[i]; k.sigma_pose[i] = c->sigma_pose[i]; }
-    k.ema = c->ema; k.gravity = c->gravity; k.update_var = c->update_var;
-}
-
 void free_all(prism_handle h) {
     void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->o_mask,
                     h->dstate, h->dstats, h->partials, h->counter, h->d_imu};
@@ -207,22 +229,6 @@ cudaError_t dalloc(prism_handle h, T** p, size_t bytes) {
     cudaError_t e = cudaMalloc((void**)p, bytes);
     if (e == cudaSuccess) h->bytes += (int64_t)bytes;
     return e;
-}
-
-// q / sqrt(((w*w + x*x) + y*y) + z*z): every pose given by the caller is
-// normalised once, here, with exactly these FP64 operations (host code is
-// compiled without floating-point contraction).
-void normalise_pose(const double* in, double* out) {
-    const double n = std::sqrt(((in[3] * in[3] + in[4] * in[4]) + in[5] * in[5]) + in[6] * in[6]);
-    for (int a = 0; a < 3; ++a) out[a] = in[a];
-    for (int a = 0; a < 4; ++a) out[3 + a] = in[3 + a] / n;
-}
-
-bool finite_pose(const double* p) {
-    for (int i = 0; i < 7; ++i)
-        if (!std::isfinite(p[i])) return false;
-    double n = p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6];
-    return n > 1e-20;
 }
 
 prism_status check_flags(prism_handle h) {

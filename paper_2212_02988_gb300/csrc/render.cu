@@ -1,215 +1,9 @@
-// render.cu — the map-mean render of App. B and the anchor it leaves for the
-// localisation (App. E.3, App. F.3).
-//
-// k_render: one thread per pixel, 16x8-pixel blocks of 4 warps, each warp an
-// 8x4 pixel tile so that a warp's rays stay close and their trilinear cells
-// share cache lines.  Each ray marches d_k = k eps, k = 1, 2, ... through the
-// occupancy plane (8 gathered corners per sample, FP32 lerps) and
-// stops at the first sample with occupancy > tau (reading R1) or at the first
-// sample outside the grid (R5).  The occupancy plane is linear with a ghost
-// border (prism_dev.cuh), so a sample costs 8 loads at fixed offsets from
-// one base index.  The hit depth and colour are the alpha
-// interpolation between samples k-1 and k (App. B, R7); the colour planes are
-// read only there.  The decision arithmetic follows the documented FP32
-// recipe with explicitly rounded intrinsics (no contraction), so sample
-// positions, corner indices and hit indices are reproducible bit for bit.
+// render.cu — single-stream launches of the render (App. B) and of the anchor
+// masks and packing; the device bodies are in render_dev.cuh.
 #include "kernels.h"
-#include "prism_dev.cuh"
+#include "render_dev.cuh"
 
 namespace prism {
-
-namespace {
-
-// Trilinear value at a cell given by its padded base index and in-cell
-// weights: lerps along x, then y, then z (the FP32 recipe).  With PX > 0 the
-// plane strides are compile-time constants (cubic grids of PX - 2 voxels a
-// side), so the 8 loads are immediate offsets from one address.
-template <bool BF16, int PX>
-__device__ __forceinline__ float trilinear(const void* plane, uint32_t base, uint32_t px_rt, uint32_t pxy_rt,
-                                           float fx, float fy, float fz) {
-    const uint32_t px = PX > 0 ? (uint32_t)PX : px_rt;
-    const uint32_t pxy = PX > 0 ? (uint32_t)(PX * PX) : pxy_rt;
-    float v000, v100, v010, v110, v001, v101, v011, v111;
-    if constexpr (BF16) {
-        const __nv_bfloat16* q = reinterpret_cast<const __nv_bfloat16*>(plane) + base;
-        v000 = __bfloat162float(__ldg(q)); v100 = __bfloat162float(__ldg(q + 1));
-        v010 = __bfloat162float(__ldg(q + px)); v110 = __bfloat162float(__ldg(q + px + 1));
-        v001 = __bfloat162float(__ldg(q + pxy)); v101 = __bfloat162float(__ldg(q + pxy + 1));
-        v011 = __bfloat162float(__ldg(q + pxy + px)); v111 = __bfloat162float(__ldg(q + pxy + px + 1));
-    } else {
-        const float* q = reinterpret_cast<const float*>(plane) + base;
-        v000 = __ldg(q); v100 = __ldg(q + 1);
-        v010 = __ldg(q + px); v110 = __ldg(q + px + 1);
-        v001 = __ldg(q + pxy); v101 = __ldg(q + pxy + 1);
-        v011 = __ldg(q + pxy + px); v111 = __ldg(q + pxy + px + 1);
-    }
-    const float c00 = lerp_rn(v000, v100, fx);
-    const float c10 = lerp_rn(v010, v110, fx);
-    const float c01 = lerp_rn(v001, v101, fx);
-    const float c11 = lerp_rn(v011, v111, fx);
-    const float c0 = lerp_rn(c00, c10, fy);
-    const float c1 = lerp_rn(c01, c11, fy);
-    return lerp_rn(c0, c1, fz);
-}
-
-// Sample k of a ray in grid units: position g = fma(k eps, rg, cg), lower
-// cell corner floor(g) as a padded base index, in-cell weights g - floor(g).
-struct Sample {
-    uint32_t base;
-    float fx, fy, fz;
-};
-
-// floor(g) for |g| < 2^22 without a conversion instruction: adding
-// 1.5 * 2^23 with rounding toward -inf leaves floor(g) in the low mantissa
-// bits (the sum's ulp is 1), and subtracting it back is exact.
-constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
-constexpr uint32_t kFloorMagicBits = 0x4B400000u;
-
-__device__ __forceinline__ Sample cell_of(uint32_t px, uint32_t pxy, float gx, float gy, float gz) {
-    const float tx = __fadd_rd(gx, kFloorMagic), ty = __fadd_rd(gy, kFloorMagic), tz = __fadd_rd(gz, kFloorMagic);
-    Sample s;
-    s.fx = __fsub_rn(gx, __fsub_rn(tx, kFloorMagic));
-    s.fy = __fsub_rn(gy, __fsub_rn(ty, kFloorMagic));
-    s.fz = __fsub_rn(gz, __fsub_rn(tz, kFloorMagic));
-    // (x0 + 1) + px ((y0 + 1) + py (z0 + 1)) with x0 = bits(tx) - magic, ...
-    // in wrapping 32-bit arithmetic; the constant folds the offsets.
-    const uint32_t c = (1u - kFloorMagicBits) * (1u + px + pxy);
-    s.base = __float_as_uint(tx) + px * __float_as_uint(ty) + pxy * __float_as_uint(tz) + c;
-    return s;
-}
-
-}  // namespace
-
-// One 16x8-pixel tile (128 threads; warp w covers the 8x4 pixels at
-// ((w & 1) 8, (w >> 1) 4) of the tile).  sR / sc: camera-to-world rotation
-// and centre in shared memory.  anchor_src / anchor_dst: when given, the
-// tile at (0, 0) copies the 7 pose doubles.
-//
-// The march runs in two loops with the same body: samples 1..k_safe, which
-// a conservative FP32 bound (one voxel of margin, far above the rounding of
-// the bound and of the sample positions) shows to lie inside the grid, skip
-// the grid test; the samples after them are tested one by one.  The samples,
-// corner indices and hit index are those of the one-loop march.
-template <bool BF16, bool DETAIL, int PX>
-__device__ __forceinline__ void render_tile(const KParams& P, const float* sR, const float* sc, const MapPlanes& M,
-                                            float* __restrict__ depth, float* __restrict__ rgb,
-                                            uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
-                                            DevStats* __restrict__ stats, int tile_x, int tile_y) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = tile_x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int v = tile_y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    const bool active = u < P.W && v < P.H;
-    const uint32_t px = PX > 0 ? (uint32_t)PX : P.px;
-    const uint32_t pxy = PX > 0 ? (uint32_t)(PX * PX) : P.pxy;
-
-    int nsamp = 0, hk = 0;
-    unsigned int uniq = 0;   // distinct occupancy corners of this ray (DETAIL only)
-    float out_d = 0.0f, out_r = 0.0f, out_g = 0.0f, out_b = 0.0f;
-    if (active) {
-        // ray set-up (FP32 recipe)
-        float dx = __fmul_rn(__fsub_rn((float)u, P.cx32), P.ifx32);
-        float dy = __fmul_rn(__fsub_rn((float)v, P.cy32), P.ify32);
-        float w0 = __fmaf_rn(sR[0], dx, __fmaf_rn(sR[1], dy, sR[2]));
-        float w1 = __fmaf_rn(sR[3], dx, __fmaf_rn(sR[4], dy, sR[5]));
-        float w2 = __fmaf_rn(sR[6], dx, __fmaf_rn(sR[7], dy, sR[8]));
-        float inv_n = __fdiv_rn(1.0f, __fsqrt_rn(__fmaf_rn(w0, w0, __fmaf_rn(w1, w1, __fmul_rn(w2, w2)))));
-        float rgx = __fmul_rn(__fmul_rn(w0, inv_n), P.inv_vs32);
-        float rgy = __fmul_rn(__fmul_rn(w1, inv_n), P.inv_vs32);
-        float rgz = __fmul_rn(__fmul_rn(w2, inv_n), P.inv_vs32);
-        float cgx = __fmaf_rn(__fsub_rn(sc[0], P.o32[0]), P.inv_vs32, -0.5f);
-        float cgy = __fmaf_rn(__fsub_rn(sc[1], P.o32[1]), P.inv_vs32, -0.5f);
-        float cgz = __fmaf_rn(__fsub_rn(sc[2], P.o32[2]), P.inv_vs32, -0.5f);
-        const float hx = (float)P.nx - 0.5f, hy = (float)P.ny - 0.5f, hz = (float)P.nz - 0.5f;
-
-        // k_safe: every sample k <= k_safe stays one voxel inside the grid
-        int k_safe = 0;
-        if (cgx >= 0.5f && cgx <= hx - 1.0f && cgy >= 0.5f && cgy <= hy - 1.0f && cgz >= 0.5f &&
-            cgz <= hz - 1.0f) {
-            float ks = (float)P.kmax;
-            const float rg3[3] = {rgx, rgy, rgz}, cg3[3] = {cgx, cgy, cgz}, h3[3] = {hx, hy, hz};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (rg3[a] > 0.0f) ks = fminf(ks, (h3[a] - 1.0f - cg3[a]) / (rg3[a] * P.eps32));
-                else if (rg3[a] < 0.0f) ks = fminf(ks, (0.5f - cg3[a]) / (rg3[a] * P.eps32));
-            }
-            k_safe = ks > 0.0f ? (int)ks : 0;
-            k_safe = k_safe < P.kmax ? k_safe : P.kmax;
-        }
-
-        float f = 0.0f, f_prev = 0.0f;
-        int k = 1;
-        float kf = 1.0f;   // (float)k, exact below 2^24
-        bool hit = false;
-        Sample cur;
-        float pfx = -2.0f, pfy = -2.0f, pfz = -2.0f;
-        auto step = [&](float gx, float gy, float gz) -> bool {
-            ++nsamp;
-            if (DETAIL) {   // consecutive cells share 8 >> (axes changed) corners (steps below one voxel)
-                const float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
-                const int ch = (flx != pfx) + (fly != pfy) + (flz != pfz);
-                uniq += nsamp == 1 ? 8u : 8u - (8u >> ch);
-                pfx = flx; pfy = fly; pfz = flz;
-            }
-            cur = cell_of(px, pxy, gx, gy, gz);
-            f = trilinear<BF16, PX>(M.occ, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            if (f > P.tau32) return true;
-            f_prev = f;
-            return false;
-        };
-        for (; k <= k_safe; ++k, kf += 1.0f) {
-            const float d = __fmul_rn(kf, P.eps32);
-            if (step(__fmaf_rn(d, rgx, cgx), __fmaf_rn(d, rgy, cgy), __fmaf_rn(d, rgz, cgz))) { hit = true; break; }
-        }
-        if (!hit) {
-            for (; k <= P.kmax; ++k, kf += 1.0f) {
-                const float d = __fmul_rn(kf, P.eps32);
-                const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
-                if (!(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
-                if (step(gx, gy, gz)) { hit = true; break; }
-            }
-        }
-        if (hit && k == 1) hk = -1;
-        if (hit && k >= 2) {
-            hk = k;
-            // sample k - 1, recomputed exactly (same recipe) instead of carried along
-            const float d1 = __fmul_rn((float)(k - 1), P.eps32);
-            const Sample prev = cell_of(px, pxy, __fmaf_rn(d1, rgx, cgx), __fmaf_rn(d1, rgy, cgy),
-                                        __fmaf_rn(d1, rgz, cgz));
-            const float alpha = __fdiv_rn(P.tau32 - f_prev, f - f_prev);
-            const float dk = __fmul_rn((float)k, P.eps32);
-            const float dstar = fmaf(alpha, dk - d1, d1);
-            out_d = dstar * inv_n;
-            float a1 = trilinear<BF16, PX>(M.r, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            float a0 = trilinear<BF16, PX>(M.r, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            out_r = fmaf(alpha, a1 - a0, a0);
-            a1 = trilinear<BF16, PX>(M.g, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            a0 = trilinear<BF16, PX>(M.g, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            out_g = fmaf(alpha, a1 - a0, a0);
-            a1 = trilinear<BF16, PX>(M.b, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            a0 = trilinear<BF16, PX>(M.b, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            out_b = fmaf(alpha, a1 - a0, a0);
-        }
-        const int p = v * P.W + u;
-        if (depth) depth[p] = out_d;
-        if (rgb) { rgb[3 * p] = out_r; rgb[3 * p + 1] = out_g; rgb[3 * p + 2] = out_b; }
-        if (mask) mask[p] = (uint8_t)(hk >= 2);
-        if (hitk) hitk[p] = hk;
-    }
-    if (stats) {
-        unsigned long long s = warp_sum_u64((unsigned long long)nsamp);
-        unsigned int hits = __popc(__ballot_sync(0xffffffffu, hk >= 2));
-        unsigned int rays = __popc(__ballot_sync(0xffffffffu, active));
-        if (DETAIL) {
-            const unsigned long long q = warp_sum_u64((unsigned long long)uniq);
-            if (lane == 0) atomicAdd(&stats->render_unique_corners, q);
-        }
-        if (lane == 0) {
-            atomicAdd(&stats->render_samples, s);
-            atomicAdd(&stats->render_hits, (unsigned long long)hits);
-            atomicAdd(&stats->render_rays, (unsigned long long)rays);
-        }
-    }
-}
 
 template <bool BF16, bool DETAIL, int PX>
 __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
@@ -228,62 +22,18 @@ __global__ void __launch_bounds__(128) k_render(KParams P, const float* __restri
     render_tile<BF16, DETAIL, PX>(P, sR, sc, M, depth, rgb, mask, hitk, stats, blockIdx.x, blockIdx.y);
 }
 
-// Depth validity (App. F.3, reading R19): valid iff d > 0, finite, and every
-// in-image 4-neighbour dn has |d - dn| <= disc (FP32).
 __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t* __restrict__ mask) {
     pdl_enter();
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P.W * P.H) return;
-    int u = p % P.W, v = p / P.W;
-    float d = depth[p];
-    bool ok = (d > 0.0f) && isfinite(d);
-    if (ok && u > 0) ok = fabsf(__fsub_rn(d, depth[p - 1])) <= P.disc32;
-    if (ok && u < P.W - 1) ok = fabsf(__fsub_rn(d, depth[p + 1])) <= P.disc32;
-    if (ok && v > 0) ok = fabsf(__fsub_rn(d, depth[p - P.W])) <= P.disc32;
-    if (ok && v < P.H - 1) ok = fabsf(__fsub_rn(d, depth[p + P.W])) <= P.disc32;
-    mask[p] = (uint8_t)ok;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P.W * P.H) depth_mask_px(P, depth, mask, p);
 }
 
-// Anchor packing (App. E.3, reading R18): per pixel
-//   a0 = (n_x, n_y, n_z, z)  with z = 0 where the normal is invalid,
-//   a1 = (r, g, b, 1 if the depth is valid else 0).
-// n = normalize((P(u+1,v) - P(u-1,v)) x (P(u,v+1) - P(u,v-1))), facing the camera.
 __global__ void k_anchor_pack(KParams P, const float* __restrict__ depth, const float* __restrict__ rgb,
                               const uint8_t* __restrict__ mask, float4* __restrict__ a0,
                               float4* __restrict__ a1) {
     pdl_enter();
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P.W * P.H) return;
-    int u = p % P.W, v = p / P.W, W = P.W;
-    bool ok = u >= 1 && u <= P.W - 2 && v >= 1 && v <= P.H - 2 && mask[p] && mask[p - 1] && mask[p + 1] &&
-              mask[p - W] && mask[p + W];
-    float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
-    if (ok) {
-        float a[3], b[3], c[3], d[3], pc[3];
-        backproject_rn(P, u + 1, v, depth[p + 1], a);
-        backproject_rn(P, u - 1, v, depth[p - 1], b);
-        backproject_rn(P, u, v + 1, depth[p + W], c);
-        backproject_rn(P, u, v - 1, depth[p - W], d);
-        backproject_rn(P, u, v, depth[p], pc);
-        float e1[3], e2[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { e1[i] = __fsub_rn(a[i], b[i]); e2[i] = __fsub_rn(c[i], d[i]); }
-        float c0 = __fsub_rn(__fmul_rn(e1[1], e2[2]), __fmul_rn(e1[2], e2[1]));
-        float c1 = __fsub_rn(__fmul_rn(e1[2], e2[0]), __fmul_rn(e1[0], e2[2]));
-        float c2 = __fsub_rn(__fmul_rn(e1[0], e2[1]), __fmul_rn(e1[1], e2[0]));
-        float nn = __fmaf_rn(c0, c0, __fmaf_rn(c1, c1, __fmul_rn(c2, c2)));
-        if (!(nn > 0.0f) || !isfinite(nn)) {
-            ok = false;
-        } else {
-            float inv = __fdiv_rn(1.0f, __fsqrt_rn(nn));
-            n0 = __fmul_rn(c0, inv); n1 = __fmul_rn(c1, inv); n2 = __fmul_rn(c2, inv);
-            float dp = __fmaf_rn(n0, pc[0], __fmaf_rn(n1, pc[1], __fmul_rn(n2, pc[2])));
-            if (dp > 0.0f) { n0 = -n0; n1 = -n1; n2 = -n2; }
-        }
-    }
-    if (!ok) n0 = n1 = n2 = 0.0f;
-    a0[p] = make_float4(n0, n1, n2, ok ? depth[p] : 0.0f);
-    a1[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], mask[p] ? 1.0f : 0.0f);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P.W * P.H) anchor_pack_px(P, depth, rgb, mask, a0, a1, p);
 }
 
 // ----------------------------------------------------------------- launchers

@@ -1,0 +1,203 @@
+// state_dev.cuh — device bodies of the FP64 prediction and of the pose
+// matrices, shared by the single-stream kernels (state.cu) and the batched
+// serving kernels (serve_kernels.cu).
+//
+// The FP64 prediction step (App. E.1 transition with the
+// linearisation of App. E.1, Eq. statepropagation, App. E.2 split into the
+// pose prior and the velocity conditional), on one block.
+//
+// Controls from the IMU window (reading R13): u_lin = R_mid mean(acc) + g,
+// R_mid = Exp(w_m dt / 2) R; u_ang = (R_end w_end - w_prev) / dt with w_end
+// the least-squares line through the gyro samples at the last sample time,
+// R_end = Exp(w_m dt) R, w_m = R mean(gyro).  Velocity integration reads the
+// printed (dt)^2 as dt (R12).  Error state (dt, dtheta, dv, dw) with the
+// rotation error on the left (R14): A = diag(I, Exp(w dt)),
+// B = diag(dt I, J_l(w dt) dt), F = [[A, B], [0, I]],
+// Sigma' = F Sigma F^T + [[B Qv B^T + Qp, B Qv], [Qv B^T, Qv]].
+// The kernel also starts the Gauss-Newton iterate at the prior mean.
+#pragma once
+
+#include "kernels.h"
+#include "linalg64.cuh"
+#include "prism_dev.cuh"
+
+namespace prism {
+
+// The prediction on one block of 256 threads.
+__device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, const double* __restrict__ imu,
+                                              int n, double dt) {
+    __shared__ double R[9], B[36], F[144], T1[144], Sig[144], Svp[36], Spv[36], Dm[36], Spp[36];
+    __shared__ double Rw[9], Jl[9], vnew[6], Lch[36], rdg[6];
+    __shared__ int ok;
+    __shared__ double sums[8];   // mean t, acc (3), gyro (3), then t_end
+    __shared__ double fit[4];    // sum dt^2, sum dt * dgyro (3)
+    const int tid = threadIdx.x, lane = tid & 31;
+    // IMU window statistics on warp 0: lane l takes samples l, l + 32, ...;
+    // the warp reduction order is fixed, so the result is deterministic.
+    if (tid < 32) {
+        const double inv_n = n > 0 ? 1.0 / n : 0.0;
+        double a[7] = {0, 0, 0, 0, 0, 0, 0}, te = -1e300;
+        for (int i = lane; i < n; i += 32) {
+            for (int c = 0; c < 7; ++c) a[c] += imu[7 * i + c];
+            te = fmax(te, imu[7 * i]);
+        }
+        for (int c = 0; c < 7; ++c) {
+            double v = a[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            a[c] = v * inv_n;
+        }
+        for (int o = 16; o > 0; o >>= 1) te = fmax(te, __shfl_xor_sync(0xffffffffu, te, o));
+        double f[4] = {0, 0, 0, 0};
+        for (int i = lane; i < n; i += 32) {
+            const double d = imu[7 * i] - a[0];
+            f[0] += d * d;
+            for (int c = 0; c < 3; ++c) f[1 + c] += d * (imu[7 * i + 4 + c] - a[4 + c]);
+        }
+        for (int c = 0; c < 4; ++c) {
+            double v = f[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            f[c] = v;
+        }
+        if (lane == 0) {
+            for (int c = 0; c < 7; ++c) sums[c] = a[c];
+            sums[7] = te;
+            for (int c = 0; c < 4; ++c) fit[c] = f[c];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ok = 1;
+        double qm[4] = {dev->q[0], dev->q[1], dev->q[2], dev->q[3]};
+        quat_normalise(qm);
+        quat_to_R(qm, R);
+        const double inv_dt = 1.0 / dt;
+        double u_lin[3] = {0, 0, 0}, u_ang[3] = {0, 0, 0};
+        if (n > 0) {
+            const double tm = sums[0], tend = sums[7];
+            const double acc[3] = {sums[1], sums[2], sums[3]}, gyr[3] = {sums[4], sums[5], sums[6]};
+            const double slope_scale = fit[0] > 0.0 ? (tend - tm) / fit[0] : 0.0;
+            double gend[3];
+            for (int a = 0; a < 3; ++a) gend[a] = gyr[a] + fit[1 + a] * slope_scale;
+            double wm[3], half[3], full[3], Rh[9], Rf[9], Rmid[9], Rend[9], am[3], we[3];
+            mat3vec(R, gyr, wm);
+            for (int a = 0; a < 3; ++a) { half[a] = 0.5 * dt * wm[a]; full[a] = dt * wm[a]; }
+            so3_exp(half, Rh);
+            so3_exp(full, Rf);
+            mat3mul(Rh, R, Rmid);
+            mat3mul(Rf, R, Rend);
+            mat3vec(Rmid, acc, am);
+            mat3vec(Rend, gend, we);
+            for (int a = 0; a < 3; ++a) {
+                u_lin[a] = am[a] + (a == 2 ? -P.gravity : 0.0);
+                u_ang[a] = (we[a] - dev->w[a]) * inv_dt;
+            }
+        }
+        double wdt[3], qe[4], qn[4];
+        for (int a = 0; a < 3; ++a) {
+            vnew[a] = dev->v[a] + u_lin[a] * dt;
+            vnew[3 + a] = dev->w[a] + u_ang[a] * dt;
+            dev->pv[a] = vnew[a];
+            dev->pw[a] = vnew[3 + a];
+            dev->pt[a] = dev->t[a] + vnew[a] * dt;
+            wdt[a] = vnew[3 + a] * dt;
+        }
+        so3_exp(wdt, Rw);
+        quat_exp(wdt, qe);
+        quat_mul(qe, qm, qn);
+        quat_normalise(qn);
+        for (int a = 0; a < 4; ++a) dev->pq[a] = qn[a];
+        so3_jl(wdt, Jl);
+    }
+    __syncthreads();
+    // A, B, F
+    for (int e = tid; e < 144; e += blockDim.x) {
+        int i = e / 12, j = e % 12;
+        double f = 0.0;
+        if (i < 6 && j < 6) {
+            f = (i < 3 && j < 3) ? (i == j ? 1.0 : 0.0) : ((i >= 3 && j >= 3) ? Rw[3 * (i - 3) + j - 3] : 0.0);
+        } else if (i < 6 && j >= 6) {
+            int jj = j - 6;
+            f = (i < 3 && jj < 3) ? (i == jj ? dt : 0.0)
+                                  : ((i >= 3 && jj >= 3) ? Jl[3 * (i - 3) + jj - 3] * dt : 0.0);
+            B[6 * i + jj] = f;
+        } else if (i >= 6 && j >= 6) {
+            f = (i == j) ? 1.0 : 0.0;
+        }
+        F[e] = f;
+    }
+    __syncthreads();
+    block_matmul(F, dev->cov, T1, 12, 12, 12);
+    block_matmul_nt(T1, F, Sig, 12, 12, 12);
+    // transition noise
+    for (int e = tid; e < 144; e += blockDim.x) {
+        int i = e / 12, j = e % 12;
+        auto qv = [&](int k) { double s = P.sigma_vel[k < 3 ? 0 : 1]; return s * s; };
+        auto qp = [&](int k) { double s = P.sigma_pose[k < 3 ? 0 : 1]; return s * s; };
+        double add = 0.0;
+        if (i < 6 && j < 6) {
+            for (int k = 0; k < 6; ++k) add += B[6 * i + k] * qv(k) * B[6 * j + k];
+            if (i == j) add += qp(i);
+        } else if (i < 6 && j >= 6) {
+            add = B[6 * i + (j - 6)] * qv(j - 6);
+        } else if (i >= 6 && j < 6) {
+            add = B[6 * j + (i - 6)] * qv(i - 6);
+        } else if (i == j) {
+            add = qv(i - 6);
+        }
+        T1[e] = Sig[e] + add;
+    }
+    __syncthreads();
+    for (int e = tid; e < 144; e += blockDim.x) {
+        int i = e / 12, j = e % 12;
+        double m = 0.5 * (T1[e] + T1[12 * j + i]);
+        Sig[e] = m;
+        dev->pcov[e] = m;
+    }
+    __syncthreads();
+    for (int e = tid; e < 36; e += blockDim.x) {
+        int i = e / 6, j = e % 6;
+        dev->cov_pp[e] = Sig[12 * i + j];
+        Spp[e] = Sig[12 * i + j];
+        Spv[e] = Sig[12 * i + 6 + j];
+        Svp[e] = Sig[12 * (6 + i) + j];
+    }
+    __syncthreads();
+    if (!spd_inverse_block(Spp, dev->prec_pp, 6, Lch, rdg, &ok)) {
+        if (tid == 0) dev->flags |= FLAG_PRIOR_NOTPD;
+        return;
+    }
+    block_matmul(Svp, dev->prec_pp, Dm, 6, 6, 6);
+    block_matmul(Dm, Spv, T1, 6, 6, 6);
+    for (int e = tid; e < 36; e += blockDim.x) {
+        int i = e / 6, j = e % 6;
+        dev->D[e] = Dm[e];
+        double a = Sig[12 * (6 + i) + 6 + j] - T1[e];
+        double b = Sig[12 * (6 + j) + 6 + i] - T1[6 * j + i];
+        dev->cov_vel[e] = 0.5 * (a + b);
+    }
+    if (tid < 6) dev->xi[tid] = 0.0;
+    if (tid < 3) dev->cur_pose[tid] = dev->pt[tid];
+    if (tid < 4) dev->cur_pose[3 + tid] = dev->pq[tid];
+}
+
+// FP32 decision matrices of a pose (see PrepKind), computed once per pose by
+// the FP64 recipe so that no kernel block repeats the FP64 chain.
+// One thread.
+__device__ __forceinline__ void prep_mats(DevState* dev, int kind, const PoseArg& pose) {
+    switch (kind) {
+        case PREP_STATE:
+            mats_c2w(dev->t, dev->c2w);
+            mats_w2c(dev->t, dev->w2c);
+            break;
+        case PREP_AUX_C2W:
+            mats_c2w(pose.p, dev->aux);
+            break;
+        case PREP_AUX_REL:
+            mats_rel(pose.p, dev->anchor_pose, dev->aux);
+            break;
+        default:
+            mats_rel(dev->cur_pose, dev->anchor_pose, dev->rel);
+    }
+}
+
+}  // namespace prism

@@ -1,91 +1,8 @@
-// track.cu — the localisation objective of App. E.3 (Eq. pointtoplanelaplace)
-// reduced to normal equations, and its FP64 finish.
-//
-// One launch = one evaluation at the current pose.  Every thread walks a
-// grid-stride set of observed pixels and, for each kept pixel, forms four
-// residuals — point-to-plane against the nearest anchor pixel and three
-// photometric against the bilinear anchor colour — with their 6-D Jacobians
-// in the anchor camera frame, J' = [a_X, y_a x a_X] (a_X: gradient with
-// respect to the point in the anchor frame, y_a = R_a^T (R P)).  Sums of
-// w J'^T J', w J'^T r (IRLS weights w = 1/(b max(|r|, floor))), J'^T J'/b^2,
-// |r|/b and the pixel count are reduced in FP32 within a warp, in FP64
-// across warps, and written as one FP64 partial per block.  The last block
-// to finish (ticket counter, no waiting) adds the partials in a fixed order
-// — the result does not depend on block scheduling — rotates them to the
-// world frame (H = T H' T^T, T = diag(R_a, R_a)) and runs the mode's finish:
-//   TRACK_GN       one Gauss-Newton step in the prior's tangent coordinates:
-//                  (M^T H M + L) dxi = -(M^T g + L xi), M = diag(I, J_l(xi_theta)),
-//                  FP64 Cholesky; xi += dxi; pose = retract(xi)            (R15)
-//   TRACK_LAPLACE  Sigma = (2 Ht + M^-T L M^-1)^-1 (Sec. 4.1, R16), EMA (App.
-//                  F.2, R17), recombination with the velocity conditional
-//                  (Sec. 3.3.2, R23) into the new state
-//   TRACK_EXPORT   H, g, Ht, cost, count to dev->ne_out
-// Integer decisions (validity, nearest pixel, bilinear cell, gates) follow
-// the FP32 recipe with explicitly rounded intrinsics.
-#include <cuda/atomic>
-
-#include "kernels.h"
-#include "linalg64.cuh"
-#include "prism_dev.cuh"
+// track.cu — single-stream launches of the localisation passes; the device
+// body is in track_dev.cuh.
+#include "track_dev.cuh"
 
 namespace prism {
-
-namespace {
-
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kMaxPerLane = 16;   // partials per lane in the last block: grid <= 512
-
-template <int MODE>
-struct NV {
-    static constexpr int value = MODE == TRACK_GN ? 29 : (MODE == TRACK_LAPLACE ? 23 : 50);
-};
-
-// offsets into the per-thread accumulator
-template <int MODE>
-struct Layout {
-    static constexpr bool H = MODE != TRACK_LAPLACE;
-    static constexpr bool G = MODE != TRACK_LAPLACE;
-    static constexpr bool HT = MODE != TRACK_GN;
-    static constexpr int oH = 0;
-    static constexpr int oG = H ? 21 : 0;
-    static constexpr int oHT = oG + (G ? 6 : 0);
-    static constexpr int oCost = oHT + (HT ? 21 : 0);
-    static constexpr int oCount = oCost + 1;
-};
-
-template <int MODE>
-__device__ __forceinline__ void accumulate(float* acc, const float J[6], float r, float w, float ib2, float cost) {
-    using L = Layout<MODE>;
-    int e = 0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = i; j < 6; ++j, ++e) {
-            float jj = J[i] * J[j];
-            if (L::H) acc[L::oH + e] = fmaf(w, jj, acc[L::oH + e]);
-            if (L::HT) acc[L::oHT + e] = fmaf(ib2, jj, acc[L::oHT + e]);
-        }
-    if (L::G) {
-        float wr = w * r;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) acc[L::oG + i] = fmaf(wr, J[i], acc[L::oG + i]);
-    }
-    acc[L::oCost] += cost;
-}
-
-// A_world = T A' T^T with T = diag(Ra, Ra), one element per thread
-__device__ inline void rotate_to_world(const double* Ra, const double* Ap, double* Aw) {
-    for (int e = threadIdx.x; e < 36; e += blockDim.x) {
-        int i = e / 6, j = e % 6, bi = i / 3, bj = j / 3, ii = i % 3, jj = j % 3;
-        double s = 0.0;
-        for (int k = 0; k < 3; ++k)
-            for (int l = 0; l < 3; ++l) s += Ra[3 * ii + k] * Ap[6 * (3 * bi + k) + 3 * bj + l] * Ra[3 * jj + l];
-        Aw[e] = s;
-    }
-}
-
-}  // namespace
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_track(KParams P, const float* __restrict__ od,
@@ -97,422 +14,7 @@ __global__ void __launch_bounds__(kThreads) k_track(KParams P, const float* __re
                                                     unsigned int* __restrict__ counter,
                                                     DevStats* __restrict__ stats) {
     pdl_enter();
-    constexpr int N = NV<MODE>::value;
-    using L = Layout<MODE>;
-    __shared__ float sM[9], sb[3];
-    __shared__ float swarp[kWarps][N];
-    __shared__ double S[64];
-    __shared__ double sm[8][36];
-    __shared__ double sx[8][36];
-    __shared__ int s_last, s_ok;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 12) {
-        const float* mats = MODE == TRACK_EXPORT ? dev->aux : dev->rel;
-        if (tid < 9) sM[tid] = mats[tid];
-        else sb[tid - 9] = mats[tid];
-    }
-    __syncthreads();
-
-    float acc[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) acc[i] = 0.0f;
-    const int W = P.W, Hh = P.H, NP = W * Hh;
-    const float fW1 = (float)(W - 1), fH1 = (float)(Hh - 1), fW2 = (float)(W - 2), fH2 = (float)(Hh - 2);
-    for (int p = blockIdx.x * kThreads + tid; p < NP; p += gridDim.x * kThreads) {
-        if (!om[p]) continue;
-        const int u = p % W, v = p / W;
-        // ---- decisions (FP32 recipe) ----
-        float Pc[3], X[3];
-        backproject_rn(P, u, v, od[p], Pc);
-        affine_rn(sM, sb, Pc, X);
-        if (!(X[2] > 0.0f)) continue;
-        const float iz = __fdiv_rn(1.0f, X[2]);
-        const float up = __fmaf_rn(__fmul_rn(P.fx32, X[0]), iz, P.cx32);
-        const float vp = __fmaf_rn(__fmul_rn(P.fy32, X[1]), iz, P.cy32);
-        const float nu = floorf(__fadd_rn(up, 0.5f)), nv = floorf(__fadd_rn(vp, 0.5f));
-        if (!(nu >= 0.0f && nu <= fW1 && nv >= 0.0f && nv <= fH1)) continue;
-        const int iu = (int)nu, iv = (int)nv;
-        const float4 A = a0[iv * W + iu];
-        if (!(A.w > 0.0f)) continue;
-        const float bu = floorf(up), bv = floorf(vp);
-        if (!(bu >= 0.0f && bu <= fW2 && bv >= 0.0f && bv <= fH2)) continue;
-        const int b00 = (int)bv * W + (int)bu;
-        const float4 I00 = a1[b00], I10 = a1[b00 + 1], I01 = a1[b00 + W], I11 = a1[b00 + W + 1];
-        if (!(I00.w > 0.0f && I10.w > 0.0f && I01.w > 0.0f && I11.w > 0.0f)) continue;
-        const float aa = __fsub_rn(up, bu), cc = __fsub_rn(vp, bv);
-        float ph[3];
-        backproject_rn(P, iu, iv, A.w, ph);
-        const float e0 = __fsub_rn(ph[0], X[0]), e1 = __fsub_rn(ph[1], X[1]), e2 = __fsub_rn(ph[2], X[2]);
-        const float rgeo = __fmaf_rn(A.x, e0, __fmaf_rn(A.y, e1, __fmul_rn(A.z, e2)));
-        if (!(fabsf(rgeo) <= P.gate_geo32)) continue;
-        const float* oc = orgb + 3 * p;
-        float rr[3];
-        {
-            float t = lerp_rn(I00.x, I10.x, aa), b = lerp_rn(I01.x, I11.x, aa);
-            rr[0] = __fsub_rn(lerp_rn(t, b, cc), oc[0]);
-            t = lerp_rn(I00.y, I10.y, aa); b = lerp_rn(I01.y, I11.y, aa);
-            rr[1] = __fsub_rn(lerp_rn(t, b, cc), oc[1]);
-            t = lerp_rn(I00.z, I10.z, aa); b = lerp_rn(I01.z, I11.z, aa);
-            rr[2] = __fsub_rn(lerp_rn(t, b, cc), oc[2]);
-        }
-        if (!(fabsf(rr[0]) <= P.gate_rgb32 && fabsf(rr[1]) <= P.gate_rgb32 && fabsf(rr[2]) <= P.gate_rgb32))
-            continue;
-        // ---- values (FP32) ----
-        const float ya0 = X[0] - sb[0], ya1 = X[1] - sb[1], ya2 = X[2] - sb[2];
-        float J[6];
-        {   // point-to-plane: a_X = -n
-            const float ax = -A.x, ay = -A.y, az = -A.z;
-            J[0] = ax; J[1] = ay; J[2] = az;
-            J[3] = ya1 * az - ya2 * ay; J[4] = ya2 * ax - ya0 * az; J[5] = ya0 * ay - ya1 * ax;
-            const float ar = fabsf(rgeo);
-            const float w = 1.0f / (P.b_geo32 * fmaxf(ar, P.floor_geo32));
-            accumulate<MODE>(acc, J, rgeo, w, 1.0f / (P.b_geo32 * P.b_geo32), ar / P.b_geo32);
-        }
-        const float izz = iz * iz;
-        const float du0 = P.fx32 * iz, du2 = -P.fx32 * X[0] * izz;
-        const float dv1 = P.fy32 * iz, dv2 = -P.fy32 * X[1] * izz;
-        const float wb = 1.0f / (P.b_rgb32 * P.b_rgb32);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float i00 = c == 0 ? I00.x : (c == 1 ? I00.y : I00.z);
-            const float i10 = c == 0 ? I10.x : (c == 1 ? I10.y : I10.z);
-            const float i01 = c == 0 ? I01.x : (c == 1 ? I01.y : I01.z);
-            const float i11 = c == 0 ? I11.x : (c == 1 ? I11.y : I11.z);
-            const float gu = (1.0f - cc) * (i10 - i00) + cc * (i11 - i01);
-            const float gv = (1.0f - aa) * (i01 - i00) + aa * (i11 - i10);
-            const float ax = gu * du0, ay = gv * dv1, az = gu * du2 + gv * dv2;
-            J[0] = ax; J[1] = ay; J[2] = az;
-            J[3] = ya1 * az - ya2 * ay; J[4] = ya2 * ax - ya0 * az; J[5] = ya0 * ay - ya1 * ax;
-            const float ar = fabsf(rr[c]);
-            const float w = 1.0f / (P.b_rgb32 * fmaxf(ar, P.floor_rgb32));
-            accumulate<MODE>(acc, J, rr[c], w, wb, ar / P.b_rgb32);
-        }
-        acc[L::oCount] += 1.0f;
-    }
-
-    // ---- block reduction: FP32, in a fixed order (warp shuffles, then warps 0..7) ----
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        float s = warp_sum(acc[i]);
-        if (lane == 0) swarp[warp][i] = s;
-    }
-    __syncthreads();
-    if (tid < N) {   // partials are stored value-major: partials[v * pstride + block]
-        float s = swarp[0][tid];
-        for (int w = 1; w < kWarps; ++w) s += swarp[w][tid];
-        partials[(size_t)tid * pstride + blockIdx.x] = s;
-    }
-    __syncthreads();
-    // Ticket: the acq_rel atomic releases this block's partials (ordered
-    // before it by the barrier) and, for the last block, acquires everyone's.
-    if (tid == 0) {
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> ticket(*counter);
-        s_last = ticket.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-
-    // ---- last block ----
-    // Stage the FP64 state the finish needs into shared memory in one
-    // parallel round (GB300's FP64 pipe has ~64-cycle latency, so the tail
-    // is a latency chain; every global round trip on it costs ~600 cycles).
-    __shared__ double st[160];   // prec_pp 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55
-    if (tid < 36) st[tid] = dev->prec_pp[tid];
-    else if (tid < 42) st[tid] = dev->xi[tid - 36];
-    else if (tid < 49) st[tid] = dev->anchor_pose[tid - 42];
-    else if (tid < 53) st[tid] = dev->pq[tid - 49];
-    else if (tid < 56) st[tid] = dev->pt[tid - 53];
-    // Fixed-order sum of the partials: warp w takes values w, w + 8, ...;
-    // lane l adds blocks l, l + 32, ... into two alternating accumulators,
-    // then a fixed shuffle tree; the order never depends on scheduling.
-    // All of a lane's loads are issued before the first add (the loop below
-    // is fully unrolled; G <= 32 * kMaxPerLane is checked at launch).
-    // Warp w sums rows v = w, w + 8, ... (at most kRows); the loads of all its
-    // rows are issued before the first add.
-    // The sums stay FP32 (a GB300 SM retires about two FP64 adds per clock,
-    // so ~9,000 of them would dominate this block's tail; FP32 keeps the
-    // sums to ~1e-6 relative, far inside what a Gauss-Newton step or the
-    // Laplace covariance needs) and are widened to FP64 for the finish.
-    const int G = gridDim.x;
-    constexpr int kRows = (N + kWarps - 1) / kWarps;
-    float x[kRows][kMaxPerLane];
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) {
-        const int v = warp + kWarps * q;
-        const float* row = partials + (size_t)(v < N ? v : 0) * pstride;
-#pragma unroll
-        for (int j = 0; j < kMaxPerLane; ++j) {
-            const int b = lane + 32 * j;
-            x[q][j] = (v < N && b < G) ? __ldcg(row + b) : 0.0f;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) {
-        float s = x[q][0];
-#pragma unroll
-        for (int j = 1; j < kMaxPerLane; ++j) s += x[q][j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const int v = warp + kWarps * q;
-        if (lane == 0 && v < N) S[v] = (double)s;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        *counter = 0u;
-        if (stats) atomicAdd(&stats->track_pixels, (unsigned long long)S[L::oCount]);
-    }
-
-    // sm[0]: Ra; sm[1]: H' (sym); sm[2]: Ht' (sym); sm[3], sm[4]: world-frame H, Ht
-    double* Ra = sm[0];
-    if (tid == 0) quat_to_R(st + 45, Ra);
-    if (L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
-        const int e = tid - 32;
-        int i = 0, r = e;
-        while (r >= 6 - i) { r -= 6 - i; ++i; }
-        const int j = i + r;
-        sm[1][6 * i + j] = sm[1][6 * j + i] = S[L::oH + e];
-    }
-    if (L::HT && tid >= 64 && tid < 85) {
-        const int e = tid - 64;
-        int i = 0, r = e;
-        while (r >= 6 - i) { r -= 6 - i; ++i; }
-        const int j = i + r;
-        sm[2][6 * i + j] = sm[2][6 * j + i] = S[L::oHT + e];
-    }
-    __syncthreads();
-    double* Hw = sm[3];
-    double* Htw = sm[4];
-    if (MODE != TRACK_GN) {
-        if (L::H) rotate_to_world(Ra, sm[1], Hw);
-        if (L::HT) rotate_to_world(Ra, sm[2], Htw);
-        __syncthreads();
-    }
-
-    if (MODE == TRACK_EXPORT) {
-        if (tid < 36) {
-            dev->ne_out[tid] = Hw[tid];
-            dev->ne_out[42 + tid] = Htw[tid];
-        }
-        if (tid < 2) {
-            double gw[3];
-            const double* gp = S + L::oG + 3 * tid;
-            mat3vec(Ra, gp, gw);
-            for (int a = 0; a < 3; ++a) dev->ne_out[36 + 3 * tid + a] = gw[a];
-        }
-        if (tid == 0) {
-            dev->ne_out[78] = S[L::oCost];
-            dev->ne_out[79] = S[L::oCount];
-        }
-        return;
-    }
-
-    if (MODE == TRACK_GN) {
-        // In the anchor frame J' = J T^T... the tangent step dxi maps to the
-        // anchor-frame perturbation through C = T M = diag(Ra^T, Ra^T J_l(xi_theta)),
-        // so (M^T H M + L) = C^T H' C + L and M^T g = C^T g'.
-        double* Cm = sx[0];   // 3x3 blocks: C0 = Ra^T, C1 = Ra^T J_l
-        double* T1 = sx[1];
-        double* Hx = sx[2];
-        double* gx = sx[3];
-        double* Jl = sx[5];
-        if (tid < 9) {   // J_l(xi_theta) = I + b K + c K^2, one element per thread
-            const double* w = st + 39;
-            double a, b, c;
-            so3_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], a, b, c);
-            double K[9];
-            skew3(w, K);
-            const int i = tid / 3, j = tid % 3;
-            const double k2 = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-            Jl[tid] = (i == j ? 1.0 : 0.0) + b * K[tid] + c * k2;
-        }
-        __syncthreads();
-        if (tid < 9) {
-            const int i = tid / 3, j = tid % 3;
-            Cm[tid] = Ra[3 * j + i];
-            Cm[9 + tid] = Ra[i] * Jl[j] + Ra[3 + i] * Jl[3 + j] + Ra[6 + i] * Jl[6 + j];
-        }
-        __syncthreads();
-        if (tid < 36) {   // T1 = H' C  (C block diagonal)
-            const int i = tid / 6, j = tid % 6, bj = j / 3, jj = j % 3;
-            const double* Cb = Cm + 9 * bj;
-            T1[tid] = sm[1][6 * i + 3 * bj] * Cb[jj] + sm[1][6 * i + 3 * bj + 1] * Cb[3 + jj] +
-                      sm[1][6 * i + 3 * bj + 2] * Cb[6 + jj];
-        } else if (tid >= 64 && tid < 70) {   // gx = -(C^T g' + L xi)
-            const int i = tid - 64, bi = i / 3, ii = i % 3;
-            const double* Cb = Cm + 9 * bi;
-            const double* gp = S + L::oG + 3 * bi;
-            double lx = 0.0;
-            for (int k = 0; k < 6; ++k) lx += st[6 * i + k] * st[36 + k];
-            gx[i] = -(Cb[ii] * gp[0] + Cb[3 + ii] * gp[1] + Cb[6 + ii] * gp[2] + lx);
-        }
-        __syncthreads();
-        if (tid < 36) {   // Hx = C^T T1 + L, symmetrised
-            const int i = tid / 6, j = tid % 6, bi = i / 3, ii = i % 3, bj = j / 3, jj = j % 3;
-            const double* Ci = Cm + 9 * bi;
-            const double* Cj = Cm + 9 * bj;
-            const double a1 = Ci[ii] * T1[6 * (3 * bi) + j] + Ci[3 + ii] * T1[6 * (3 * bi + 1) + j] +
-                              Ci[6 + ii] * T1[6 * (3 * bi + 2) + j];
-            const double a2 = Cj[jj] * T1[6 * (3 * bj) + i] + Cj[3 + jj] * T1[6 * (3 * bj + 1) + i] +
-                              Cj[6 + jj] * T1[6 * (3 * bj + 2) + i];
-            Hx[tid] = 0.5 * (a1 + a2) + 0.5 * (st[tid] + st[6 * j + i]);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            // 6x6 FP64 Cholesky and both triangular solves, fully unrolled in
-            // registers (the chain is latency-bound on GB300's FP64 pipe)
-            double A[6][6], b[6], r[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                b[i] = gx[i];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) A[i][j] = Hx[6 * i + j];
-            }
-            bool pd = true;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                double d = A[j][j];
-#pragma unroll
-                for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-                pd = pd && d > 0.0 && isfinite(d);
-                const double rj = rsqrt(d);
-                r[j] = rj;
-#pragma unroll
-                for (int i = j + 1; i < 6; ++i) {
-                    double t = A[i][j];
-#pragma unroll
-                    for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
-                    A[i][j] = t * rj;
-                }
-            }
-            if (pd) {
-                double y[6], step[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    double t = b[i];
-#pragma unroll
-                    for (int k = 0; k < i; ++k) t -= A[i][k] * y[k];
-                    y[i] = t * r[i];
-                }
-#pragma unroll
-                for (int i = 5; i >= 0; --i) {
-                    double t = y[i];
-#pragma unroll
-                    for (int k = i + 1; k < 6; ++k) t -= A[k][i] * step[k];
-                    step[i] = t * r[i];
-                }
-                double xi[6], pose[7], qe[4];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) xi[i] = st[36 + i] + step[i];
-                quat_exp(xi + 3, qe);
-                quat_mul(qe, st + 49, pose + 3);
-                quat_normalise(pose + 3);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) pose[a] = st[53 + a] + xi[a];
-                float m[12];
-                mats_rel(pose, st + 42, m);
-#pragma unroll
-                for (int i = 0; i < 12; ++i) dev->rel[i] = m[i];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) dev->xi[i] = xi[i];
-#pragma unroll
-                for (int i = 0; i < 7; ++i) dev->cur_pose[i] = pose[i];
-            } else {
-                dev->flags |= FLAG_GN_NOTPD;
-            }
-        }
-        return;
-    }
-
-    // MODE == TRACK_LAPLACE: Sigma = (2 Ht + Mi^T L Mi)^-1, Mi = diag(I, J_l(xi_theta)^-1)
-    double* Mi = sx[0];
-    double* T1 = sx[1];
-    double* Hl = sx[2];
-    double* Sl = sx[3];
-    double* Sp = sx[4];
-    double* Dp = sx[5];
-    double* DS = sx[6];
-    double* Lf = sx[7];
-    __shared__ double rdg[6];
-    if (tid == 0) {
-        double Jli[9];
-        so3_jl_inv(st + 39, Jli);
-        for (int i = 0; i < 36; ++i) Mi[i] = 0.0;
-        for (int i = 0; i < 3; ++i) {
-            Mi[6 * i + i] = 1.0;
-            for (int j = 0; j < 3; ++j) Mi[6 * (3 + i) + 3 + j] = Jli[3 * i + j];
-        }
-    }
-    __syncthreads();
-    if (tid < 36) {   // T1 = L Mi
-        const int i = tid / 6, j = tid % 6;
-        double a = 0.0;
-        for (int k = 0; k < 6; ++k) a += st[6 * i + k] * Mi[6 * k + j];
-        T1[tid] = a;
-    }
-    __syncthreads();
-    if (tid < 36) {   // Hl = 2 Ht + Mi^T T1, symmetrised
-        const int i = tid / 6, j = tid % 6;
-        double a1 = 0.0, a2 = 0.0;
-        for (int k = 0; k < 6; ++k) { a1 += Mi[6 * k + i] * T1[6 * k + j]; a2 += Mi[6 * k + j] * T1[6 * k + i]; }
-        Hl[tid] = Htw[tid] + Htw[6 * j + i] + 0.5 * (a1 + a2);
-    }
-    __syncthreads();
-    if (!spd_inverse_block(Hl, Sl, 6, Lf, rdg, &s_ok)) {
-        if (tid == 0) {
-            dev->flags |= FLAG_LAPLACE_NOTPD;
-            dev->ne_out[78] = S[L::oCost];
-            dev->ne_out[79] = S[L::oCount];
-        }
-        return;
-    }
-    const bool first = dev->n_localised == 0;
-    if (tid < 36) {   // EMA (App. F.2) and D' = D Mi
-        const int i = tid / 6, j = tid % 6;
-        Sp[tid] = first ? Sl[tid] : P.ema * dev->cov[12 * i + j] + (1.0 - P.ema) * Sl[tid];
-        double a = 0.0;
-        for (int k = 0; k < 6; ++k) a += dev->D[6 * i + k] * Mi[6 * k + j];
-        Dp[tid] = a;
-    }
-    __syncthreads();
-    if (tid < 36) {   // DS = D' Sp
-        const int i = tid / 6, j = tid % 6;
-        double a = 0.0;
-        for (int k = 0; k < 6; ++k) a += Dp[6 * i + k] * Sp[6 * k + j];
-        DS[tid] = a;
-    } else if (tid >= 64 && tid < 70) {   // v = vbar + D xi
-        const int i = tid - 64;
-        double dv = 0.0;
-        for (int k = 0; k < 6; ++k) dv += dev->D[6 * i + k] * st[36 + k];
-        if (i < 3) dev->v[i] = dev->pv[i] + dv;
-        else dev->w[i - 3] = dev->pw[i - 3] + dv;
-    }
-    __syncthreads();
-    if (tid < 144) {   // cov = [[Sp, Sp D'^T], [D' Sp, D' Sp D'^T + S_vel]]
-        const int i = tid / 12, j = tid % 12;
-        double c;
-        if (i < 6 && j < 6) {
-            c = 0.5 * (Sp[6 * i + j] + Sp[6 * j + i]);
-        } else if (i >= 6 && j < 6) {
-            c = DS[6 * (i - 6) + j];
-        } else if (i < 6 && j >= 6) {
-            c = DS[6 * (j - 6) + i];
-        } else {
-            const int a = i - 6, b = j - 6;
-            double s1 = 0.0, s2 = 0.0;
-            for (int k = 0; k < 6; ++k) { s1 += DS[6 * a + k] * Dp[6 * b + k]; s2 += DS[6 * b + k] * Dp[6 * a + k]; }
-            c = 0.5 * (s1 + s2) + 0.5 * (dev->cov_vel[6 * a + b] + dev->cov_vel[6 * b + a]);
-        }
-        dev->cov[tid] = c;
-    }
-    if (tid == 0) {
-        for (int a = 0; a < 3; ++a) dev->t[a] = dev->cur_pose[a];
-        for (int a = 0; a < 4; ++a) dev->q[a] = dev->cur_pose[3 + a];
-        dev->n_localised += 1;
-        mats_c2w(dev->cur_pose, dev->c2w);
-        mats_w2c(dev->cur_pose, dev->w2c);
-        dev->ne_out[78] = S[L::oCost];
-        dev->ne_out[79] = S[L::oCount];
-    }
+    track_item<MODE>(P, od, orgb, om, a0, a1, dev, partials, pstride, counter, stats, blockIdx.x, gridDim.x);
 }
 
 // One wave: as many blocks as fit on the device at once (fewer partials for
@@ -537,14 +39,18 @@ int track_grid(const KParams& P, int max_blocks) {
     return g > 0 ? g : 1;
 }
 
+int track_launch_grid(const KParams& P, int mode, int max_blocks) {
+    const int grid = track_grid(P, max_blocks);
+    const int wave = mode == TRACK_GN ? wave_blocks<TRACK_GN>()
+                                      : (mode == TRACK_LAPLACE ? wave_blocks<TRACK_LAPLACE>() : wave_blocks<TRACK_EXPORT>());
+    return grid < wave ? grid : wave;
+}
+
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s) {
-    int grid = track_grid(P, max_blocks);
-    const int wave = mode == TRACK_GN ? wave_blocks<TRACK_GN>()
-                                      : (mode == TRACK_LAPLACE ? wave_blocks<TRACK_LAPLACE>() : wave_blocks<TRACK_EXPORT>());
-    if (grid > wave) grid = wave;
+    const int grid = track_launch_grid(P, mode, max_blocks);
     switch (mode) {
         case TRACK_GN:
             launch_pdl(k_track<TRACK_GN>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,

@@ -39,7 +39,8 @@ class Sequence:
         rng = np.random.default_rng(self.seed)
         duration = (max(w.n_frames, self.n_frames) + 1) / w.rate
         margin = 3.0 * w.voxel
-        self.traj = make_trajectory(w, rng, duration, margin)
+        period = w.n_frames / w.rate if w.periodic else None
+        self.traj = make_trajectory(w, rng, duration, margin, period)
         keep = self.traj.position(np.linspace(0, duration, max(200, int(duration * 40))))
         self.scene = make_scene(w, np.random.default_rng(self.seed + 1), keep)
         self.imu_t, self.imu_acc, self.imu_gyro = make_imu(

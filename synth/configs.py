@@ -45,6 +45,7 @@ class Workload:
     gyro_sigma: float = 0.002
     acc_bias_walk: float = 1e-3    # m/s^2 per sqrt(s)
     gyro_bias_walk: float = 1e-4   # rad/s per sqrt(s)
+    periodic: bool = False         # trajectory repeats every n_frames / rate seconds
 
     @property
     def voxel(self) -> float:

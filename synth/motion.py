@@ -84,26 +84,32 @@ class Trajectory:
 
 
 def make_trajectory(w: Workload, rng: np.random.Generator, duration: float,
-                    wall_margin: float) -> Trajectory:
+                    wall_margin: float, period: float | None = None) -> Trajectory:
+    """With `period`, every frequency drawn is moved to the nearest positive
+    multiple of 1/period, so the whole motion repeats with that period (the
+    random draws, and hence all other trajectories, are unchanged)."""
+    def per(f):
+        return f if period is None else np.maximum(1.0, np.round(f * period)) / period
+
     half = 0.5 * w.extent
     region = np.array([half - wall_margin - 1.0, half - wall_margin - 1.0,
                        0.3 if w.extent < 5 else 0.6])
     J = 3
     base_f = w.v_max / (2 * np.pi * region[:2].mean())
-    p_freq = base_f * rng.uniform(0.6, 1.5, size=(3, J))
+    p_freq = per(base_f * rng.uniform(0.6, 1.5, size=(3, J)))
     p_amp = rng.uniform(0.3, 1.0, size=(3, J))
     p_phase = rng.uniform(0, 2 * np.pi, size=(3, J))
     K = 2
-    r_freq = rng.uniform(0.05, 0.4, size=(3, K)) * max(1.0, w.w_max_deg / 120.0)
+    r_freq = per(rng.uniform(0.05, 0.4, size=(3, K)) * max(1.0, w.w_max_deg / 120.0))
     r_amp = np.stack([rng.uniform(0.5, 1.0, K), rng.uniform(0.05, 0.15, K),
                       rng.uniform(0.03, 0.08, K)])
     r_phase = rng.uniform(0, 2 * np.pi, size=(3, K))
     if w.jitter:
-        j_freq = rng.uniform(7.0, 13.0, size=(3, 2))
+        j_freq = per(rng.uniform(7.0, 13.0, size=(3, 2)))
         j_amp = np.full((3, 2), 0.002)
         j_phase = rng.uniform(0, 2 * np.pi, size=(3, 2))
         pj_amp = np.full((3, 2), 0.002)
-        pj_freq = rng.uniform(7.0, 13.0, size=(3, 2))
+        pj_freq = per(rng.uniform(7.0, 13.0, size=(3, 2)))
         pj_phase = rng.uniform(0, 2 * np.pi, size=(3, 2))
     else:
         j_freq = np.zeros((3, 1))

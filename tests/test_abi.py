@@ -89,3 +89,64 @@ def test_product_path_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text, f
+
+
+def test_serve_struct_layouts_and_defaults(lib, tmp_path):
+    src = tmp_path / "probe_serve.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "prism_serve.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(prism_serve_config), sizeof(prism_serve_result), sizeof(prism_serve_stats),
+         offsetof(prism_serve_result, state), offsetof(prism_serve_stats, kernel_launches));
+  return 0;
+}
+""")
+    exe = tmp_path / "probe_serve"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(x) for x in subprocess.check_output([str(exe)], text=True).split()]
+    assert vals == [C.sizeof(lib.ServeConfig), C.sizeof(lib.ServeResult), C.sizeof(lib.ServeStats),
+                    lib.ServeResult.state.offset, lib.ServeStats.kernel_launches.offset]
+    c = lib.ServeConfig()
+    lib.load().prism_serve_config_default(C.byref(c))
+    assert (c.max_slots, c.storage, c.n_gn, c.max_inflight, c.use_graph) == (32, lib.STORAGE_BF16, 10, 2, 1)
+
+
+def test_serve_stream_bytes_host_only(lib):
+    """The admission footprint is computed on the host (no device needed):
+    the six map planes dominate, bf16 halves them, and it grows with the
+    image."""
+    L = lib.load()
+
+    def cfg(n, w, h):
+        c = lib.Config()
+        L.prism_config_default(C.byref(c), n, 6.4, w, h)
+        return c
+
+    def pad(x):
+        return (x + 255) // 256 * 256
+
+    c = cfg(256, 640, 480)
+    f32 = L.prism_serve_stream_bytes(C.byref(c), lib.STORAGE_F32)
+    b16 = L.prism_serve_stream_bytes(C.byref(c), lib.STORAGE_BF16)
+    npad = 258 ** 3
+    assert f32 - b16 == 6 * (pad(4 * npad) - pad(2 * npad))
+    assert f32 > 6 * 4 * npad
+    assert L.prism_serve_stream_bytes(C.byref(cfg(256, 320, 240)), lib.STORAGE_F32) < f32
+    bad = cfg(60, 80, 60)
+    assert L.prism_serve_stream_bytes(C.byref(bad), lib.STORAGE_F32) == -1
+    assert L.prism_serve_stream_bytes(C.byref(c), 7) == -1
+
+
+def test_serve_create_rejects_bad_config_without_gpu_work(lib):
+    L = lib.load()
+    c = lib.ServeConfig()
+    L.prism_serve_config_default(C.byref(c))
+    c.max_slots = 65
+    h = C.c_void_p()
+    assert L.prism_serve_create(C.byref(c), C.byref(h)) == lib.EINVAL
+    assert b"max_slots" in L.prism_serve_last_error(None)
+    c.max_slots, c.n_gn = 8, 63
+    assert L.prism_serve_create(C.byref(c), C.byref(h)) == lib.EINVAL
+    assert L.prism_serve_destroy(None) == lib.EINVAL
