@@ -21,7 +21,11 @@ SOURCES = ["render.cu", "track.cu", "state.cu", "fuse.cu", "mapio.cu", "prism_ab
 HEADERS = ["prism_dev.cuh", "linalg64.cuh", "kernels.h", "render_dev.cuh", "track_dev.cuh", "fuse_dev.cuh",
            "state_dev.cuh", "serve.h", "host_util.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
+# -fmad=false: device code contracts no multiply-add on its own, so every
+# value is the rounding sequence its source spells out (fused operations are
+# written as fma / fmaf / intrinsics where wanted) whatever kernel a shared
+# device body is inlined into; host code likewise with -ffp-contract=off.
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 

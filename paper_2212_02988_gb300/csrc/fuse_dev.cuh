@@ -124,7 +124,7 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
         const float vl = var * P.upd_prec32;
         const float inv = 1.0f / (1.0f + vl);
         const bool edge = x == 0 || y == 0 || z == 0 || x == P.nx - 1 || y == P.ny - 1 || z == P.nz - 1;
-        const float mu1 = (mu + vl * f) * inv, var1 = var * inv;
+        const float mu1 = fmaf(vl, f, mu) * inv, var1 = var * inv;
         map_store<BF16>(M.occ, idx, mu1);
         map_store<BF16>(M.var_occ, idx, var1);
         if (edge) {
@@ -137,9 +137,9 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
             const float cl = cvar * P.upd_prec32;
             const float cinv = 1.0f / (1.0f + cl);
             const float* o = rgb + 3 * pix;
-            map_store<BF16>(M.r, idx, (map_load_rw<BF16>(M.r, idx) + cl * o[0]) * cinv);
-            map_store<BF16>(M.g, idx, (map_load_rw<BF16>(M.g, idx) + cl * o[1]) * cinv);
-            map_store<BF16>(M.b, idx, (map_load_rw<BF16>(M.b, idx) + cl * o[2]) * cinv);
+            map_store<BF16>(M.r, idx, fmaf(cl, o[0], map_load_rw<BF16>(M.r, idx)) * cinv);
+            map_store<BF16>(M.g, idx, fmaf(cl, o[1], map_load_rw<BF16>(M.g, idx)) * cinv);
+            map_store<BF16>(M.b, idx, fmaf(cl, o[2], map_load_rw<BF16>(M.b, idx)) * cinv);
             map_store<BF16>(M.var_rgb, idx, cvar * cinv);
             if (edge) {
                 void* planes[4] = {M.r, M.g, M.b, M.var_rgb};

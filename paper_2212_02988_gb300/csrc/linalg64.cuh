@@ -1,10 +1,17 @@
 // linalg64.cuh — small FP64 linear algebra for the state kernels (6x6 and
 // 12x12 matrices, row-major), run by one thread or spread over a block.
+// Multiply-adds are written as fma (the library is compiled without
+// implicit contraction), so each result is the same in every kernel.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace prism {
+
+// a0 b0 + a1 b1 + a2 b2 as fma(a0, b0, fma(a1, b1, a2 b2))
+__device__ __forceinline__ double fdot3(double a0, double b0, double a1, double b1, double a2, double b2) {
+    return fma(a0, b0, fma(a1, b1, a2 * b2));
+}
 
 __device__ inline void skew3(const double w[3], double K[9]) {
     K[0] = 0.0; K[1] = -w[2]; K[2] = w[1];
@@ -15,11 +22,11 @@ __device__ inline void skew3(const double w[3], double K[9]) {
 __device__ inline void mat3mul(const double* A, const double* B, double* C) {
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+            C[3 * i + j] = fdot3(A[3 * i], B[j], A[3 * i + 1], B[3 + j], A[3 * i + 2], B[6 + j]);
 }
 
 __device__ inline void mat3vec(const double* A, const double* x, double* y) {
-    for (int i = 0; i < 3; ++i) y[i] = A[3 * i] * x[0] + A[3 * i + 1] * x[1] + A[3 * i + 2] * x[2];
+    for (int i = 0; i < 3; ++i) y[i] = fdot3(A[3 * i], x[0], A[3 * i + 1], x[1], A[3 * i + 2], x[2]);
 }
 
 // Coefficients of Exp and J_l as functions of th^2.  For th < 1/4 they are
@@ -29,9 +36,12 @@ __device__ inline void mat3vec(const double* A, const double* x, double* y) {
 __device__ inline void so3_coeffs(double th2, double& a, double& b, double& c) {
     if (th2 < 0.0625) {
         const double x = th2;
-        a = 1.0 + x * (-1.0 / 6 + x * (1.0 / 120 + x * (-1.0 / 5040 + x * (1.0 / 362880 + x * (-1.0 / 39916800)))));
-        b = 0.5 + x * (-1.0 / 24 + x * (1.0 / 720 + x * (-1.0 / 40320 + x * (1.0 / 3628800 + x * (-1.0 / 479001600)))));
-        c = 1.0 / 6 + x * (-1.0 / 120 + x * (1.0 / 5040 + x * (-1.0 / 362880 + x * (1.0 / 39916800 + x * (-1.0 / 6227020800.0)))));
+        a = fma(x, fma(x, fma(x, fma(x, fma(x, -1.0 / 39916800, 1.0 / 362880), -1.0 / 5040), 1.0 / 120), -1.0 / 6), 1.0);
+        b = fma(x, fma(x, fma(x, fma(x, fma(x, -1.0 / 479001600, 1.0 / 3628800), -1.0 / 40320), 1.0 / 720), -1.0 / 24),
+                0.5);
+        c = fma(x, fma(x, fma(x, fma(x, fma(x, -1.0 / 6227020800.0, 1.0 / 39916800), -1.0 / 362880), 1.0 / 5040),
+                       -1.0 / 120),
+                1.0 / 6);
     } else {
         const double th = sqrt(th2), sn = sin(th), cs = cos(th);
         a = sn / th;
@@ -43,31 +53,31 @@ __device__ inline void so3_coeffs(double th2, double& a, double& b, double& c) {
 // Rodrigues: Exp(w) = I + a K + b K^2
 __device__ inline void so3_exp(const double w[3], double R[9]) {
     double a, b, c;
-    so3_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], a, b, c);
+    so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
     double K[9], K2[9];
     skew3(w, K);
     mat3mul(K, K, K2);
-    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+    for (int i = 0; i < 9; ++i) R[i] = fma(a, K[i], fma(b, K2[i], i % 4 == 0 ? 1.0 : 0.0));
 }
 
 // Left Jacobian of SO(3): I + b K + c K^2
 __device__ inline void so3_jl(const double w[3], double J[9]) {
     double a, b, c;
-    so3_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], a, b, c);
+    so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
     double K[9], K2[9];
     skew3(w, K);
     mat3mul(K, K, K2);
-    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0 ? 1.0 : 0.0) + b * K[i] + c * K2[i];
+    for (int i = 0; i < 9; ++i) J[i] = fma(b, K[i], fma(c, K2[i], i % 4 == 0 ? 1.0 : 0.0));
 }
 
 // Inverse left Jacobian of SO(3): I - K/2 + c K^2 with
 // c = 1/th^2 - (1 + cos th) / (2 th sin th); for th < 1/4 its Taylor series
 // 1/12 + th^2/720 + th^4/30240 + th^6/1209600 + th^8/47900160.
 __device__ inline void so3_jl_inv(const double w[3], double J[9]) {
-    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
     double c;
     if (th2 < 0.0625) {
-        c = 1.0 / 12 + th2 * (1.0 / 720 + th2 * (1.0 / 30240 + th2 * (1.0 / 1209600 + th2 * (1.0 / 47900160))));
+        c = fma(th2, fma(th2, fma(th2, fma(th2, 1.0 / 47900160, 1.0 / 1209600), 1.0 / 30240), 1.0 / 720), 1.0 / 12);
     } else {
         const double th = sqrt(th2);
         c = 1.0 / th2 - (1.0 + cos(th)) / (2.0 * th * sin(th));
@@ -75,18 +85,20 @@ __device__ inline void so3_jl_inv(const double w[3], double J[9]) {
     double K[9], K2[9];
     skew3(w, K);
     mat3mul(K, K, K2);
-    for (int i = 0; i < 9; ++i) J[i] = (i % 4 == 0 ? 1.0 : 0.0) - 0.5 * K[i] + c * K2[i];
+    for (int i = 0; i < 9; ++i) J[i] = fma(-0.5, K[i], fma(c, K2[i], i % 4 == 0 ? 1.0 : 0.0));
 }
 
 // Unit quaternion of Exp(w): (cos(th/2), sin(th/2)/th w), with the half-angle
 // coefficients from so3_coeffs' series at th/2.
 __device__ inline void quat_exp(const double w[3], double q[4]) {
-    const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
     double ch, sh;
     if (th2 < 0.25) {   // x = (th/2)^2 < 1/16
         const double x = 0.25 * th2;
-        ch = 1.0 + x * (-0.5 + x * (1.0 / 24 + x * (-1.0 / 720 + x * (1.0 / 40320 + x * (-1.0 / 3628800)))));
-        sh = 0.5 * (1.0 + x * (-1.0 / 6 + x * (1.0 / 120 + x * (-1.0 / 5040 + x * (1.0 / 362880 + x * (-1.0 / 39916800))))));
+        ch = fma(x, fma(x, fma(x, fma(x, fma(x, -1.0 / 3628800, 1.0 / 40320), -1.0 / 720), 1.0 / 24), -0.5), 1.0);
+        sh = 0.5 * fma(x, fma(x, fma(x, fma(x, fma(x, -1.0 / 39916800, 1.0 / 362880), -1.0 / 5040), 1.0 / 120),
+                              -1.0 / 6),
+                       1.0);
     } else {
         const double th = sqrt(th2);
         ch = cos(0.5 * th);
@@ -97,15 +109,15 @@ __device__ inline void quat_exp(const double w[3], double q[4]) {
 
 // Hamilton product a (x) b (w first).
 __device__ inline void quat_mul(const double* a, const double* b, double* q) {
-    q[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
-    q[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
-    q[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
-    q[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    q[0] = fma(a[0], b[0], -fma(a[1], b[1], fma(a[2], b[2], a[3] * b[3])));
+    q[1] = fma(a[0], b[1], fma(a[1], b[0], fma(a[2], b[3], -(a[3] * b[2]))));
+    q[2] = fma(a[0], b[2], fma(-a[1], b[3], fma(a[2], b[0], a[3] * b[1])));
+    q[3] = fma(a[0], b[3], fma(a[1], b[2], fma(-a[2], b[1], a[3] * b[0])));
 }
 
 // Normalised, with w >= 0.
 __device__ inline void quat_normalise(double* q) {
-    double r = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double r = rsqrt(fma(q[0], q[0], fdot3(q[1], q[1], q[2], q[2], q[3], q[3])));
     if (q[0] < 0.0) r = -r;
     for (int i = 0; i < 4; ++i) q[i] *= r;
 }
@@ -159,14 +171,14 @@ __device__ inline void quat_to_R(const double* q, double* R) {
 __device__ inline bool cholesky(double* A, double* rdiag, int n) {
     for (int j = 0; j < n; ++j) {
         double s = A[j * n + j];
-        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        for (int k = 0; k < j; ++k) s = fma(-A[j * n + k], A[j * n + k], s);
         if (!(s > 0.0) || !isfinite(s)) return false;
         const double r = rsqrt(s);
         A[j * n + j] = s * r;
         rdiag[j] = r;
         for (int i = j + 1; i < n; ++i) {
             double t = A[i * n + j];
-            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+            for (int k = 0; k < j; ++k) t = fma(-A[i * n + k], A[j * n + k], t);
             A[i * n + j] = t * r;
         }
     }
@@ -178,12 +190,12 @@ __device__ inline void chol_solve(const double* L, const double* rdiag, const do
     double y[12];
     for (int i = 0; i < n; ++i) {
         double s = b[i];
-        for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        for (int k = 0; k < i; ++k) s = fma(-L[i * n + k], y[k], s);
         y[i] = s * rdiag[i];
     }
     for (int i = n - 1; i >= 0; --i) {
         double s = y[i];
-        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        for (int k = i + 1; k < n; ++k) s = fma(-L[k * n + i], x[k], s);
         x[i] = s * rdiag[i];
     }
 }
@@ -224,7 +236,7 @@ __device__ inline void block_matmul(const double* A, const double* B, double* C,
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
         int i = e / m, j = e % m;
         double s = 0.0;
-        for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * m + j];
+        for (int l = 0; l < k; ++l) s = fma(A[i * k + l], B[l * m + j], s);
         C[e] = s;
     }
     __syncthreads();
@@ -235,7 +247,7 @@ __device__ inline void block_matmul_tn(const double* A, const double* B, double*
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
         int i = e / m, j = e % m;
         double s = 0.0;
-        for (int l = 0; l < k; ++l) s += A[l * n + i] * B[l * m + j];
+        for (int l = 0; l < k; ++l) s = fma(A[l * n + i], B[l * m + j], s);
         C[e] = s;
     }
     __syncthreads();
@@ -246,7 +258,7 @@ __device__ inline void block_matmul_nt(const double* A, const double* B, double*
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
         int i = e / m, j = e % m;
         double s = 0.0;
-        for (int l = 0; l < k; ++l) s += A[i * k + l] * B[j * k + l];
+        for (int l = 0; l < k; ++l) s = fma(A[i * k + l], B[j * k + l], s);
         C[e] = s;
     }
     __syncthreads();

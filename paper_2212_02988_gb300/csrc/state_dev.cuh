@@ -50,8 +50,8 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
         double f[4] = {0, 0, 0, 0};
         for (int i = lane; i < n; i += 32) {
             const double d = imu[7 * i] - a[0];
-            f[0] += d * d;
-            for (int c = 0; c < 3; ++c) f[1 + c] += d * (imu[7 * i + 4 + c] - a[4 + c]);
+            f[0] = fma(d, d, f[0]);
+            for (int c = 0; c < 3; ++c) f[1 + c] = fma(d, imu[7 * i + 4 + c] - a[4 + c], f[1 + c]);
         }
         for (int c = 0; c < 4; ++c) {
             double v = f[c];
@@ -77,7 +77,7 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
             const double acc[3] = {sums[1], sums[2], sums[3]}, gyr[3] = {sums[4], sums[5], sums[6]};
             const double slope_scale = fit[0] > 0.0 ? (tend - tm) / fit[0] : 0.0;
             double gend[3];
-            for (int a = 0; a < 3; ++a) gend[a] = gyr[a] + fit[1 + a] * slope_scale;
+            for (int a = 0; a < 3; ++a) gend[a] = fma(fit[1 + a], slope_scale, gyr[a]);
             double wm[3], half[3], full[3], Rh[9], Rf[9], Rmid[9], Rend[9], am[3], we[3];
             mat3vec(R, gyr, wm);
             for (int a = 0; a < 3; ++a) { half[a] = 0.5 * dt * wm[a]; full[a] = dt * wm[a]; }
@@ -94,11 +94,11 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
         }
         double wdt[3], qe[4], qn[4];
         for (int a = 0; a < 3; ++a) {
-            vnew[a] = dev->v[a] + u_lin[a] * dt;
-            vnew[3 + a] = dev->w[a] + u_ang[a] * dt;
+            vnew[a] = fma(u_lin[a], dt, dev->v[a]);
+            vnew[3 + a] = fma(u_ang[a], dt, dev->w[a]);
             dev->pv[a] = vnew[a];
             dev->pw[a] = vnew[3 + a];
-            dev->pt[a] = dev->t[a] + vnew[a] * dt;
+            dev->pt[a] = fma(vnew[a], dt, dev->t[a]);
             wdt[a] = vnew[3 + a] * dt;
         }
         so3_exp(wdt, Rw);
@@ -135,7 +135,7 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
         auto qp = [&](int k) { double s = P.sigma_pose[k < 3 ? 0 : 1]; return s * s; };
         double add = 0.0;
         if (i < 6 && j < 6) {
-            for (int k = 0; k < 6; ++k) add += B[6 * i + k] * qv(k) * B[6 * j + k];
+            for (int k = 0; k < 6; ++k) add = fma(B[6 * i + k] * qv(k), B[6 * j + k], add);
             if (i == j) add += qp(i);
         } else if (i < 6 && j >= 6) {
             add = B[6 * i + (j - 6)] * qv(j - 6);

@@ -84,7 +84,7 @@ __device__ inline void rotate_to_world(const double* Ra, const double* Ap, doubl
         int i = e / 6, j = e % 6, bi = i / 3, bj = j / 3, ii = i % 3, jj = j % 3;
         double s = 0.0;
         for (int k = 0; k < 3; ++k)
-            for (int l = 0; l < 3; ++l) s += Ra[3 * ii + k] * Ap[6 * (3 * bi + k) + 3 * bj + l] * Ra[3 * jj + l];
+            for (int l = 0; l < 3; ++l) s = fma(Ra[3 * ii + k] * Ap[6 * (3 * bi + k) + 3 * bj + l], Ra[3 * jj + l], s);
         Aw[e] = s;
     }
 }
@@ -171,7 +171,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         {   // point-to-plane: a_X = -n
             const float ax = -A.x, ay = -A.y, az = -A.z;
             J[0] = ax; J[1] = ay; J[2] = az;
-            J[3] = ya1 * az - ya2 * ay; J[4] = ya2 * ax - ya0 * az; J[5] = ya0 * ay - ya1 * ax;
+            J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
             const float ar = fabsf(rgeo);
             const float w = 1.0f / (P.b_geo32 * fmaxf(ar, P.floor_geo32));
             accumulate<MODE>(acc, J, rgeo, w, 1.0f / (P.b_geo32 * P.b_geo32), ar / P.b_geo32);
@@ -186,11 +186,11 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             const float i10 = c == 0 ? I10.x : (c == 1 ? I10.y : I10.z);
             const float i01 = c == 0 ? I01.x : (c == 1 ? I01.y : I01.z);
             const float i11 = c == 0 ? I11.x : (c == 1 ? I11.y : I11.z);
-            const float gu = (1.0f - cc) * (i10 - i00) + cc * (i11 - i01);
-            const float gv = (1.0f - aa) * (i01 - i00) + aa * (i11 - i10);
-            const float ax = gu * du0, ay = gv * dv1, az = gu * du2 + gv * dv2;
+            const float gu = fmaf(1.0f - cc, i10 - i00, cc * (i11 - i01));
+            const float gv = fmaf(1.0f - aa, i01 - i00, aa * (i11 - i10));
+            const float ax = gu * du0, ay = gv * dv1, az = fmaf(gu, du2, gv * dv2);
             J[0] = ax; J[1] = ay; J[2] = az;
-            J[3] = ya1 * az - ya2 * ay; J[4] = ya2 * ax - ya0 * az; J[5] = ya0 * ay - ya1 * ax;
+            J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
             const float ar = fabsf(rr[c]);
             const float w = 1.0f / (P.b_rgb32 * fmaxf(ar, P.floor_rgb32));
             accumulate<MODE>(acc, J, rr[c], w, wb, ar / P.b_rgb32);
@@ -326,42 +326,42 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         if (tid < 9) {   // J_l(xi_theta) = I + b K + c K^2, one element per thread
             const double* w = st + 39;
             double a, b, c;
-            so3_coeffs(w[0] * w[0] + w[1] * w[1] + w[2] * w[2], a, b, c);
+            so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
             double K[9];
             skew3(w, K);
             const int i = tid / 3, j = tid % 3;
-            const double k2 = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-            Jl[tid] = (i == j ? 1.0 : 0.0) + b * K[tid] + c * k2;
+            const double k2 = fdot3(K[3 * i], K[j], K[3 * i + 1], K[3 + j], K[3 * i + 2], K[6 + j]);
+            Jl[tid] = fma(b, K[tid], fma(c, k2, i == j ? 1.0 : 0.0));
         }
         __syncthreads();
         if (tid < 9) {
             const int i = tid / 3, j = tid % 3;
             Cm[tid] = Ra[3 * j + i];
-            Cm[9 + tid] = Ra[i] * Jl[j] + Ra[3 + i] * Jl[3 + j] + Ra[6 + i] * Jl[6 + j];
+            Cm[9 + tid] = fdot3(Ra[i], Jl[j], Ra[3 + i], Jl[3 + j], Ra[6 + i], Jl[6 + j]);
         }
         __syncthreads();
         if (tid < 36) {   // T1 = H' C  (C block diagonal)
             const int i = tid / 6, j = tid % 6, bj = j / 3, jj = j % 3;
             const double* Cb = Cm + 9 * bj;
-            T1[tid] = sm[1][6 * i + 3 * bj] * Cb[jj] + sm[1][6 * i + 3 * bj + 1] * Cb[3 + jj] +
-                      sm[1][6 * i + 3 * bj + 2] * Cb[6 + jj];
+            T1[tid] = fdot3(sm[1][6 * i + 3 * bj], Cb[jj], sm[1][6 * i + 3 * bj + 1], Cb[3 + jj],
+                            sm[1][6 * i + 3 * bj + 2], Cb[6 + jj]);
         } else if (tid >= 64 && tid < 70) {   // gx = -(C^T g' + L xi)
             const int i = tid - 64, bi = i / 3, ii = i % 3;
             const double* Cb = Cm + 9 * bi;
             const double* gp = S + L::oG + 3 * bi;
             double lx = 0.0;
-            for (int k = 0; k < 6; ++k) lx += st[6 * i + k] * st[36 + k];
-            gx[i] = -(Cb[ii] * gp[0] + Cb[3 + ii] * gp[1] + Cb[6 + ii] * gp[2] + lx);
+            for (int k = 0; k < 6; ++k) lx = fma(st[6 * i + k], st[36 + k], lx);
+            gx[i] = -fma(Cb[ii], gp[0], fma(Cb[3 + ii], gp[1], fma(Cb[6 + ii], gp[2], lx)));
         }
         __syncthreads();
         if (tid < 36) {   // Hx = C^T T1 + L, symmetrised
             const int i = tid / 6, j = tid % 6, bi = i / 3, ii = i % 3, bj = j / 3, jj = j % 3;
             const double* Ci = Cm + 9 * bi;
             const double* Cj = Cm + 9 * bj;
-            const double a1 = Ci[ii] * T1[6 * (3 * bi) + j] + Ci[3 + ii] * T1[6 * (3 * bi + 1) + j] +
-                              Ci[6 + ii] * T1[6 * (3 * bi + 2) + j];
-            const double a2 = Cj[jj] * T1[6 * (3 * bj) + i] + Cj[3 + jj] * T1[6 * (3 * bj + 1) + i] +
-                              Cj[6 + jj] * T1[6 * (3 * bj + 2) + i];
+            const double a1 = fdot3(Ci[ii], T1[6 * (3 * bi) + j], Ci[3 + ii], T1[6 * (3 * bi + 1) + j],
+                                    Ci[6 + ii], T1[6 * (3 * bi + 2) + j]);
+            const double a2 = fdot3(Cj[jj], T1[6 * (3 * bj) + i], Cj[3 + jj], T1[6 * (3 * bj + 1) + i],
+                                    Cj[6 + jj], T1[6 * (3 * bj + 2) + i]);
             Hx[tid] = 0.5 * (a1 + a2) + 0.5 * (st[tid] + st[6 * j + i]);
         }
         __syncthreads();
@@ -380,7 +380,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             for (int j = 0; j < 6; ++j) {
                 double d = A[j][j];
 #pragma unroll
-                for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+                for (int k = 0; k < j; ++k) d = fma(-A[j][k], A[j][k], d);
                 pd = pd && d > 0.0 && isfinite(d);
                 const double rj = rsqrt(d);
                 r[j] = rj;
@@ -388,7 +388,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                 for (int i = j + 1; i < 6; ++i) {
                     double t = A[i][j];
 #pragma unroll
-                    for (int k = 0; k < j; ++k) t -= A[i][k] * A[j][k];
+                    for (int k = 0; k < j; ++k) t = fma(-A[i][k], A[j][k], t);
                     A[i][j] = t * rj;
                 }
             }
@@ -398,14 +398,14 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                 for (int i = 0; i < 6; ++i) {
                     double t = b[i];
 #pragma unroll
-                    for (int k = 0; k < i; ++k) t -= A[i][k] * y[k];
+                    for (int k = 0; k < i; ++k) t = fma(-A[i][k], y[k], t);
                     y[i] = t * r[i];
                 }
 #pragma unroll
                 for (int i = 5; i >= 0; --i) {
                     double t = y[i];
 #pragma unroll
-                    for (int k = i + 1; k < 6; ++k) t -= A[k][i] * step[k];
+                    for (int k = i + 1; k < 6; ++k) t = fma(-A[k][i], step[k], t);
                     step[i] = t * r[i];
                 }
                 double xi[6], pose[7], qe[4];
@@ -454,14 +454,17 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (tid < 36) {   // T1 = L Mi
         const int i = tid / 6, j = tid % 6;
         double a = 0.0;
-        for (int k = 0; k < 6; ++k) a += st[6 * i + k] * Mi[6 * k + j];
+        for (int k = 0; k < 6; ++k) a = fma(st[6 * i + k], Mi[6 * k + j], a);
         T1[tid] = a;
     }
     __syncthreads();
     if (tid < 36) {   // Hl = 2 Ht + Mi^T T1, symmetrised
         const int i = tid / 6, j = tid % 6;
         double a1 = 0.0, a2 = 0.0;
-        for (int k = 0; k < 6; ++k) { a1 += Mi[6 * k + i] * T1[6 * k + j]; a2 += Mi[6 * k + j] * T1[6 * k + i]; }
+        for (int k = 0; k < 6; ++k) {
+            a1 = fma(Mi[6 * k + i], T1[6 * k + j], a1);
+            a2 = fma(Mi[6 * k + j], T1[6 * k + i], a2);
+        }
         Hl[tid] = Htw[tid] + Htw[6 * j + i] + 0.5 * (a1 + a2);
     }
     __syncthreads();
@@ -476,21 +479,21 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     const bool first = dev->n_localised == 0;
     if (tid < 36) {   // EMA (App. F.2) and D' = D Mi
         const int i = tid / 6, j = tid % 6;
-        Sp[tid] = first ? Sl[tid] : P.ema * dev->cov[12 * i + j] + (1.0 - P.ema) * Sl[tid];
+        Sp[tid] = first ? Sl[tid] : fma(P.ema, dev->cov[12 * i + j], (1.0 - P.ema) * Sl[tid]);
         double a = 0.0;
-        for (int k = 0; k < 6; ++k) a += dev->D[6 * i + k] * Mi[6 * k + j];
+        for (int k = 0; k < 6; ++k) a = fma(dev->D[6 * i + k], Mi[6 * k + j], a);
         Dp[tid] = a;
     }
     __syncthreads();
     if (tid < 36) {   // DS = D' Sp
         const int i = tid / 6, j = tid % 6;
         double a = 0.0;
-        for (int k = 0; k < 6; ++k) a += Dp[6 * i + k] * Sp[6 * k + j];
+        for (int k = 0; k < 6; ++k) a = fma(Dp[6 * i + k], Sp[6 * k + j], a);
         DS[tid] = a;
     } else if (tid >= 64 && tid < 70) {   // v = vbar + D xi
         const int i = tid - 64;
         double dv = 0.0;
-        for (int k = 0; k < 6; ++k) dv += dev->D[6 * i + k] * st[36 + k];
+        for (int k = 0; k < 6; ++k) dv = fma(dev->D[6 * i + k], st[36 + k], dv);
         if (i < 3) dev->v[i] = dev->pv[i] + dv;
         else dev->w[i - 3] = dev->pw[i - 3] + dv;
     }
@@ -507,7 +510,10 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         } else {
             const int a = i - 6, b = j - 6;
             double s1 = 0.0, s2 = 0.0;
-            for (int k = 0; k < 6; ++k) { s1 += DS[6 * a + k] * Dp[6 * b + k]; s2 += DS[6 * b + k] * Dp[6 * a + k]; }
+            for (int k = 0; k < 6; ++k) {
+                s1 = fma(DS[6 * a + k], Dp[6 * b + k], s1);
+                s2 = fma(DS[6 * b + k], Dp[6 * a + k], s2);
+            }
             c = 0.5 * (s1 + s2) + 0.5 * (dev->cov_vel[6 * a + b] + dev->cov_vel[6 * b + a]);
         }
         dev->cov[tid] = c;
