@@ -140,7 +140,7 @@ def measured_peaks():
 
 def render_source_hash():
     h = hashlib.sha256()
-    for f in ("render.cu", "prism_dev.cuh"):
+    for f in ("render.cu", "render_dev.cuh", "prism_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2212_02988_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
