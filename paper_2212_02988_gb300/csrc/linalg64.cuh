@@ -70,6 +70,17 @@ __device__ inline void so3_jl(const double w[3], double J[9]) {
     for (int i = 0; i < 9; ++i) J[i] = fma(b, K[i], fma(c, K2[i], i % 4 == 0 ? 1.0 : 0.0));
 }
 
+// Entry (i, j) of J_l(w) = I + b K + c K^2, K = [w]_x (the same operations
+// whichever thread or kernel evaluates it).
+__device__ inline double so3_jl_entry(const double w[3], int i, int j) {
+    double a, b, c;
+    so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
+    double K[9];
+    skew3(w, K);
+    const double k2 = fdot3(K[3 * i], K[j], K[3 * i + 1], K[3 + j], K[3 * i + 2], K[6 + j]);
+    return fma(b, K[3 * i + j], fma(c, k2, i == j ? 1.0 : 0.0));
+}
+
 // Inverse left Jacobian of SO(3): I - K/2 + c K^2 with
 // c = 1/th^2 - (1 + cos th) / (2 th sin th); for th < 1/4 its Taylor series
 // 1/12 + th^2/720 + th^4/30240 + th^6/1209600 + th^8/47900160.
@@ -166,99 +177,111 @@ __device__ inline void quat_to_R(const double* q, double* R) {
     R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
 }
 
-// In-place Cholesky of an n x n SPD matrix into its lower factor, with the
-// reciprocals of the diagonal in rdiag; false if not positive definite.
-__device__ inline bool cholesky(double* A, double* rdiag, int n) {
-    for (int j = 0; j < n; ++j) {
-        double s = A[j * n + j];
-        for (int k = 0; k < j; ++k) s = fma(-A[j * n + k], A[j * n + k], s);
-        if (!(s > 0.0) || !isfinite(s)) return false;
-        const double r = rsqrt(s);
-        A[j * n + j] = s * r;
-        rdiag[j] = r;
-        for (int i = j + 1; i < n; ++i) {
-            double t = A[i * n + j];
-            for (int k = 0; k < j; ++k) t = fma(-A[i * n + k], A[j * n + k], t);
-            A[i * n + j] = t * r;
+// Cholesky of an N x N SPD matrix held in registers (fully unrolled): the
+// lower factor replaces A, r holds the reciprocals of its diagonal; false if
+// not positive definite.
+template <int N>
+__device__ __forceinline__ bool cholesky_reg(double (&A)[N][N], double (&r)[N]) {
+    bool pd = true;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        double d = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fma(-A[j][k], A[j][k], d);
+        pd = pd && d > 0.0 && isfinite(d);
+        const double rj = rsqrt(d);
+        r[j] = rj;
+        A[j][j] = d * rj;
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            double t = A[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t = fma(-A[i][k], A[j][k], t);
+            A[i][j] = t * rj;
         }
     }
-    return true;
+    return pd;
 }
 
-// Solve L L^T x = b given the factor (lower triangle) and its diagonal reciprocals.
-__device__ inline void chol_solve(const double* L, const double* rdiag, const double* b, double* x, int n) {
-    double y[12];
-    for (int i = 0; i < n; ++i) {
-        double s = b[i];
-        for (int k = 0; k < i; ++k) s = fma(-L[i * n + k], y[k], s);
-        y[i] = s * rdiag[i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int k = i + 1; k < n; ++k) s = fma(-L[k * n + i], x[k], s);
-        x[i] = s * rdiag[i];
-    }
-}
-
-// Block-cooperative inverse of an SPD matrix (n <= 12) into Ainv (shared or
-// global): thread 0 factors into the shared scratch L/rdiag, then thread j
-// solves for column j; the result is symmetrised.  Every thread of the
-// block must call it.  Returns false (on every thread) if not PD.
-__device__ inline bool spd_inverse_block(const double* A, double* Ainv, int n, double* L, double* rdiag,
-                                         int* ok) {
+// Block-cooperative inverse of an N x N SPD matrix (A and Ainv in shared
+// or global memory): thread 0 factors in registers into the shared scratch
+// L / rdiag, then thread j solves for column j (unrolled); the result is
+// symmetrised.  Every thread of the block must call it.  Returns false (on
+// every thread) if not PD.
+template <int N>
+__device__ inline bool spd_inverse_block(const double* A, double* Ainv, double* L, double* rdiag, int* ok) {
     if (threadIdx.x == 0) {
-        for (int i = 0; i < n * n; ++i) L[i] = A[i];
-        *ok = cholesky(L, rdiag, n) ? 1 : 0;
+        double a[N][N], r[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) a[i][j] = A[i * N + j];
+        const bool pd = cholesky_reg<N>(a, r);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            rdiag[i] = r[i];
+#pragma unroll
+            for (int j = 0; j <= i; ++j) L[i * N + j] = a[i][j];
+        }
+        *ok = pd ? 1 : 0;
     }
     __syncthreads();
     const bool good = *ok != 0;
-    if (good && threadIdx.x < n) {
-        double e[12], x[12];
-        for (int i = 0; i < n; ++i) e[i] = (i == (int)threadIdx.x) ? 1.0 : 0.0;
-        chol_solve(L, rdiag, e, x, n);
-        for (int i = 0; i < n; ++i) Ainv[i * n + threadIdx.x] = x[i];
+    if (good && threadIdx.x < N) {
+        const int c = threadIdx.x;
+        double y[N], x[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = i == c ? 1.0 : 0.0;
+#pragma unroll
+            for (int k = 0; k < i; ++k) s = fma(-L[i * N + k], y[k], s);
+            y[i] = s * rdiag[i];
+        }
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+            double s = y[i];
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) s = fma(-L[k * N + i], x[k], s);
+            x[i] = s * rdiag[i];
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) Ainv[i * N + c] = x[i];
     }
     __syncthreads();
     if (good)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int i = e / n, j = e % n;
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const int i = e / N, j = e % N;
             if (i < j) {
-                const double m = 0.5 * (Ainv[i * n + j] + Ainv[j * n + i]);
-                Ainv[i * n + j] = Ainv[j * n + i] = m;
+                const double m = 0.5 * (Ainv[i * N + j] + Ainv[j * N + i]);
+                Ainv[i * N + j] = Ainv[j * N + i] = m;
             }
         }
     __syncthreads();
     return good;
 }
 
-// C = A (n x k) * B (k x m), computed by the threads of a block (element per thread).
-__device__ inline void block_matmul(const double* A, const double* B, double* C, int n, int k, int m) {
-    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
+// C = A (N x K) * B (K x M), computed by the threads of a block (element per
+// thread); operands in shared memory.
+template <int N, int K, int M>
+__device__ inline void block_matmul(const double* A, const double* B, double* C) {
+    for (int e = threadIdx.x; e < N * M; e += blockDim.x) {
+        const int i = e / M, j = e % M;
         double s = 0.0;
-        for (int l = 0; l < k; ++l) s = fma(A[i * k + l], B[l * m + j], s);
+#pragma unroll
+        for (int l = 0; l < K; ++l) s = fma(A[i * K + l], B[l * M + j], s);
         C[e] = s;
     }
     __syncthreads();
 }
 
-// C = A^T (A: k x n) * B (k x m)
-__device__ inline void block_matmul_tn(const double* A, const double* B, double* C, int n, int k, int m) {
-    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
+// C = A (N x K) * B^T (B: M x K)
+template <int N, int K, int M>
+__device__ inline void block_matmul_nt(const double* A, const double* B, double* C) {
+    for (int e = threadIdx.x; e < N * M; e += blockDim.x) {
+        const int i = e / M, j = e % M;
         double s = 0.0;
-        for (int l = 0; l < k; ++l) s = fma(A[l * n + i], B[l * m + j], s);
-        C[e] = s;
-    }
-    __syncthreads();
-}
-
-// C = A (n x k) * B^T (B: m x k)
-__device__ inline void block_matmul_nt(const double* A, const double* B, double* C, int n, int k, int m) {
-    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
-        double s = 0.0;
-        for (int l = 0; l < k; ++l) s = fma(A[i * k + l], B[j * k + l], s);
+#pragma unroll
+        for (int l = 0; l < K; ++l) s = fma(A[i * K + l], B[j * K + l], s);
         C[e] = s;
     }
     __syncthreads();

@@ -81,6 +81,11 @@ struct DevState {
     double ne_out[80];
     // render-adjoint pose gradient (world-frame perturbation)
     double grad_pose[6];
+    // Gauss-Newton tangent map of the current iterate, ready for the next
+    // pass's finish: C0 = R_a^T, C1 = R_a^T J_l(xi_theta) (3x3 each), and L xi
+    // (L = prior pose precision)
+    double gn_C[18];
+    double gn_Lxi[6];
     // FP32 decision matrices, each computed once per pose by the FP64 recipe:
     float c2w[12];             // state mean, camera -> world: R (9), centre (3)
     float w2c[12];             // state mean, world -> camera: M (9), b (3)

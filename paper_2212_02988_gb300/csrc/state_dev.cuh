@@ -26,12 +26,15 @@ namespace prism {
 // The prediction on one block of 256 threads.
 __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, const double* __restrict__ imu,
                                               int n, double dt) {
-    __shared__ double R[9], B[36], F[144], T1[144], Sig[144], Svp[36], Spv[36], Dm[36], Spp[36];
+    __shared__ double R[9], B[36], F[144], T1[144], Sig[144], Cv[144], Svp[36], Spv[36], Dm[36], Spp[36], Prec[36];
     __shared__ double Rw[9], Jl[9], vnew[6], Lch[36], rdg[6];
     __shared__ int ok;
     __shared__ double sums[8];   // mean t, acc (3), gyro (3), then t_end
     __shared__ double fit[4];    // sum dt^2, sum dt * dgyro (3)
     const int tid = threadIdx.x, lane = tid & 31;
+    // the previous covariance, staged once (the products below read it in
+    // dependent chains)
+    for (int e = tid; e < 144; e += blockDim.x) Cv[e] = dev->cov[e];
     // IMU window statistics on warp 0: lane l takes samples l, l + 32, ...;
     // the warp reduction order is fixed, so the result is deterministic.
     if (tid < 32) {
@@ -126,8 +129,8 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
         F[e] = f;
     }
     __syncthreads();
-    block_matmul(F, dev->cov, T1, 12, 12, 12);
-    block_matmul_nt(T1, F, Sig, 12, 12, 12);
+    block_matmul<12, 12, 12>(F, Cv, T1);
+    block_matmul_nt<12, 12, 12>(T1, F, Sig);
     // transition noise
     for (int e = tid; e < 144; e += blockDim.x) {
         int i = e / 12, j = e % 12;
@@ -162,14 +165,15 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
         Svp[e] = Sig[12 * (6 + i) + j];
     }
     __syncthreads();
-    if (!spd_inverse_block(Spp, dev->prec_pp, 6, Lch, rdg, &ok)) {
+    if (!spd_inverse_block<6>(Spp, Prec, Lch, rdg, &ok)) {
         if (tid == 0) dev->flags |= FLAG_PRIOR_NOTPD;
         return;
     }
-    block_matmul(Svp, dev->prec_pp, Dm, 6, 6, 6);
-    block_matmul(Dm, Spv, T1, 6, 6, 6);
+    block_matmul<6, 6, 6>(Svp, Prec, Dm);
+    block_matmul<6, 6, 6>(Dm, Spv, T1);
     for (int e = tid; e < 36; e += blockDim.x) {
         int i = e / 6, j = e % 6;
+        dev->prec_pp[e] = Prec[e];
         dev->D[e] = Dm[e];
         double a = Sig[12 * (6 + i) + 6 + j] - T1[e];
         double b = Sig[12 * (6 + j) + 6 + i] - T1[6 * j + i];
@@ -195,8 +199,24 @@ __device__ __forceinline__ void prep_mats(DevState* dev, int kind, const PoseArg
         case PREP_AUX_REL:
             mats_rel(pose.p, dev->anchor_pose, dev->aux);
             break;
-        default:
+        default: {
             mats_rel(dev->cur_pose, dev->anchor_pose, dev->rel);
+            // the Gauss-Newton tangent map at the current iterate (see
+            // track_dev.cuh): C0 = R_a^T, C1 = R_a^T J_l(xi_theta), L xi
+            double Ra[9], Jl[9];
+            quat_to_R(dev->anchor_pose + 3, Ra);
+            for (int e = 0; e < 9; ++e) Jl[e] = so3_jl_entry(dev->xi + 3, e / 3, e % 3);
+            for (int e = 0; e < 9; ++e) {
+                const int i = e / 3, j = e % 3;
+                dev->gn_C[e] = Ra[3 * j + i];
+                dev->gn_C[9 + e] = fdot3(Ra[i], Jl[j], Ra[3 + i], Jl[3 + j], Ra[6 + i], Jl[6 + j]);
+            }
+            for (int i = 0; i < 6; ++i) {
+                double lx = 0.0;
+                for (int k = 0; k < 6; ++k) lx = fma(dev->prec_pp[6 * i + k], dev->xi[k], lx);
+                dev->gn_Lxi[i] = lx;
+            }
+        }
     }
 }
 

@@ -224,12 +224,29 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     // Stage the FP64 state the finish needs into shared memory in one
     // parallel round (GB300's FP64 pipe has ~64-cycle latency, so the tail
     // is a latency chain; every global round trip on it costs ~600 cycles).
-    __shared__ double st[160];   // prec_pp 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55
+    // prec_pp 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55; Gauss-Newton
+    // also the tangent map C 56..73 and L xi 74..79; Laplace also D 56..91, pose
+    // block of the previous covariance 92..127, cov_vel 128..163, pv 164..166,
+    // pw 167..169
+    __shared__ double st[176];
+    __shared__ int s_nloc;
     if (tid < 36) st[tid] = dev->prec_pp[tid];
     else if (tid < 42) st[tid] = dev->xi[tid - 36];
     else if (tid < 49) st[tid] = dev->anchor_pose[tid - 42];
     else if (tid < 53) st[tid] = dev->pq[tid - 49];
     else if (tid < 56) st[tid] = dev->pt[tid - 53];
+    if (MODE == TRACK_GN) {
+        if (tid >= 56 && tid < 74) st[tid] = dev->gn_C[tid - 56];
+        else if (tid >= 74 && tid < 80) st[tid] = dev->gn_Lxi[tid - 74];
+    }
+    if (MODE == TRACK_LAPLACE) {
+        if (tid >= 56 && tid < 92) st[tid] = dev->D[tid - 56];
+        else if (tid >= 92 && tid < 128) st[tid] = dev->cov[12 * ((tid - 92) / 6) + (tid - 92) % 6];
+        else if (tid >= 128 && tid < 164) st[tid] = dev->cov_vel[tid - 128];
+        else if (tid >= 164 && tid < 167) st[tid] = dev->pv[tid - 164];
+        else if (tid >= 167 && tid < 170) st[tid] = dev->pw[tid - 167];
+        else if (tid == 170) s_nloc = dev->n_localised;
+    }
     // Fixed-order sum of the partials: warp w takes values w, w + 8, ...;
     // lane l adds blocks l, l + 32, ... into two alternating accumulators,
     // then a fixed shuffle tree; the order never depends on scheduling.
@@ -272,7 +289,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
 
     // sm[0]: Ra; sm[1]: H' (sym); sm[2]: Ht' (sym); sm[3], sm[4]: world-frame H, Ht
     double* Ra = sm[0];
-    if (tid == 0) quat_to_R(st + 45, Ra);
+    if (MODE != TRACK_GN && tid == 0) quat_to_R(st + 45, Ra);
     if (L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
         const int e = tid - 32;
         int i = 0, r = e;
@@ -317,29 +334,17 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (MODE == TRACK_GN) {
         // In the anchor frame J' = J T^T... the tangent step dxi maps to the
         // anchor-frame perturbation through C = T M = diag(Ra^T, Ra^T J_l(xi_theta)),
-        // so (M^T H M + L) = C^T H' C + L and M^T g = C^T g'.
-        double* Cm = sx[0];   // 3x3 blocks: C0 = Ra^T, C1 = Ra^T J_l
+        // so (M^T H M + L) = C^T H' C + L and M^T g = C^T g'.  C and L xi of the
+        // current iterate were prepared by the previous pass's finish (or by the
+        // pose matrices before the first pass), off this pass's critical path.
+        const double* Cm = st + 56;   // 3x3 blocks: C0 = Ra^T, C1 = Ra^T J_l
+        const double* Lx = st + 74;
         double* T1 = sx[1];
         double* Hx = sx[2];
         double* gx = sx[3];
-        double* Jl = sx[5];
-        if (tid < 9) {   // J_l(xi_theta) = I + b K + c K^2, one element per thread
-            const double* w = st + 39;
-            double a, b, c;
-            so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
-            double K[9];
-            skew3(w, K);
-            const int i = tid / 3, j = tid % 3;
-            const double k2 = fdot3(K[3 * i], K[j], K[3 * i + 1], K[3 + j], K[3 * i + 2], K[6 + j]);
-            Jl[tid] = fma(b, K[tid], fma(c, k2, i == j ? 1.0 : 0.0));
-        }
-        __syncthreads();
-        if (tid < 9) {
-            const int i = tid / 3, j = tid % 3;
-            Cm[tid] = Ra[3 * j + i];
-            Cm[9 + tid] = fdot3(Ra[i], Jl[j], Ra[3 + i], Jl[3 + j], Ra[6 + i], Jl[6 + j]);
-        }
-        __syncthreads();
+        double* xn = sx[4];
+        double* Jn = sx[5];
+        __shared__ int s_pd;
         if (tid < 36) {   // T1 = H' C  (C block diagonal)
             const int i = tid / 6, j = tid % 6, bj = j / 3, jj = j % 3;
             const double* Cb = Cm + 9 * bj;
@@ -349,9 +354,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             const int i = tid - 64, bi = i / 3, ii = i % 3;
             const double* Cb = Cm + 9 * bi;
             const double* gp = S + L::oG + 3 * bi;
-            double lx = 0.0;
-            for (int k = 0; k < 6; ++k) lx = fma(st[6 * i + k], st[36 + k], lx);
-            gx[i] = -fma(Cb[ii], gp[0], fma(Cb[3 + ii], gp[1], fma(Cb[6 + ii], gp[2], lx)));
+            gx[i] = -fma(Cb[ii], gp[0], fma(Cb[3 + ii], gp[1], fma(Cb[6 + ii], gp[2], Lx[i])));
         }
         __syncthreads();
         if (tid < 36) {   // Hx = C^T T1 + L, symmetrised
@@ -375,23 +378,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
 #pragma unroll
                 for (int j = 0; j < 6; ++j) A[i][j] = Hx[6 * i + j];
             }
-            bool pd = true;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                double d = A[j][j];
-#pragma unroll
-                for (int k = 0; k < j; ++k) d = fma(-A[j][k], A[j][k], d);
-                pd = pd && d > 0.0 && isfinite(d);
-                const double rj = rsqrt(d);
-                r[j] = rj;
-#pragma unroll
-                for (int i = j + 1; i < 6; ++i) {
-                    double t = A[i][j];
-#pragma unroll
-                    for (int k = 0; k < j; ++k) t = fma(-A[i][k], A[j][k], t);
-                    A[i][j] = t * rj;
-                }
-            }
+            const bool pd = cholesky_reg<6>(A, r);
             if (pd) {
                 double y[6], step[6];
 #pragma unroll
@@ -408,25 +395,41 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                     for (int k = i + 1; k < 6; ++k) t = fma(-A[k][i], step[k], t);
                     step[i] = t * r[i];
                 }
-                double xi[6], pose[7], qe[4];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) xi[i] = st[36 + i] + step[i];
-                quat_exp(xi + 3, qe);
-                quat_mul(qe, st + 49, pose + 3);
-                quat_normalise(pose + 3);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) pose[a] = st[53 + a] + xi[a];
-                float m[12];
-                mats_rel(pose, st + 42, m);
-#pragma unroll
-                for (int i = 0; i < 12; ++i) dev->rel[i] = m[i];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) dev->xi[i] = xi[i];
-#pragma unroll
-                for (int i = 0; i < 7; ++i) dev->cur_pose[i] = pose[i];
-            } else {
-                dev->flags |= FLAG_GN_NOTPD;
+                for (int i = 0; i < 6; ++i) xn[i] = st[36 + i] + step[i];
             }
+            s_pd = pd;
+        }
+        __syncthreads();
+        if (!s_pd) {
+            if (tid == 0) dev->flags |= FLAG_GN_NOTPD;
+            return;
+        }
+        if (tid == 0) {   // retraction and the FP32 matrices of the next pass
+            double pose[7], qe[4];
+            quat_exp(xn + 3, qe);
+            quat_mul(qe, st + 49, pose + 3);
+            quat_normalise(pose + 3);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) pose[a] = st[53 + a] + xn[a];
+            float m[12];
+            mats_rel(pose, st + 42, m);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) dev->rel[i] = m[i];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) dev->xi[i] = xn[i];
+#pragma unroll
+            for (int i = 0; i < 7; ++i) dev->cur_pose[i] = pose[i];
+        } else if (tid >= 32 && tid < 41) {   // meanwhile: the tangent map of the new iterate
+            const int e = tid - 32, i = e / 3, j = e % 3;
+            Jn[e] = so3_jl_entry(xn + 3, i, j);
+            __syncwarp(0x1ffu);
+            dev->gn_C[9 + e] = fdot3(Cm[3 * i], Jn[j], Cm[3 * i + 1], Jn[3 + j], Cm[3 * i + 2], Jn[6 + j]);
+        } else if (tid >= 64 && tid < 70) {
+            const int i = tid - 64;
+            double lx = 0.0;
+            for (int k = 0; k < 6; ++k) lx = fma(st[6 * i + k], xn[k], lx);
+            dev->gn_Lxi[i] = lx;
         }
         return;
     }
@@ -468,7 +471,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         Hl[tid] = Htw[tid] + Htw[6 * j + i] + 0.5 * (a1 + a2);
     }
     __syncthreads();
-    if (!spd_inverse_block(Hl, Sl, 6, Lf, rdg, &s_ok)) {
+    if (!spd_inverse_block<6>(Hl, Sl, Lf, rdg, &s_ok)) {
         if (tid == 0) {
             dev->flags |= FLAG_LAPLACE_NOTPD;
             dev->ne_out[78] = S[L::oCost];
@@ -476,12 +479,12 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         return;
     }
-    const bool first = dev->n_localised == 0;
+    const bool first = s_nloc == 0;
     if (tid < 36) {   // EMA (App. F.2) and D' = D Mi
         const int i = tid / 6, j = tid % 6;
-        Sp[tid] = first ? Sl[tid] : fma(P.ema, dev->cov[12 * i + j], (1.0 - P.ema) * Sl[tid]);
+        Sp[tid] = first ? Sl[tid] : fma(P.ema, st[92 + tid], (1.0 - P.ema) * Sl[tid]);
         double a = 0.0;
-        for (int k = 0; k < 6; ++k) a = fma(dev->D[6 * i + k], Mi[6 * k + j], a);
+        for (int k = 0; k < 6; ++k) a = fma(st[56 + 6 * i + k], Mi[6 * k + j], a);
         Dp[tid] = a;
     }
     __syncthreads();
@@ -493,9 +496,9 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     } else if (tid >= 64 && tid < 70) {   // v = vbar + D xi
         const int i = tid - 64;
         double dv = 0.0;
-        for (int k = 0; k < 6; ++k) dv = fma(dev->D[6 * i + k], st[36 + k], dv);
-        if (i < 3) dev->v[i] = dev->pv[i] + dv;
-        else dev->w[i - 3] = dev->pw[i - 3] + dv;
+        for (int k = 0; k < 6; ++k) dv = fma(st[56 + 6 * i + k], st[36 + k], dv);
+        if (i < 3) dev->v[i] = st[164 + i] + dv;
+        else dev->w[i - 3] = st[167 + i - 3] + dv;
     }
     __syncthreads();
     if (tid < 144) {   // cov = [[Sp, Sp D'^T], [D' Sp, D' Sp D'^T + S_vel]]
@@ -514,7 +517,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                 s1 = fma(DS[6 * a + k], Dp[6 * b + k], s1);
                 s2 = fma(DS[6 * b + k], Dp[6 * a + k], s2);
             }
-            c = 0.5 * (s1 + s2) + 0.5 * (dev->cov_vel[6 * a + b] + dev->cov_vel[6 * b + a]);
+            c = 0.5 * (s1 + s2) + 0.5 * (st[128 + 6 * a + b] + st[128 + 6 * b + a]);
         }
         dev->cov[tid] = c;
     }
