@@ -163,69 +163,96 @@ __device__ __forceinline__ void affine_rn(const float M[9], const float b[3], co
 }
 
 // ----------------------------------------------------------- FP64 pose recipe
-// Rotation of a unit quaternion (w, x, y, z), products formed first.  Poses
-// enter the library normalised (host poses at the C ABI with the FP64
+// Poses enter the library normalised (host poses at the C ABI with the FP64
 // operations of normalise_pose there; device poses by the value path), so
-// the recipe itself needs no square root or division.
-__device__ __forceinline__ void quat_to_R_rn(const double* q, double R[9]) {
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    double xx = __dmul_rn(x, x), yy = __dmul_rn(y, y), zz = __dmul_rn(z, z);
-    double xy = __dmul_rn(x, y), xz = __dmul_rn(x, z), yz = __dmul_rn(y, z);
-    double wx = __dmul_rn(w, x), wy = __dmul_rn(w, y), wz = __dmul_rn(w, z);
-    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(yy, zz)));
-    R[1] = __dmul_rn(2.0, __dsub_rn(xy, wz));
-    R[2] = __dmul_rn(2.0, __dadd_rn(xz, wy));
-    R[3] = __dmul_rn(2.0, __dadd_rn(xy, wz));
-    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, zz)));
-    R[5] = __dmul_rn(2.0, __dsub_rn(yz, wx));
-    R[6] = __dmul_rn(2.0, __dsub_rn(xz, wy));
-    R[7] = __dmul_rn(2.0, __dadd_rn(yz, wx));
-    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(xx, yy)));
-}
+// the recipe needs no square root or division.  R(q) of a unit quaternion
+// (w, x, y, z), products formed first:
+//   R = [1 - 2(yy + zz), 2(xy - wz), 2(xz + wy);
+//        2(xy + wz), 1 - 2(xx + zz), 2(yz - wx);
+//        2(xz - wy), 2(yz + wx), 1 - 2(xx + yy)]
+// rounded once to FP32 for the camera-to-world matrices, and combined for
+//   world-to-camera  M = R^T, b = -((R0i t0 + R1i t1) + R2i t2),
+//   pose -> anchor   M = Ra^T R, b = Ra^T (t - ta)  (sums in the order k = 0, 1, 2),
+// each operation rounded once (dot3_rn), then rounded to FP32.
 
 // (a0*b0 + a1*b1) + a2*b2, each operation rounded
 __device__ __forceinline__ double dot3_rn(double a0, double b0, double a1, double b1, double a2, double b2) {
     return __dadd_rn(__dadd_rn(__dmul_rn(a0, b0), __dmul_rn(a1, b1)), __dmul_rn(a2, b2));
 }
 
-// FP32 camera-to-world rotation and centre of a pose (render set-up):
-// out = (R (9, row-major), t (3)).
-__device__ __forceinline__ void mats_c2w(const double* pose, float* out) {
-    double R[9];
-    quat_to_R_rn(pose + 3, R);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) out[i] = (float)R[i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) out[9 + a] = (float)pose[a];
+// ------------------------------------------------- warp-parallel pose recipe
+// GB300's FP64 pipe retires about one warp instruction per 64 cycles per
+// SM sub-partition whatever the number of active lanes, so the FP64 chains
+// below put independent entries into the lanes of one warp: every lane runs
+// the same branch-free instruction stream on its own operands (selected by
+// lane), and each entry is computed with exactly the operations of the
+// recipe above.
+
+// Entry e (0..8, row-major) of R(q): 2 (p + s r) with products
+// p, r of two quaternion components, s = +-1, and 1 - that on the diagonal
+// (a - b is evaluated as a + (-b), which IEEE rounds identically).
+__device__ __forceinline__ double quat_R_entry_rn(double w, double x, double y, double z, int e) {
+    // per entry: component indices (a, b, c, d) of p = q_a q_b, r = q_c q_d, sign of r, diagonal
+    // 0: yy+zz D; 1: xy-wz; 2: xz+wy; 3: xy+wz; 4: xx+zz D; 5: yz-wx; 6: xz-wy; 7: yz+wx; 8: xx+yy D
+    constexpr uint32_t kA = 0x19956u, kB = 0x1fdbau, kC = 0x20303u, kD = 0x267efu;   // 2 bits an entry
+    constexpr uint32_t kNeg = 0x62u, kDiag = 0x111u;                                   // 1 bit an entry
+    const int sh = 2 * e;
+    auto pick = [&](uint32_t tab) {
+        const uint32_t k = (tab >> sh) & 3u;
+        return k == 0u ? w : (k == 1u ? x : (k == 2u ? y : z));
+    };
+    const double p = __dmul_rn(pick(kA), pick(kB));
+    const double r = __dmul_rn(pick(kC), pick(kD));
+    const double u = __dmul_rn(2.0, __dadd_rn(p, ((kNeg >> e) & 1u) ? -r : r));
+    const double du = __dsub_rn(1.0, u);
+    return ((kDiag >> e) & 1u) ? du : u;
 }
 
-// FP32 world-to-camera transform of a pose: M = R^T, b = -((R0i t0 + R1i t1) + R2i t2).
-__device__ __forceinline__ void mats_w2c(const double* pose, float* out) {
-    double R[9];
-    quat_to_R_rn(pose + 3, R);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) out[3 * i + j] = (float)R[3 * j + i];
-        out[9 + i] = (float)(-dot3_rn(R[i], pose[0], R[3 + i], pose[1], R[6 + i], pose[2]));
-    }
+// The FP32 camera-to-world, world-to-camera and pose-to-anchor matrices of
+// the recipe above (R then t; M then b), computed by the 32
+// lanes of one warp (all must call; lanes outside the outputs compute and
+// discard).  out entries are written by lanes 0..11.
+__device__ __forceinline__ void warp_mats_c2w(const double* pose, float* out) {
+    const int lane = threadIdx.x & 31;
+    const double Re = quat_R_entry_rn(pose[3], pose[4], pose[5], pose[6], lane < 9 ? lane : 0);
+    if (lane < 9) out[lane] = (float)Re;
+    else if (lane < 12) out[lane] = (float)pose[lane - 9];
 }
 
-// FP32 transform from the camera at `pose` to the camera at `anchor`:
-// M = Ra^T R, b = Ra^T (t - ta).
-__device__ __forceinline__ void mats_rel(const double* pose, const double* anchor, float* out) {
-    double R[9], Ra[9], d[3];
-    quat_to_R_rn(pose + 3, R);
-    quat_to_R_rn(anchor + 3, Ra);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            out[3 * i + j] = (float)dot3_rn(Ra[i], R[j], Ra[3 + i], R[3 + j], Ra[6 + i], R[6 + j]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = __dsub_rn(pose[a], anchor[a]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) out[9 + i] = (float)dot3_rn(Ra[i], d[0], Ra[3 + i], d[1], Ra[6 + i], d[2]);
+__device__ __forceinline__ void warp_mats_w2c(const double* pose, float* out) {
+    const int lane = threadIdx.x & 31;
+    const double Re = quat_R_entry_rn(pose[3], pose[4], pose[5], pose[6], lane < 9 ? lane : 0);
+    // out[3i + j] = R[3j + i]; out[9 + i] = -dot3(R[i], t0, R[3 + i], t1, R[6 + i], t2)
+    const int e = lane < 9 ? 3 * (lane % 3) + lane / 3 : 0;
+    const double tr = __shfl_sync(0xffffffffu, Re, e);
+    const int i = lane >= 9 && lane < 12 ? lane - 9 : 0;
+    const double a0 = __shfl_sync(0xffffffffu, Re, i), a1 = __shfl_sync(0xffffffffu, Re, 3 + i),
+                 a2 = __shfl_sync(0xffffffffu, Re, 6 + i);
+    const double bv = -dot3_rn(a0, pose[0], a1, pose[1], a2, pose[2]);
+    if (lane < 9) out[lane] = (float)tr;
+    else if (lane < 12) out[lane] = (float)bv;
+}
+
+__device__ __forceinline__ void warp_mats_rel(const double* pose, const double* anchor, float* out) {
+    const int lane = threadIdx.x & 31;
+    // lanes 0..8: R(pose) entries; lanes 9..17: R(anchor) entries
+    const bool pa = lane < 9;
+    const double* q = pa ? pose + 3 : anchor + 3;
+    const double Re = quat_R_entry_rn(q[0], q[1], q[2], q[3], pa ? lane : (lane < 18 ? lane - 9 : 0));
+    // element e = lane (< 12): i = row; M[i][j] = dot3(Ra[i], R[j], Ra[3+i], R[3+j], Ra[6+i], R[6+j]),
+    // b[i] = dot3(Ra[i], d0, Ra[3+i], d1, Ra[6+i], d2) with d = t - ta
+    const int e = lane < 12 ? lane : 0;
+    const int i = e < 9 ? e / 3 : e - 9, j = e % 3;
+    const double a0 = __shfl_sync(0xffffffffu, Re, 9 + i), a1 = __shfl_sync(0xffffffffu, Re, 12 + i),
+                 a2 = __shfl_sync(0xffffffffu, Re, 15 + i);
+    const double r0 = __shfl_sync(0xffffffffu, Re, j), r1 = __shfl_sync(0xffffffffu, Re, 3 + j),
+                 r2 = __shfl_sync(0xffffffffu, Re, 6 + j);
+    const bool mrow = e < 9;
+    const double b0 = mrow ? r0 : __dsub_rn(pose[0], anchor[0]);
+    const double b1 = mrow ? r1 : __dsub_rn(pose[1], anchor[1]);
+    const double b2 = mrow ? r2 : __dsub_rn(pose[2], anchor[2]);
+    const double v = dot3_rn(a0, b0, a1, b1, a2, b2);
+    if (lane < 12) out[lane] = (float)v;
 }
 
 // --------------------------------------------------------- warp helpers

@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(256) kb_predict(const SlotDesc* __restrict__ s
     const SlotDesc& S = slots[m.slot];
     predict_block(S.P, S.dev, imu + 7 * m.imu_off, m.n_imu, m.dt);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         PoseArg pa{};
-        prep_mats(S.dev, PREP_REL, pa);
+        prep_mats_warp(S.dev, PREP_REL, pa);
     }
 }
 

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(256) k_predict(KParams P, DevState* dev, const
 
 __global__ void k_prep(DevState* dev, int kind, PoseArg pose) {
     pdl_enter();
-    if (threadIdx.x == 0) prep_mats(dev, kind, pose);
+    prep_mats_warp(dev, kind, pose);   // one warp
 }
 
 cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s) {

@@ -185,36 +185,46 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
 }
 
 // FP32 decision matrices of a pose (see PrepKind), computed once per pose by
-// the FP64 recipe so that no kernel block repeats the FP64 chain.
-// One thread.
-__device__ __forceinline__ void prep_mats(DevState* dev, int kind, const PoseArg& pose) {
+// the FP64 recipe so that no kernel block repeats the FP64 chain; for
+// PREP_REL also the Gauss-Newton tangent map of the current iterate (see
+// track_dev.cuh).  All 32 lanes of one warp call it; entries go one a lane.
+__device__ __forceinline__ void prep_mats_warp(DevState* dev, int kind, const PoseArg& pose) {
+    const int lane = threadIdx.x & 31;
     switch (kind) {
         case PREP_STATE:
-            mats_c2w(dev->t, dev->c2w);
-            mats_w2c(dev->t, dev->w2c);
+            warp_mats_c2w(dev->t, dev->c2w);
+            warp_mats_w2c(dev->t, dev->w2c);
             break;
         case PREP_AUX_C2W:
-            mats_c2w(pose.p, dev->aux);
+            warp_mats_c2w(pose.p, dev->aux);
             break;
         case PREP_AUX_REL:
-            mats_rel(pose.p, dev->anchor_pose, dev->aux);
+            warp_mats_rel(pose.p, dev->anchor_pose, dev->aux);
             break;
         default: {
-            mats_rel(dev->cur_pose, dev->anchor_pose, dev->rel);
-            // the Gauss-Newton tangent map at the current iterate (see
-            // track_dev.cuh): C0 = R_a^T, C1 = R_a^T J_l(xi_theta), L xi
-            double Ra[9], Jl[9];
-            quat_to_R(dev->anchor_pose + 3, Ra);
-            for (int e = 0; e < 9; ++e) Jl[e] = so3_jl_entry(dev->xi + 3, e / 3, e % 3);
-            for (int e = 0; e < 9; ++e) {
-                const int i = e / 3, j = e % 3;
-                dev->gn_C[e] = Ra[3 * j + i];
-                dev->gn_C[9 + e] = fdot3(Ra[i], Jl[j], Ra[3 + i], Jl[3 + j], Ra[6 + i], Jl[6 + j]);
+            warp_mats_rel(dev->cur_pose, dev->anchor_pose, dev->rel);
+            // C0 = Ra^T, C1 = Ra^T J_l(xi_theta): lanes 0..8 hold Ra entries,
+            // lanes 9..17 J_l entries; lanes 18..23 L xi
+            const double* qa = dev->anchor_pose + 3;
+            const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0);
+            const double ra = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], e);
+            const double jl = so3_jl_entry(dev->xi + 3, e / 3, e % 3);
+            const double v = lane < 9 ? ra : jl;
+            const int i = e / 3, j = e % 3;
+            const double ra_i0 = __shfl_sync(0xffffffffu, v, i), ra_i1 = __shfl_sync(0xffffffffu, v, 3 + i),
+                         ra_i2 = __shfl_sync(0xffffffffu, v, 6 + i);
+            const double jl_0j = __shfl_sync(0xffffffffu, v, 9 + j), jl_1j = __shfl_sync(0xffffffffu, v, 12 + j),
+                         jl_2j = __shfl_sync(0xffffffffu, v, 15 + j);
+            const double c0 = __shfl_sync(0xffffffffu, v, 3 * j + i);
+            if (lane < 9) {
+                dev->gn_C[lane] = c0;
+                dev->gn_C[9 + lane] = fdot3(ra_i0, jl_0j, ra_i1, jl_1j, ra_i2, jl_2j);
             }
-            for (int i = 0; i < 6; ++i) {
+            if (lane >= 18 && lane < 24) {
+                const int r = lane - 18;
                 double lx = 0.0;
-                for (int k = 0; k < 6; ++k) lx = fma(dev->prec_pp[6 * i + k], dev->xi[k], lx);
-                dev->gn_Lxi[i] = lx;
+                for (int k = 0; k < 6; ++k) lx = fma(dev->prec_pp[6 * r + k], dev->xi[k], lx);
+                dev->gn_Lxi[r] = lx;
             }
         }
     }

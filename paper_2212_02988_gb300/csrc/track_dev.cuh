@@ -368,58 +368,108 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             Hx[tid] = 0.5 * (a1 + a2) + 0.5 * (st[tid] + st[6 * j + i]);
         }
         __syncthreads();
-        if (tid == 0) {
-            // 6x6 FP64 Cholesky and both triangular solves, fully unrolled in
-            // registers (the chain is latency-bound on GB300's FP64 pipe)
-            double A[6][6], b[6], r[6];
+        if (warp == 0) {
+            // 6x6 FP64 Cholesky (right-looking) and both triangular solves on one
+            // warp, lane i < 6 holding row i: each step is one warp instruction
+            // for all rows.  Every element accumulates its terms in the order of
+            // the left-looking recipe (k increasing); the back substitution
+            // subtracts in the order the steps become known (k decreasing).
+            __shared__ double Ls[36];
+            double a[6], r[6];
+            const int row = lane < 6 ? lane : 5;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                b[i] = gx[i];
+            for (int j = 0; j < 6; ++j) a[j] = Hx[6 * row + j];
+            double bi = gx[row];
+            bool pd = true;
 #pragma unroll
-                for (int j = 0; j < 6; ++j) A[i][j] = Hx[6 * i + j];
-            }
-            const bool pd = cholesky_reg<6>(A, r);
-            if (pd) {
-                double y[6], step[6];
+            for (int j = 0; j < 6; ++j) {
+                const double d = __shfl_sync(0xffffffffu, a[j], j);
+                pd = pd && d > 0.0 && isfinite(d);
+                const double rj = rsqrt(d);
+                r[j] = rj;
+                if (lane > j) a[j] = a[j] * rj;   // L_ij
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    double t = b[i];
-#pragma unroll
-                    for (int k = 0; k < i; ++k) t = fma(-A[i][k], y[k], t);
-                    y[i] = t * r[i];
+                for (int m = j + 1; m < 6; ++m) {
+                    const double lmj = __shfl_sync(0xffffffffu, a[j], m);
+                    if (lane >= m) a[m] = fma(-a[j], lmj, a[m]);
                 }
-#pragma unroll
-                for (int i = 5; i >= 0; --i) {
-                    double t = y[i];
-#pragma unroll
-                    for (int k = i + 1; k < 6; ++k) t = fma(-A[k][i], step[k], t);
-                    step[i] = t * r[i];
-                }
-#pragma unroll
-                for (int i = 0; i < 6; ++i) xn[i] = st[36 + i] + step[i];
             }
-            s_pd = pd;
+            // forward: y_j = b_j r_j, then b_i -= L_ij y_j below it
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                const double yj = __shfl_sync(0xffffffffu, bi, j) * r[j];
+                if (lane == j) bi = yj;
+                else if (lane > j) bi = fma(-a[j], yj, bi);
+            }
+            if (lane < 6) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) Ls[6 * lane + j] = a[j];
+            }
+            __syncwarp();
+            // backward: step_k = y_k r_k, then y_i -= L_ki step_k above it
+#pragma unroll
+            for (int k = 5; k >= 0; --k) {
+                const double sk = __shfl_sync(0xffffffffu, bi, k) * r[k];
+                if (lane == k) bi = sk;
+                else if (lane < k) bi = fma(-Ls[6 * k + row], sk, bi);
+            }
+            if (pd && lane < 6) xn[lane] = st[36 + lane] + bi;
+            if (lane == 0) s_pd = pd;
         }
         __syncthreads();
         if (!s_pd) {
             if (tid == 0) dev->flags |= FLAG_GN_NOTPD;
             return;
         }
-        if (tid == 0) {   // retraction and the FP32 matrices of the next pass
-            double pose[7], qe[4];
-            quat_exp(xn + 3, qe);
-            quat_mul(qe, st + 49, pose + 3);
-            quat_normalise(pose + 3);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) pose[a] = st[53 + a] + xn[a];
-            float m[12];
-            mats_rel(pose, st + 42, m);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) dev->rel[i] = m[i];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) dev->xi[i] = xn[i];
-#pragma unroll
-            for (int i = 0; i < 7; ++i) dev->cur_pose[i] = pose[i];
+        if (warp == 0) {   // retraction and the FP32 matrices of the next pass, one quaternion component a lane
+            const double w0 = xn[3], w1 = xn[4], w2 = xn[5];
+            const double th2 = fdot3(w0, w0, w1, w1, w2, w2);
+            const int c = lane & 3;
+            double qe;
+            if (th2 < 0.25) {   // the half-angle series of quat_exp: ch (lane c = 0), sh (c > 0)
+                const double x = 0.25 * th2;
+                const bool c0 = c == 0;
+                const double p = fma(x, fma(x, fma(x, fma(x, fma(x, c0 ? -1.0 / 3628800 : -1.0 / 39916800,
+                                                                 c0 ? 1.0 / 40320 : 1.0 / 362880),
+                                                          c0 ? -1.0 / 720 : -1.0 / 5040),
+                                                   c0 ? 1.0 / 24 : 1.0 / 120),
+                                            c0 ? -0.5 : -1.0 / 6),
+                                     1.0);
+                const double sh = 0.5 * p;
+                qe = c0 ? p : sh * (c == 1 ? w0 : (c == 2 ? w1 : w2));
+            } else {
+                double q4[4];
+                quat_exp(xn + 3, q4);
+                qe = c == 0 ? q4[0] : (c == 1 ? q4[1] : (c == 2 ? q4[2] : q4[3]));
+            }
+            // Hamilton product qe (x) pq, component c (the operations of quat_mul)
+            const double a0 = __shfl_sync(0xffffffffu, qe, 0), a1 = __shfl_sync(0xffffffffu, qe, 1),
+                         a2 = __shfl_sync(0xffffffffu, qe, 2), a3 = __shfl_sync(0xffffffffu, qe, 3);
+            const double* pq = st + 49;
+            const int p0 = c, p1 = c ^ 1, p2 = c ^ 2, p3 = c ^ 3;
+            const double t3 = a3 * pq[p3];
+            const double qm = fma(a0, pq[p0], fma((c == 0 || c == 2) ? -a1 : a1, pq[p1],
+                                                  fma((c == 0 || c == 3) ? -a2 : a2, pq[p2],
+                                                      (c == 0 || c == 1) ? -t3 : t3)));
+            // normalised, w >= 0 (quat_normalise)
+            const double n0 = __shfl_sync(0xffffffffu, qm, 0), n1 = __shfl_sync(0xffffffffu, qm, 1),
+                         n2 = __shfl_sync(0xffffffffu, qm, 2), n3 = __shfl_sync(0xffffffffu, qm, 3);
+            double rn = rsqrt(fma(n0, n0, fdot3(n1, n1, n2, n2, n3, n3)));
+            if (n0 < 0.0) rn = -rn;
+            const double qn = (c == 0 ? n0 : (c == 1 ? n1 : (c == 2 ? n2 : n3))) * rn;
+            double pose[7];
+            pose[3] = __shfl_sync(0xffffffffu, qn, 0);
+            pose[4] = __shfl_sync(0xffffffffu, qn, 1);
+            pose[5] = __shfl_sync(0xffffffffu, qn, 2);
+            pose[6] = __shfl_sync(0xffffffffu, qn, 3);
+            const int ta = lane < 3 ? lane : 0;
+            const double tv = st[53 + ta] + xn[ta];
+            pose[0] = __shfl_sync(0xffffffffu, tv, 0);
+            pose[1] = __shfl_sync(0xffffffffu, tv, 1);
+            pose[2] = __shfl_sync(0xffffffffu, tv, 2);
+            warp_mats_rel(pose, st + 42, dev->rel);
+            if (lane < 6) dev->xi[lane] = xn[lane];
+            if (lane < 7) dev->cur_pose[lane] = pose[lane];
         } else if (tid >= 32 && tid < 41) {   // meanwhile: the tangent map of the new iterate
             const int e = tid - 32, i = e / 3, j = e % 3;
             Jn[e] = so3_jl_entry(xn + 3, i, j);
@@ -521,14 +571,19 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         dev->cov[tid] = c;
     }
-    if (tid == 0) {
-        for (int a = 0; a < 3; ++a) dev->t[a] = dev->cur_pose[a];
-        for (int a = 0; a < 4; ++a) dev->q[a] = dev->cur_pose[3 + a];
-        dev->n_localised += 1;
-        mats_c2w(dev->cur_pose, dev->c2w);
-        mats_w2c(dev->cur_pose, dev->w2c);
-        dev->ne_out[78] = S[L::oCost];
-        dev->ne_out[79] = S[L::oCount];
+    if (warp == 0) {   // the new mean and its FP32 matrices, one entry a lane
+        double pose[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) pose[i] = dev->cur_pose[i];
+        warp_mats_c2w(pose, dev->c2w);
+        warp_mats_w2c(pose, dev->w2c);
+        if (lane < 3) dev->t[lane] = pose[lane];
+        if (lane < 4) dev->q[lane] = pose[3 + lane];
+        if (lane == 0) {
+            dev->n_localised += 1;
+            dev->ne_out[78] = S[L::oCost];
+            dev->ne_out[79] = S[L::oCount];
+        }
     }
 }
 
