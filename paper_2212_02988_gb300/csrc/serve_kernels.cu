@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) kb_pack(const SlotDesc* __restrict__ slot
 
 // One localisation pass of every localising member; item = one virtual block.
 template <int MODE>
-__global__ void __launch_bounds__(256) kb_track(const SlotDesc* __restrict__ slots, BatchDesc* __restrict__ b,
+__global__ void __launch_bounds__(256, 2) kb_track(const SlotDesc* __restrict__ slots, BatchDesc* __restrict__ b,
                                                 int ctr) {
     pdl_enter();
     const int* off = MODE == TRACK_GN ? b->gn_off : b->lap_off;

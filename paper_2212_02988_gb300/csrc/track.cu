@@ -4,8 +4,9 @@
 
 namespace prism {
 
+// Two blocks per SM for the passes of every step (at most 128 registers).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_track(KParams P, const float* __restrict__ od,
+__global__ void __launch_bounds__(kThreads, MODE == TRACK_EXPORT ? 1 : 2) k_track(KParams P, const float* __restrict__ od,
                                                     const float* __restrict__ orgb,
                                                     const uint8_t* __restrict__ om,
                                                     const float4* __restrict__ a0,

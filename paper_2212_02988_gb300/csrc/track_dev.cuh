@@ -89,6 +89,114 @@ __device__ inline void rotate_to_world(const double* Ra, const double* Ap, doubl
     }
 }
 
+// One observed pixel between its loads and its residuals.
+struct TrackPix {
+    float X0, X1, X2, iz, up, vp, aa, cc;
+    float4 A, I00, I10, I01, I11;
+    float c0, c1, c2;   // observed colour
+    int iu, iv;
+    bool ok;
+};
+
+// Decisions up to the anchor gathers of pixel p, and the gathers themselves,
+// issued together (nearest normal/depth and the four bilinear colour taps)
+// as soon as the projection is known.  ok = the pixel passed the mask,
+// z > 0 and both image-range tests; the remaining gates are in track_eval.
+__device__ __forceinline__ void track_fetch(const KParams& P, const float* sM, const float* sb,
+                                            const float* __restrict__ od, const float* __restrict__ orgb,
+                                            const uint8_t* __restrict__ om, const float4* __restrict__ a0,
+                                            const float4* __restrict__ a1, int p, int W, float fW1, float fH1,
+                                            float fW2, float fH2, TrackPix& q) {
+    const bool m = om[p] != 0;
+    const float z = od[p];
+    q.c0 = orgb[3 * p];
+    q.c1 = orgb[3 * p + 1];
+    q.c2 = orgb[3 * p + 2];
+    const int u = p % W, v = p / W;
+    // ---- decisions (FP32 recipe) ----
+    float Pc[3], X[3];
+    backproject_rn(P, u, v, z, Pc);
+    affine_rn(sM, sb, Pc, X);
+    q.X0 = X[0]; q.X1 = X[1]; q.X2 = X[2];
+    q.iz = __fdiv_rn(1.0f, X[2]);
+    q.up = __fmaf_rn(__fmul_rn(P.fx32, X[0]), q.iz, P.cx32);
+    q.vp = __fmaf_rn(__fmul_rn(P.fy32, X[1]), q.iz, P.cy32);
+    const float nu = floorf(__fadd_rn(q.up, 0.5f)), nv = floorf(__fadd_rn(q.vp, 0.5f));
+    const float bu = floorf(q.up), bv = floorf(q.vp);
+    q.ok = m && X[2] > 0.0f && nu >= 0.0f && nu <= fW1 && nv >= 0.0f && nv <= fH1 && bu >= 0.0f &&
+           bu <= fW2 && bv >= 0.0f && bv <= fH2;
+    q.iu = q.ok ? (int)nu : 0;
+    q.iv = q.ok ? (int)nv : 0;
+    q.aa = __fsub_rn(q.up, bu);
+    q.cc = __fsub_rn(q.vp, bv);
+    if (q.ok) {
+        const int b00 = (int)bv * W + (int)bu;
+        q.A = a0[q.iv * W + q.iu];
+        q.I00 = a1[b00];
+        q.I10 = a1[b00 + 1];
+        q.I01 = a1[b00 + W];
+        q.I11 = a1[b00 + W + 1];
+    }
+}
+
+// The remaining gates of a fetched pixel (valid anchor depth and colour taps,
+// |r_geo|, |r_rgb|) and, if kept, its four residuals and Jacobians into acc.
+template <int MODE>
+__device__ __forceinline__ void track_eval(const KParams& P, const float* sb, const TrackPix& q, float* acc) {
+    using L = Layout<MODE>;
+    if (!q.ok) return;
+    const float4 A = q.A, I00 = q.I00, I10 = q.I10, I01 = q.I01, I11 = q.I11;
+    if (!(A.w > 0.0f)) return;
+    if (!(I00.w > 0.0f && I10.w > 0.0f && I01.w > 0.0f && I11.w > 0.0f)) return;
+    const float aa = q.aa, cc = q.cc;
+    float ph[3];
+    backproject_rn(P, q.iu, q.iv, A.w, ph);
+    const float e0 = __fsub_rn(ph[0], q.X0), e1 = __fsub_rn(ph[1], q.X1), e2 = __fsub_rn(ph[2], q.X2);
+    const float rgeo = __fmaf_rn(A.x, e0, __fmaf_rn(A.y, e1, __fmul_rn(A.z, e2)));
+    if (!(fabsf(rgeo) <= P.gate_geo32)) return;
+    float rr[3];
+    {
+        float t = lerp_rn(I00.x, I10.x, aa), b = lerp_rn(I01.x, I11.x, aa);
+        rr[0] = __fsub_rn(lerp_rn(t, b, cc), q.c0);
+        t = lerp_rn(I00.y, I10.y, aa); b = lerp_rn(I01.y, I11.y, aa);
+        rr[1] = __fsub_rn(lerp_rn(t, b, cc), q.c1);
+        t = lerp_rn(I00.z, I10.z, aa); b = lerp_rn(I01.z, I11.z, aa);
+        rr[2] = __fsub_rn(lerp_rn(t, b, cc), q.c2);
+    }
+    if (!(fabsf(rr[0]) <= P.gate_rgb32 && fabsf(rr[1]) <= P.gate_rgb32 && fabsf(rr[2]) <= P.gate_rgb32)) return;
+    // ---- values (FP32) ----
+    const float ya0 = q.X0 - sb[0], ya1 = q.X1 - sb[1], ya2 = q.X2 - sb[2];
+    float J[6];
+    {   // point-to-plane: a_X = -n
+        const float ax = -A.x, ay = -A.y, az = -A.z;
+        J[0] = ax; J[1] = ay; J[2] = az;
+        J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
+        const float ar = fabsf(rgeo);
+        const float w = 1.0f / (P.b_geo32 * fmaxf(ar, P.floor_geo32));
+        accumulate<MODE>(acc, J, rgeo, w, 1.0f / (P.b_geo32 * P.b_geo32), ar / P.b_geo32);
+    }
+    const float iz = q.iz, izz = iz * iz;
+    const float du0 = P.fx32 * iz, du2 = -P.fx32 * q.X0 * izz;
+    const float dv1 = P.fy32 * iz, dv2 = -P.fy32 * q.X1 * izz;
+    const float wb = 1.0f / (P.b_rgb32 * P.b_rgb32);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float i00 = c == 0 ? I00.x : (c == 1 ? I00.y : I00.z);
+        const float i10 = c == 0 ? I10.x : (c == 1 ? I10.y : I10.z);
+        const float i01 = c == 0 ? I01.x : (c == 1 ? I01.y : I01.z);
+        const float i11 = c == 0 ? I11.x : (c == 1 ? I11.y : I11.z);
+        const float gu = fmaf(1.0f - cc, i10 - i00, cc * (i11 - i01));
+        const float gv = fmaf(1.0f - aa, i01 - i00, aa * (i11 - i10));
+        const float ax = gu * du0, ay = gv * dv1, az = fmaf(gu, du2, gv * dv2);
+        J[0] = ax; J[1] = ay; J[2] = az;
+        J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
+        const float ar = fabsf(rr[c]);
+        const float w = 1.0f / (P.b_rgb32 * fmaxf(ar, P.floor_rgb32));
+        accumulate<MODE>(acc, J, rr[c], w, wb, ar / P.b_rgb32);
+    }
+    acc[L::oCount] += 1.0f;
+}
+
 }  // namespace track_detail
 
 using namespace track_detail;
@@ -126,76 +234,18 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     for (int i = 0; i < N; ++i) acc[i] = 0.0f;
     const int W = P.W, Hh = P.H, NP = W * Hh;
     const float fW1 = (float)(W - 1), fH1 = (float)(Hh - 1), fW2 = (float)(W - 2), fH2 = (float)(Hh - 2);
-    for (int p = vb * kThreads + tid; p < NP; p += nvb * kThreads) {
-        if (!om[p]) continue;
-        const int u = p % W, v = p / W;
-        // ---- decisions (FP32 recipe) ----
-        float Pc[3], X[3];
-        backproject_rn(P, u, v, od[p], Pc);
-        affine_rn(sM, sb, Pc, X);
-        if (!(X[2] > 0.0f)) continue;
-        const float iz = __fdiv_rn(1.0f, X[2]);
-        const float up = __fmaf_rn(__fmul_rn(P.fx32, X[0]), iz, P.cx32);
-        const float vp = __fmaf_rn(__fmul_rn(P.fy32, X[1]), iz, P.cy32);
-        const float nu = floorf(__fadd_rn(up, 0.5f)), nv = floorf(__fadd_rn(vp, 0.5f));
-        if (!(nu >= 0.0f && nu <= fW1 && nv >= 0.0f && nv <= fH1)) continue;
-        const int iu = (int)nu, iv = (int)nv;
-        const float4 A = a0[iv * W + iu];
-        if (!(A.w > 0.0f)) continue;
-        const float bu = floorf(up), bv = floorf(vp);
-        if (!(bu >= 0.0f && bu <= fW2 && bv >= 0.0f && bv <= fH2)) continue;
-        const int b00 = (int)bv * W + (int)bu;
-        const float4 I00 = a1[b00], I10 = a1[b00 + 1], I01 = a1[b00 + W], I11 = a1[b00 + W + 1];
-        if (!(I00.w > 0.0f && I10.w > 0.0f && I01.w > 0.0f && I11.w > 0.0f)) continue;
-        const float aa = __fsub_rn(up, bu), cc = __fsub_rn(vp, bv);
-        float ph[3];
-        backproject_rn(P, iu, iv, A.w, ph);
-        const float e0 = __fsub_rn(ph[0], X[0]), e1 = __fsub_rn(ph[1], X[1]), e2 = __fsub_rn(ph[2], X[2]);
-        const float rgeo = __fmaf_rn(A.x, e0, __fmaf_rn(A.y, e1, __fmul_rn(A.z, e2)));
-        if (!(fabsf(rgeo) <= P.gate_geo32)) continue;
-        const float* oc = orgb + 3 * p;
-        float rr[3];
-        {
-            float t = lerp_rn(I00.x, I10.x, aa), b = lerp_rn(I01.x, I11.x, aa);
-            rr[0] = __fsub_rn(lerp_rn(t, b, cc), oc[0]);
-            t = lerp_rn(I00.y, I10.y, aa); b = lerp_rn(I01.y, I11.y, aa);
-            rr[1] = __fsub_rn(lerp_rn(t, b, cc), oc[1]);
-            t = lerp_rn(I00.z, I10.z, aa); b = lerp_rn(I01.z, I11.z, aa);
-            rr[2] = __fsub_rn(lerp_rn(t, b, cc), oc[2]);
-        }
-        if (!(fabsf(rr[0]) <= P.gate_rgb32 && fabsf(rr[1]) <= P.gate_rgb32 && fabsf(rr[2]) <= P.gate_rgb32))
-            continue;
-        // ---- values (FP32) ----
-        const float ya0 = X[0] - sb[0], ya1 = X[1] - sb[1], ya2 = X[2] - sb[2];
-        float J[6];
-        {   // point-to-plane: a_X = -n
-            const float ax = -A.x, ay = -A.y, az = -A.z;
-            J[0] = ax; J[1] = ay; J[2] = az;
-            J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
-            const float ar = fabsf(rgeo);
-            const float w = 1.0f / (P.b_geo32 * fmaxf(ar, P.floor_geo32));
-            accumulate<MODE>(acc, J, rgeo, w, 1.0f / (P.b_geo32 * P.b_geo32), ar / P.b_geo32);
-        }
-        const float izz = iz * iz;
-        const float du0 = P.fx32 * iz, du2 = -P.fx32 * X[0] * izz;
-        const float dv1 = P.fy32 * iz, dv2 = -P.fy32 * X[1] * izz;
-        const float wb = 1.0f / (P.b_rgb32 * P.b_rgb32);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float i00 = c == 0 ? I00.x : (c == 1 ? I00.y : I00.z);
-            const float i10 = c == 0 ? I10.x : (c == 1 ? I10.y : I10.z);
-            const float i01 = c == 0 ? I01.x : (c == 1 ? I01.y : I01.z);
-            const float i11 = c == 0 ? I11.x : (c == 1 ? I11.y : I11.z);
-            const float gu = fmaf(1.0f - cc, i10 - i00, cc * (i11 - i01));
-            const float gv = fmaf(1.0f - aa, i01 - i00, aa * (i11 - i10));
-            const float ax = gu * du0, ay = gv * dv1, az = fmaf(gu, du2, gv * dv2);
-            J[0] = ax; J[1] = ay; J[2] = az;
-            J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
-            const float ar = fabsf(rr[c]);
-            const float w = 1.0f / (P.b_rgb32 * fmaxf(ar, P.floor_rgb32));
-            accumulate<MODE>(acc, J, rr[c], w, wb, ar / P.b_rgb32);
-        }
-        acc[L::oCount] += 1.0f;
+    // Two pixels per iteration: both are fetched (all their loads in flight)
+    // before either is evaluated; the sums see the pixels in the order of a
+    // plain stride loop.
+    const int stride = nvb * kThreads;
+    for (int p = vb * kThreads + tid; p < NP; p += 2 * stride) {
+        TrackPix q0, q1;
+        track_fetch(P, sM, sb, od, orgb, om, a0, a1, p, W, fW1, fH1, fW2, fH2, q0);
+        const bool two = p + stride < NP;
+        if (two) track_fetch(P, sM, sb, od, orgb, om, a0, a1, p + stride, W, fW1, fH1, fW2, fH2, q1);
+        else q1.ok = false;
+        track_eval<MODE>(P, sb, q0, acc);
+        track_eval<MODE>(P, sb, q1, acc);
     }
 
     // ---- block reduction: FP32, in a fixed order (warp shuffles, then warps 0..7) ----
