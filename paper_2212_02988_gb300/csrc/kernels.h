@@ -62,9 +62,11 @@ int track_launch_grid(const KParams& P, int mode, int max_blocks);
 constexpr int TRACK_NV_MAX = 50;   // FP32 values per block partial
 
 // state.cu — FP64 prediction and GN start; the FP32 matrices of a pose.
+// pdl = false: a plain launch (for a kernel that follows an event wait, whose
+// dependency must not be relaxed to the previous kernel of the stream).
 cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt,
-                           cudaStream_t s);
-cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s);
+                           cudaStream_t s, bool pdl = true);
+cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s, bool pdl = true);
 
 // fuse.cu — the per-voxel map update with the world-to-camera matrices
 // `w2c` (12 FP32 on the device, DevState::w2c).

@@ -119,6 +119,16 @@ struct prism_ctx {
     int max_blocks = 0;
     double* d_imu = nullptr;
     int imu_cap = 0;
+    // prism_step's prediction stream: the prior of step t + 1 needs only the
+    // posterior of step t, so it runs beside step t's fuse and render
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_state = nullptr;   // main stream: the posterior is final
+    cudaEvent_t ev_pred = nullptr;    // side stream: the prior is ready
+    static constexpr int kImuRing = 4;
+    double* h_imu[kImuRing] = {nullptr, nullptr, nullptr, nullptr};   // pinned IMU staging
+    cudaEvent_t ev_imu[kImuRing] = {nullptr, nullptr, nullptr, nullptr};
+    int h_imu_cap = 0;
+    int imu_slot = 0;
     bool has_anchor = false;
     bool has_prior = false;
     int64_t steps = 0;
@@ -186,17 +196,18 @@ cudaEvent_t take_event(prism_handle h) {
 struct PhaseTimer {
     prism_handle h;
     int phase;
+    cudaStream_t s;
     cudaEvent_t a = nullptr;
-    PhaseTimer(prism_handle h_, int ph) : h(h_), phase(ph) {
+    PhaseTimer(prism_handle h_, int ph, cudaStream_t s_ = nullptr) : h(h_), phase(ph), s(s_ ? s_ : h_->stream) {
         if (h->timing) {
             a = take_event(h);
-            cudaEventRecord(a, h->stream);
+            cudaEventRecord(a, s);
         }
     }
     ~PhaseTimer() {
         if (a) {
             cudaEvent_t b = take_event(h);
-            cudaEventRecord(b, h->stream);
+            cudaEventRecord(b, s);
             h->pending.push_back({phase, a, b});
         }
     }
@@ -222,6 +233,16 @@ void free_all(prism_handle h) {
         if (p) cudaFree(p);
     for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    for (int k = 0; k < prism_ctx::kImuRing; ++k) {
+        if (h->h_imu[k]) cudaFreeHost(h->h_imu[k]);
+        if (h->ev_imu[k]) cudaEventDestroy(h->ev_imu[k]);
+    }
+    if (h->ev_state) cudaEventDestroy(h->ev_state);
+    if (h->ev_pred) cudaEventDestroy(h->ev_pred);
 }
 
 template <class T>
@@ -281,6 +302,7 @@ prism_status write_state(prism_handle h, const prism_state* s) {
     CK(h, cudaMemcpy(h->dstate, &d, sizeof(d), cudaMemcpyHostToDevice), "write state");
     PoseArg pa{};
     LAUNCH(h, launch_prep(h->dstate, PREP_STATE, pa, h->stream), "pose matrices");
+    CK(h, cudaEventRecord(h->ev_state, h->stream), "state event");
     h->has_prior = false;
     return PRISM_OK;
 }
@@ -300,11 +322,14 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
     return PRISM_OK;
 }
 
-prism_status do_localise(prism_handle h, const float* depth, const float* rgb) {
+// after_side: the prior was predicted on the side stream (prism_step); the
+// pose matrices wait for it.
+prism_status do_localise(prism_handle h, const float* depth, const float* rgb, bool after_side = false) {
     PhaseTimer t(h, PH_LOCALISE);
     LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
     PoseArg pa{};
-    LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream), "pose matrices");
+    if (after_side) CK(h, cudaStreamWaitEvent(h->stream, h->ev_pred, 0), "wait for the prior");
+    LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream, !after_side), "pose matrices");
     for (int it = 0; it < h->cfg.n_gn; ++it)
         LAUNCH(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                            h->counter, h->max_blocks, h->dstats, h->stream),
@@ -312,6 +337,7 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb) {
     LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                        h->counter, h->max_blocks, h->dstats, h->stream),
        "Laplace pass");
+    CK(h, cudaEventRecord(h->ev_state, h->stream), "state event");
     h->has_prior = false;
     return PRISM_OK;
 }
@@ -341,6 +367,54 @@ prism_status do_predict(prism_handle h, const double* imu, int32_t n, double dt)
         CK(h, cudaMemcpyAsync(h->d_imu, imu, (size_t)n * 7 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
            "IMU upload");
     LAUNCH(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->stream), "predict");
+    h->has_prior = true;
+    return PRISM_OK;
+}
+
+// prism_step's prediction: on the side stream once the posterior is final
+// (it then overlaps the previous step's fuse and render), the IMU window
+// staged through a ring of pinned buffers so that the upload is asynchronous.
+prism_status do_predict_side(prism_handle h, const double* imu, int32_t n, double dt) {
+    if (n > h->imu_cap || n > h->h_imu_cap) {
+        CK(h, cudaStreamSynchronize(h->side), "stream synchronize");
+        CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+        const int cap = n < 256 ? 256 : n;
+        if (n > h->imu_cap) {
+            if (h->d_imu) {
+                cudaFree(h->d_imu);
+                h->bytes -= (int64_t)h->imu_cap * 7 * sizeof(double);
+                h->d_imu = nullptr;
+                h->imu_cap = 0;
+            }
+            CK(h, dalloc(h, &h->d_imu, (size_t)cap * 7 * sizeof(double)), "IMU buffer");
+            h->imu_cap = cap;
+        }
+        if (n > h->h_imu_cap) {
+            for (int k = 0; k < prism_ctx::kImuRing; ++k) {
+                if (h->h_imu[k]) cudaFreeHost(h->h_imu[k]);
+                h->h_imu[k] = nullptr;
+            }
+            h->h_imu_cap = 0;
+            for (int k = 0; k < prism_ctx::kImuRing; ++k)
+                CK(h, cudaMallocHost(&h->h_imu[k], (size_t)cap * 7 * sizeof(double)), "IMU staging");
+            h->h_imu_cap = cap;
+        }
+    }
+    const int k = h->imu_slot;
+    h->imu_slot = (k + 1) % prism_ctx::kImuRing;
+    CK(h, cudaEventSynchronize(h->ev_imu[k]), "IMU staging reuse");   // its last upload has run
+    if (n > 0) std::memcpy(h->h_imu[k], imu, (size_t)n * 7 * sizeof(double));
+    CK(h, cudaStreamWaitEvent(h->side, h->ev_state, 0), "wait for the posterior");
+    {
+        PhaseTimer t(h, PH_PREDICT, h->side);
+        if (n > 0)
+            CK(h, cudaMemcpyAsync(h->d_imu, h->h_imu[k], (size_t)n * 7 * sizeof(double), cudaMemcpyHostToDevice,
+                                  h->side),
+               "IMU upload");
+        CK(h, cudaEventRecord(h->ev_imu[k], h->side), "IMU event");
+        LAUNCH(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->side, false), "predict");
+    }
+    CK(h, cudaEventRecord(h->ev_pred, h->side), "prior event");
     h->has_prior = true;
     return PRISM_OK;
 }
@@ -437,6 +511,17 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         dalloc(h, &h->counter, sizeof(unsigned int)))
         return cleanup(PRISM_ENOMEM, "device allocation failed");
     cudaGetLastError();
+    {   // the prediction stream (high priority: its one block is scheduled ahead of waiting fuse tiles)
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if ((e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_pred, cudaEventDisableTiming)) != cudaSuccess)
+            return cleanup(PRISM_ECUDA, std::string("streams: ") + cudaGetErrorString(e));
+        for (int k = 0; k < prism_ctx::kImuRing; ++k)
+            if ((e = cudaEventCreateWithFlags(&h->ev_imu[k], cudaEventDisableTiming)) != cudaSuccess)
+                return cleanup(PRISM_ECUDA, std::string("events: ") + cudaGetErrorString(e));
+    }
     if ((e = launch_map_fill(h->kp, h->map, (float)cfg->init_occ, (float)cfg->init_rgb, (float)cfg->prior_var,
                              h->stream)) != cudaSuccess)
         return cleanup(PRISM_ECUDA, std::string("map fill: ") + cudaGetErrorString(e));
@@ -529,8 +614,8 @@ prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
         std::string why;
         if (!imu_ok(imu, n, dt, why)) return fail(h, PRISM_EINVAL, why);
         if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
-        if ((st = do_predict(h, imu, n, dt)) != PRISM_OK) return st;
-        if ((st = do_localise(h, depth, rgb)) != PRISM_OK) return st;
+        if ((st = do_predict_side(h, imu, n, dt)) != PRISM_OK) return st;
+        if ((st = do_localise(h, depth, rgb, true)) != PRISM_OK) return st;
         mask_ready = true;
     }
     if ((st = do_fuse(h, depth, rgb, mask_ready)) != PRISM_OK) return st;
@@ -653,6 +738,7 @@ prism_status prism_get_stats(prism_handle h, prism_stats* out) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     if (!out) return fail(h, PRISM_EINVAL, "out is NULL");
     DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->side), "stream synchronize");
     CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
     DevStats s;
     CK(h, cudaMemcpy(&s, h->dstats, sizeof(s), cudaMemcpyDeviceToHost), "read stats");
@@ -683,6 +769,7 @@ prism_status prism_get_timing(prism_handle h, prism_timing* out) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     if (!out) return fail(h, PRISM_EINVAL, "out is NULL");
     DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->side), "stream synchronize");
     CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
     collect_timing(h);
     out->predict_ms = h->acc_ms[PH_PREDICT];
@@ -701,6 +788,7 @@ prism_status prism_get_timing(prism_handle h, prism_timing* out) {
 prism_status prism_timing_reset(prism_handle h) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     DeviceGuard g(h->device);
+    CK(h, cudaStreamSynchronize(h->side), "stream synchronize");
     CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
     collect_timing(h);
     for (int i = 0; i < PH_COUNT; ++i) { h->acc_ms[i] = 0.0; h->acc_n[i] = 0; }

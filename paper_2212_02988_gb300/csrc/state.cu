@@ -15,13 +15,16 @@ __global__ void k_prep(DevState* dev, int kind, PoseArg pose) {
     prep_mats_warp(dev, kind, pose);   // one warp
 }
 
-cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s) {
-    launch_pdl(k_prep, 1, 32, s, dev, kind, pose);
+cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s, bool pdl) {
+    if (pdl) return launch_pdl(k_prep, 1, 32, s, dev, kind, pose);
+    k_prep<<<1, 32, 0, s>>>(dev, kind, pose);
     return cudaGetLastError();
 }
 
-cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt, cudaStream_t s) {
-    launch_pdl(k_predict, 1, 256, s, P, dev, imu, n, dt);
+cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt, cudaStream_t s,
+                           bool pdl) {
+    if (pdl) return launch_pdl(k_predict, 1, 256, s, P, dev, imu, n, dt);
+    k_predict<<<1, 256, 0, s>>>(P, dev, imu, n, dt);
     return cudaGetLastError();
 }
 
