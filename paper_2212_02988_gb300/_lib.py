@@ -22,7 +22,7 @@ STORAGE_F32, STORAGE_BF16 = 0, 1
 class Config(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("storage", C.c_int32),
                 ("width", C.c_int32), ("height", C.c_int32), ("n_gn", C.c_int32),
-                ("reserved", C.c_int32), ("voxel", C.c_double), ("origin", C.c_double * 3),
+                ("skip_empty", C.c_int32), ("voxel", C.c_double), ("origin", C.c_double * 3),
                 ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
                 ("eps", C.c_double), ("tau", C.c_double), ("max_depth", C.c_double),
                 ("trunc", C.c_double), ("prior_var", C.c_double), ("init_occ", C.c_double),

@@ -16,7 +16,8 @@
 // f_occ = -clamp(sdf, -trunc, trunc) (App. D: f_update = [-f_sdf, f_rgb]);
 // colour (one shared variance, reading R11) only where |sdf| <= trunc (R10).
 // A voxel outside the update region is neither read nor written, and a
-// tile whose bounding sphere misses the view frustum exits at once.
+// tile whose bounding sphere misses the view frustum exits at once; every
+// other tile refreshes its occupancy bound (kernels.h, MapPlanes::tb).
 #pragma once
 
 #include "kernels.h"
@@ -147,6 +148,19 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
             }
             ++n_col;
         }
+    }
+    // the tile's occupancy bound after this update (the render's brick skipping)
+    {
+        float m = -INFINITY, am = 0.0f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int within = threadIdx.x + 256 * half;
+            const float v = map_load_rw<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
+                                                               bz * 8 + (within >> 6)));
+            m = fmaxf(m, v);
+            am = fmaxf(am, fabsf(v));
+        }
+        tile_bound_store(M.tb, tile, m, am);
     }
     if (stats) {
         unsigned int a = (unsigned int)warp_sum_u64(n_occ), b = (unsigned int)warp_sum_u64(n_col);

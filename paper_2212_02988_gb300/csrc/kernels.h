@@ -33,6 +33,12 @@ struct MapPlanes {
     void* b;
     void* var_occ;
     void* var_rgb;
+    // per 8^3 tile: (max occupancy mean, max |occupancy mean|) over its voxels,
+    // kept current by the fuse and by map fill / load; per brick b (the cells
+    // whose lower corner lies in tile b): the same over tiles b + {0, 1}^3,
+    // derived from tb by launch_brick_bounds (render_dev.cuh)
+    float2* tb;
+    float2* bb;
 };
 
 // render.cu — mats: 12 FP32 values on the device (DevState::c2w or ::aux);
@@ -81,6 +87,10 @@ cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* o
                             const float* var_occ, const float* var_rgb, cudaStream_t s);
 cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, float* rgb, float* var_occ,
                              float* var_rgb, cudaStream_t s);
+// The tile bounds M.tb of the whole map (after a fill or a load), and the
+// brick bounds M.bb derived from them (after any change of M.tb).
+cudaError_t launch_tile_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s);
+cudaError_t launch_brick_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s);
 
 // render_bwd.cu — adjoint of the render at the pose whose matrices are in
 // `mats` (DevState::aux); adds the pose gradient to dev->grad_pose.

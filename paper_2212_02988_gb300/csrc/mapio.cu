@@ -3,6 +3,7 @@
 // (a ghost border holding copies of the edge voxels, prism_dev.cuh).
 #include "kernels.h"
 #include "prism_dev.cuh"
+#include "render_dev.cuh"
 
 namespace prism {
 
@@ -59,6 +60,34 @@ __global__ void k_map_store(KParams P, MapPlanes M, float* __restrict__ occ, flo
     }
 }
 
+// One block per 8^3 tile: (max, max |.|) of the tile's occupancy means.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_tile_bounds(KParams P, MapPlanes M) {
+    pdl_enter();
+    const uint32_t tile = blockIdx.x;
+    const int bx = tile % P.nbx, by = (tile / P.nbx) % P.nby, bz = tile / (P.nbx * P.nby);
+    float m = -INFINITY, a = 0.0f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int within = threadIdx.x + 256 * half;
+        const float v = map_load<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
+                                                         bz * 8 + (within >> 6)));
+        m = fmaxf(m, v);
+        a = fmaxf(a, fabsf(v));
+    }
+    tile_bound_store(M.tb, tile, m, a);
+}
+
+// One thread per brick: the bound of tiles b + {0, 1}^3 (render_dev.cuh).
+__global__ void __launch_bounds__(256) k_brick_bounds(KParams P, MapPlanes M) {
+    pdl_enter();
+    const int n = P.nbx * P.nby * P.nbz;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
+        const int bx = b % P.nbx, by = (b / P.nbx) % P.nby, bz = b / (P.nbx * P.nby);
+        M.bb[b] = render_detail::brick_bound(P, M.tb, bx, by, bz);
+    }
+}
+
 static unsigned int io_grid(uint32_t n) {
     uint32_t g = (n + 255) / 256;
     return g > 152u * 64u ? 152u * 64u : (g ? g : 1u);
@@ -85,6 +114,20 @@ cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, f
     if (P.bf16) launch_pdl(k_map_store<true>, io_grid(n), 256, s, P, M, occ, rgb, var_occ, var_rgb, n);
     else launch_pdl(k_map_store<false>, io_grid(n), 256, s, P, M, occ, rgb, var_occ, var_rgb, n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tile_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s) {
+    const unsigned int tiles = (unsigned int)(P.nbx * P.nby * P.nbz);
+    if (P.bf16) launch_pdl(k_tile_bounds<true>, tiles, 256, s, P, M);
+    else launch_pdl(k_tile_bounds<false>, tiles, 256, s, P, M);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_brick_bounds(P, M, s);
+}
+
+cudaError_t launch_brick_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s) {
+    const unsigned int n = (unsigned int)(P.nbx * P.nby * P.nbz);
+    return launch_pdl(k_brick_bounds, (n + 255) / 256, 256, s, P, M);
 }
 
 }  // namespace prism

@@ -26,6 +26,7 @@ bool valid_config(const prism_config* c, std::string& why) {
     if (c->storage != PRISM_STORAGE_F32 && c->storage != PRISM_STORAGE_BF16) return bad("storage must be 0 or 1");
     if (c->width < 3 || c->height < 3 || (double)c->width * c->height > 1.0e8) return bad("image size out of range");
     if (c->n_gn < 1 || c->n_gn > 1000) return bad("n_gn must be in [1, 1000]");
+    if (c->skip_empty != 0 && c->skip_empty != 1) return bad("skip_empty must be 0 or 1");
     if (!(c->voxel > 0) || !(c->eps > 0) || !(c->fx > 0) || !(c->fy > 0)) return bad("voxel, eps, fx, fy must be > 0");
     if (!(c->prior_var > 0) || !(c->update_var > 0) || !(c->trunc > 0)) return bad("variances and trunc must be > 0");
     if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
@@ -44,6 +45,7 @@ void fill_kparams(const prism_config* c, KParams& k) {
     k.npad = k.pxy * ((uint32_t)c->nz + 2);
     k.W = c->width; k.H = c->height;
     k.bf16 = c->storage == PRISM_STORAGE_BF16;
+    k.skip = c->skip_empty;
     // the march cannot take more than (nx + ny + nz) vs / eps in-grid samples
     double kcap = 2.0 * (c->nx + c->ny + c->nz) * c->voxel / c->eps + 2.0;
     double kuser = c->max_depth > 0 ? std::floor(c->max_depth / c->eps) : kcap;
@@ -346,6 +348,7 @@ prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool 
     PhaseTimer t(h, PH_FUSE);
     if (!mask_ready) LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
     LAUNCH(h, launch_fuse(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->stream), "fuse");
+    if (h->kp.skip) LAUNCH(h, launch_brick_bounds(h->kp, h->map, h->stream), "brick bounds");
     return PRISM_OK;
 }
 
@@ -440,6 +443,7 @@ void prism_config_default(prism_config* c, int32_t n, double extent, int32_t wid
     c->width = width;
     c->height = height;
     c->n_gn = 10;
+    c->skip_empty = 1;
     c->voxel = extent / n;
     for (int a = 0; a < 3; ++a) c->origin[a] = -0.5 * extent;
     c->fx = c->fy = 70.0 * width / 80.0;
@@ -496,8 +500,12 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         delete h;
         return fail(nullptr, st, m);
     };
-    if (dalloc(h, &h->map_block, 6 * plane) != cudaSuccess) return cleanup(PRISM_ENOMEM, "map allocation failed");
+    const size_t tbytes = (((size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(float2) + 255) / 256) * 256;
+    if (dalloc(h, &h->map_block, 6 * plane + 2 * tbytes) != cudaSuccess)
+        return cleanup(PRISM_ENOMEM, "map allocation failed");
     char* base = (char*)h->map_block;
+    h->map.tb = (float2*)(base + 6 * plane);
+    h->map.bb = (float2*)(base + 6 * plane + tbytes);
     h->map.occ = base;
     h->map.r = base + plane;
     h->map.g = base + 2 * plane;
@@ -523,7 +531,8 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
                 return cleanup(PRISM_ECUDA, std::string("events: ") + cudaGetErrorString(e));
     }
     if ((e = launch_map_fill(h->kp, h->map, (float)cfg->init_occ, (float)cfg->init_rgb, (float)cfg->prior_var,
-                             h->stream)) != cudaSuccess)
+                             h->stream)) != cudaSuccess ||
+        (e = launch_tile_bounds(h->kp, h->map, h->stream)) != cudaSuccess)
         return cleanup(PRISM_ECUDA, std::string("map fill: ") + cudaGetErrorString(e));
     if ((e = cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream)) != cudaSuccess ||
@@ -648,6 +657,10 @@ prism_status prism_map_load(prism_handle h, const float* occ, const float* rgb, 
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     DeviceGuard g(h->device);
     LAUNCH(h, launch_map_load(h->kp, h->map, occ, rgb, var_occ, var_rgb, h->stream), "map load");
+    if (occ) {
+        LAUNCH(h, launch_tile_bounds(h->kp, h->map, h->stream), "tile bounds");
+        ++h->launches;   // and the brick bounds derived from them
+    }
     return PRISM_OK;
 }
 

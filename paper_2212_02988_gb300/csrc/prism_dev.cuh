@@ -51,6 +51,7 @@ struct KParams {
     int W, H;                  // image size
     int kmax;                  // last ray sample index
     int bf16;                  // map storage is bf16
+    int skip;                  // rays skip bricks whose occupancy bound stays below tau
     float o32[3];              // grid origin
     float vs32, inv_vs32;      // voxel size and its inverse
     float eps32, tau32, trunc32, disc32;
@@ -261,6 +262,24 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// Block-wide (max v, max a) over a 256-thread block, stored by thread 0 as
+// the tile bound of `tile` (every thread must call it).
+__device__ __forceinline__ void tile_bound_store(float2* tb, uint32_t tile, float v, float a) {
+    __shared__ float s_v[8], s_a[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_v[w] = v; s_a[w] = a; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < 8; ++i) { v = fmaxf(v, s_v[i]); a = fmaxf(a, s_a[i]); }
+        tb[tile] = make_float2(v, a);
+    }
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -6,7 +6,7 @@
 namespace prism {
 
 template <bool BF16, bool DETAIL, int PX>
-__global__ void __launch_bounds__(128) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
+__global__ void __launch_bounds__(128, 10) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
                                                 float* __restrict__ depth, float* __restrict__ rgb,
                                                 uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
                                                 DevStats* __restrict__ stats, const double* __restrict__ anchor_src,

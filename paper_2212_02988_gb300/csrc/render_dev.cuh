@@ -61,6 +61,7 @@ __device__ __forceinline__ float trilinear(const void* plane, uint32_t base, uin
 struct Sample {
     uint32_t base;
     float fx, fy, fz;
+    int ix, iy, iz;   // lower corner (x0, y0, z0), x0 in [-1, n - 1]
 };
 
 // floor(g) for |g| < 2^22 without a conversion instruction: adding
@@ -79,7 +80,60 @@ __device__ __forceinline__ Sample cell_of(uint32_t px, uint32_t pxy, float gx, f
     // in wrapping 32-bit arithmetic; the constant folds the offsets.
     const uint32_t c = (1u - kFloorMagicBits) * (1u + px + pxy);
     s.base = __float_as_uint(tx) + px * __float_as_uint(ty) + pxy * __float_as_uint(tz) + c;
+    s.ix = (int)(__float_as_uint(tx) - kFloorMagicBits);
+    s.iy = (int)(__float_as_uint(ty) - kFloorMagicBits);
+    s.iz = (int)(__float_as_uint(tz) - kFloorMagicBits);
     return s;
+}
+
+// Brick skipping.  A cell whose lower corner x0 lies in brick b = max(x0, 0) / 8
+// (per axis) reads corners from tiles b and b + 1 only; brick_bound is the
+// bound of those 8 tiles (MapPlanes::bb).  A trilinear value is a convex
+// combination of its corners, so if the bound is below tau by more than the
+// lerps' rounding (7 lerps, each within ~3 2^-24 of the corners' magnitude:
+// 2^-18 (1 + max |corner|) is a safe margin), no sample in the brick can be a
+// hit and the march may jump over it.
+__device__ __forceinline__ float2 brick_bound(const KParams& P, const float2* __restrict__ tb, int bx, int by,
+                                              int bz) {
+    const int bx1 = min(bx + 1, P.nbx - 1), by1 = min(by + 1, P.nby - 1), bz1 = min(bz + 1, P.nbz - 1);
+    float m = -INFINITY, a = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int x = c & 1 ? bx1 : bx, y = c & 2 ? by1 : by, z = c & 4 ? bz1 : bz;
+        const float2 t = tb[x + P.nbx * (y + P.nby * z)];
+        m = fmaxf(m, t.x);
+        a = fmaxf(a, t.y);
+    }
+    return make_float2(m, a);
+}
+
+__device__ __forceinline__ bool brick_skippable(const KParams& P, const float2* __restrict__ bb, int brick) {
+    const float2 t = __ldg(bb + brick);
+    return t.x < P.tau32 - 0x1p-18f * (1.0f + t.y);
+}
+
+// The first sample index at or after which the ray may leave brick (bx, by, bz):
+// the exit distance of the brick's cell-corner box [8b, 8b + 8) (lower bound -1
+// for b = 0), pulled 1e-3 voxels inside, over eps, plus one.  irg are the
+// reciprocals of the ray's grid direction (0 where it is 0) and ieps = 1 / eps;
+// the products stand in for the quotients, whose rounding (and that of the
+// sample positions) is far below the 1e-3 voxel margin.  Every sample before
+// the returned index has its cell in the brick.
+__device__ __forceinline__ int brick_exit(const KParams& P, int bx, int by, int bz, float irgx, float irgy,
+                                          float irgz, float cgx, float cgy, float cgz, float ieps) {
+    constexpr float m = 1e-3f;
+    float dmin = INFINITY;
+    const int b3[3] = {bx, by, bz};
+    const float ir3[3] = {irgx, irgy, irgz}, cg3[3] = {cgx, cgy, cgz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = b3[a] == 0 ? -1.0f : 8.0f * (float)b3[a];
+        const float hi = 8.0f * (float)(b3[a] + 1);
+        if (ir3[a] > 0.0f) dmin = fminf(dmin, (hi - m - cg3[a]) * ir3[a]);
+        else if (ir3[a] < 0.0f) dmin = fminf(dmin, (lo + m - cg3[a]) * ir3[a]);
+    }
+    const float kn = floorf(dmin * ieps) + 1.0f;
+    return kn < (float)(P.kmax + 1) ? (int)kn : P.kmax + 1;
 }
 
 }  // namespace render_detail
@@ -89,11 +143,13 @@ __device__ __forceinline__ Sample cell_of(uint32_t px, uint32_t pxy, float gx, f
 // and centre in shared memory.  anchor_src / anchor_dst: when given, the
 // tile at (0, 0) copies the 7 pose doubles.
 //
-// The march runs in two loops with the same body: samples 1..k_safe, which
-// a conservative FP32 bound (one voxel of margin, far above the rounding of
-// the bound and of the sample positions) shows to lie inside the grid, skip
-// the grid test; the samples after them are tested one by one.  The samples,
-// corner indices and hit index are those of the one-loop march.
+// The march tests the grid bounds only for samples after k_safe, which a
+// conservative FP32 bound (one voxel of margin, far above the rounding of the
+// bound and of the sample positions) keeps inside the grid, and (with
+// P.skip) jumps over 8^3 bricks whose occupancy bound shows that no sample
+// in them can be a hit.  The samples evaluated, their corner indices and
+// the hit index are those of the one-loop march over every sample; the
+// value of a jumped-over sample k - 1 is recomputed at the hit.
 template <bool BF16, bool DETAIL, int PX>
 __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, const float* sc, const MapPlanes& M,
                                             float* __restrict__ depth, float* __restrict__ rgb,
@@ -141,36 +197,54 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
         }
 
         float f = 0.0f, f_prev = 0.0f;
+        bool prev_ok = false;   // f_prev holds the value of sample k - 1
         int k = 1;
-        float kf = 1.0f;   // (float)k, exact below 2^24
+        float kf = 1.0f;        // (float)k, exact below 2^24
         bool hit = false;
         render_detail::Sample cur;
         float pfx = -2.0f, pfy = -2.0f, pfz = -2.0f;
-        auto step = [&](float gx, float gy, float gz) -> bool {
+        bool fresh = true;      // DETAIL: the next evaluated sample starts a new run of corners
+        int cur_brick = -1;
+        bool cur_skip = false;
+        const bool skip = P.skip && M.bb != nullptr;
+        // for the brick exits: 1 / rg (0 where rg = 0) and 1 / eps
+        const float irgx = rgx != 0.0f ? 1.0f / rgx : 0.0f, irgy = rgy != 0.0f ? 1.0f / rgy : 0.0f,
+                    irgz = rgz != 0.0f ? 1.0f / rgz : 0.0f, ieps = 1.0f / P.eps32;
+        while (k <= P.kmax) {
+            const float d = __fmul_rn(kf, P.eps32);
+            const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
+            if (k > k_safe && !(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
+            cur = render_detail::cell_of(px, pxy, gx, gy, gz);
+            if (skip) {
+                const int bx = max(cur.ix, 0) >> 3, by = max(cur.iy, 0) >> 3, bz = max(cur.iz, 0) >> 3;
+                const int brick = bx + P.nbx * (by + P.nby * bz);
+                if (brick != cur_brick) {
+                    cur_brick = brick;
+                    cur_skip = render_detail::brick_skippable(P, M.bb, brick);
+                }
+                if (cur_skip) {   // no sample of this brick can be a hit: jump past it
+                    const int kn = render_detail::brick_exit(P, bx, by, bz, irgx, irgy, irgz, cgx, cgy, cgz, ieps);
+                    k = kn > k ? kn : k + 1;
+                    kf = (float)k;
+                    prev_ok = false;
+                    fresh = true;
+                    continue;
+                }
+            }
             ++nsamp;
             if (DETAIL) {   // consecutive cells share 8 >> (axes changed) corners (steps below one voxel)
                 const float flx = floorf(gx), fly = floorf(gy), flz = floorf(gz);
                 const int ch = (flx != pfx) + (fly != pfy) + (flz != pfz);
-                uniq += nsamp == 1 ? 8u : 8u - (8u >> ch);
+                uniq += fresh ? 8u : 8u - (8u >> ch);
                 pfx = flx; pfy = fly; pfz = flz;
+                fresh = false;
             }
-            cur = render_detail::cell_of(px, pxy, gx, gy, gz);
             f = render_detail::trilinear<BF16, PX>(M.occ, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            if (f > P.tau32) return true;
+            if (f > P.tau32) { hit = true; break; }
             f_prev = f;
-            return false;
-        };
-        for (; k <= k_safe; ++k, kf += 1.0f) {
-            const float d = __fmul_rn(kf, P.eps32);
-            if (step(__fmaf_rn(d, rgx, cgx), __fmaf_rn(d, rgy, cgy), __fmaf_rn(d, rgz, cgz))) { hit = true; break; }
-        }
-        if (!hit) {
-            for (; k <= P.kmax; ++k, kf += 1.0f) {
-                const float d = __fmul_rn(kf, P.eps32);
-                const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
-                if (!(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
-                if (step(gx, gy, gz)) { hit = true; break; }
-            }
+            prev_ok = true;
+            ++k;
+            kf += 1.0f;
         }
         if (hit && k == 1) hk = -1;
         if (hit && k >= 2) {
@@ -179,6 +253,8 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
             const float d1 = __fmul_rn((float)(k - 1), P.eps32);
             const render_detail::Sample prev = render_detail::cell_of(px, pxy, __fmaf_rn(d1, rgx, cgx), __fmaf_rn(d1, rgy, cgy),
                                         __fmaf_rn(d1, rgz, cgz));
+            // sample k - 1 was jumped over: its value, by the same recipe
+            if (!prev_ok) f_prev = render_detail::trilinear<BF16, PX>(M.occ, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
             const float alpha = __fdiv_rn(P.tau32 - f_prev, f - f_prev);
             const float dk = __fmul_rn((float)k, P.eps32);
             const float dstar = fmaf(alpha, dk - d1, d1);

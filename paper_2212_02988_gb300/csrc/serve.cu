@@ -45,7 +45,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Byte layout of one stream's single device allocation.
 struct StreamLayout {
-    size_t plane, off_map, off_depth, off_rgb, off_omask, off_adepth, off_argb, off_amask, off_a0, off_a1,
+    size_t plane, off_map, off_tb, off_bb, off_depth, off_rgb, off_omask, off_adepth, off_argb, off_amask, off_a0, off_a1,
         off_dev, off_stats, off_partials, off_counter, total;
     int max_blocks;
 };
@@ -66,6 +66,8 @@ StreamLayout layout_of(const prism_config* c, int storage, int sms) {
     auto take = [&](size_t bytes) { const size_t at = o; o += align256(bytes); return at; };
     L.plane = align256(npad * es);
     L.off_map = take(6 * L.plane);
+    L.off_tb = take((size_t)(c->nx / 8) * (c->ny / 8) * (c->nz / 8) * sizeof(float2));
+    L.off_bb = take((size_t)(c->nx / 8) * (c->ny / 8) * (c->nz / 8) * sizeof(float2));
     L.off_depth = take(npix * 4);
     L.off_rgb = take(npix * 12);
     L.off_omask = take(npix);
@@ -216,6 +218,8 @@ cudaError_t setup_stream(prism_server* S, Stream* st, int slot, int* kernels) {
     d.M.b = b + L.off_map + 3 * L.plane;
     d.M.var_occ = b + L.off_map + 4 * L.plane;
     d.M.var_rgb = b + L.off_map + 5 * L.plane;
+    d.M.tb = (float2*)(b + L.off_tb);
+    d.M.bb = (float2*)(b + L.off_bb);
     d.dev = (DevState*)(b + L.off_dev);
     d.stats = (DevStats*)(b + L.off_stats);
     d.depth = (float*)(b + L.off_depth);
@@ -243,6 +247,8 @@ cudaError_t setup_stream(prism_server* S, Stream* st, int slot, int* kernels) {
             return e;
         *kernels += 1;
     }
+    if ((e = launch_tile_bounds(st->kp, d.M, S->stream)) != cudaSuccess) return e;
+    *kernels += 2;
     *kernels += 1;
     // first state, as prism_set_state writes it (normalised pose, zero anchor)
     DevState ds;
@@ -391,7 +397,7 @@ void run_batch(prism_server* S, std::unique_lock<std::mutex>& lk) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.out, S->d_out, sizeof(ServeOut) * B.n, cudaMemcpyDeviceToHost, S->stream);
     if (e == cudaSuccess) e = cudaEventRecord(R.done, S->stream);
     lk.lock();
-    S->launches += 8 + n_gn;
+    S->launches += 9 + n_gn;
     if (use_graph) S->graph_launches += 1;
     if (e != cudaSuccess) set_failed(S, std::string("batch launch: ") + cudaGetErrorString(e));
     S->cv_done.notify_all();   // wakes the completion thread

@@ -112,6 +112,19 @@ __global__ void __launch_bounds__(256) kb_fuse(const SlotDesc* __restrict__ slot
     }
 }
 
+// The brick bounds of every member after its fuse (render_dev.cuh).
+__global__ void __launch_bounds__(256) kb_bricks(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
+    pdl_enter();
+    const int total = b->fuse_off[b->n];   // one brick per 8^3 tile
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int i = find_member(b->fuse_off, b->n, e);
+        const SlotDesc& S = slots[b->m[i].slot];
+        const int br = e - b->fuse_off[i];
+        const int bx = br % S.P.nbx, by = (br / S.P.nbx) % S.P.nby, bz = br / (S.P.nbx * S.P.nby);
+        S.M.bb[br] = render_detail::brick_bound(S.P, S.M.tb, bx, by, bz);
+    }
+}
+
 // The anchor render at each member's new state mean; item = one 16x8 tile.
 template <bool BF16>
 __global__ void __launch_bounds__(128) kb_render(const SlotDesc* __restrict__ slots, BatchDesc* __restrict__ b,
@@ -201,6 +214,7 @@ cudaError_t launch_batch_step(const SlotDesc* slots, BatchDesc* batch, const dou
     PRISM_BK(launch_pdl(kb_track<TRACK_LAPLACE>, g.track_lap, 256, s, slots, batch, n_gn));
     if (bf16) PRISM_BK(launch_pdl(kb_fuse<true>, g.fuse, 256, s, slots, batch));
     else PRISM_BK(launch_pdl(kb_fuse<false>, g.fuse, 256, s, slots, batch));
+    PRISM_BK(launch_pdl(kb_bricks, g.pix, 256, s, slots, batch));
     if (bf16) PRISM_BK(launch_pdl(kb_render<true>, g.render, 128, s, slots, batch, n_gn + 1));
     else PRISM_BK(launch_pdl(kb_render<false>, g.render, 128, s, slots, batch, n_gn + 1));
     PRISM_BK(launch_pdl(kb_mask, g.pix, 256, s, slots, batch, 1));

@@ -67,6 +67,7 @@ def test_config_default_is_the_paper(lib):
         gold["gate_geo"]["value"], gold["gate_rgb"]["value"], gold["b_geo"]["value"], gold["b_rgb"]["value"],
         gold["ema"]["value"])
     assert c.fx == 560.0 and c.cx == 319.5 and c.cy == 239.5
+    assert c.skip_empty == 1
 
 
 def test_invalid_config_rejected_without_gpu_work(lib):
@@ -77,6 +78,9 @@ def test_invalid_config_rejected_without_gpu_work(lib):
     h = C.c_void_p()
     assert L.prism_create_map(C.byref(c), None, None, C.byref(h)) == lib.EINVAL
     assert b"multiples of 8" in L.prism_last_error(None)
+    c.nx, c.skip_empty = 64, 2
+    assert L.prism_create_map(C.byref(c), None, None, C.byref(h)) == lib.EINVAL
+    assert b"skip_empty" in L.prism_last_error(None)
     assert L.prism_destroy(None) == lib.EINVAL
     assert L.prism_status_string(lib.ENOTPD) == b"matrix not positive definite"
 
