@@ -46,8 +46,34 @@ __device__ void store_ghosts(const KParams& P, void* plane, int x, int y, int z,
 
 }  // namespace fuse_detail
 
-// One 8x8x8 tile (256 threads).
-template <bool BF16>
+// Conservative frustum cull of tile (bx, by, bz): its bounding sphere
+// (centre c, radius r, with a margin far above FP32 rounding) lies entirely
+// behind the camera or outside a side plane of the pixel range
+// u, v in [-1/2, W - 1/2) x [-1/2, H - 1/2).  sM / sb: world-to-camera.
+__device__ __forceinline__ bool tile_outside_frustum(const KParams& P, const float* sM, const float* sb, int bx,
+                                                     int by, int bz) {
+    const float h = 4.0f * P.vs32;
+    const float cw[3] = {P.o32[0] + (8 * bx + 4) * P.vs32, P.o32[1] + (8 * by + 4) * P.vs32,
+                         P.o32[2] + (8 * bz + 4) * P.vs32};
+    float c[3];
+    for (int r = 0; r < 3; ++r) c[r] = sM[3 * r] * cw[0] + sM[3 * r + 1] * cw[1] + sM[3 * r + 2] * cw[2] + sb[r];
+    const float rad = 1.7321f * h * 1.001f + 1e-4f;
+    bool out = c[2] < -rad;
+    auto plane = [&](float a, float b) {   // half-space a * x_axis + b * z >= 0, unit-normalised
+        return rsqrtf(a * a + b * b);
+    };
+    const float l0 = P.cx32 + 0.5f, l1 = (float)P.W - 0.5f - P.cx32;
+    const float t0 = P.cy32 + 0.5f, t1 = (float)P.H - 0.5f - P.cy32;
+    out = out || (P.fx32 * c[0] + l0 * c[2]) * plane(P.fx32, l0) < -rad;
+    out = out || (-P.fx32 * c[0] + l1 * c[2]) * plane(P.fx32, l1) < -rad;
+    out = out || (P.fy32 * c[1] + t0 * c[2]) * plane(P.fy32, t0) < -rad;
+    out = out || (-P.fy32 * c[1] + t1 * c[2]) * plane(P.fy32, t1) < -rad;
+    return out;
+}
+
+// One 8x8x8 tile (256 threads); CULL: test the frustum first (else the
+// caller has listed only tiles that pass it).
+template <bool BF16, bool CULL = true>
 __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, const float* __restrict__ w2c,
                                           const float* __restrict__ depth, const float* __restrict__ rgb,
                                           const uint8_t* __restrict__ mask, DevStats* __restrict__ stats,
@@ -60,31 +86,11 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
         else sb[threadIdx.x - 9] = w2c[threadIdx.x];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // Conservative frustum cull of the whole tile: its bounding sphere
-        // (centre c, radius r, with a margin far above FP32 rounding) lies
-        // entirely behind the camera or outside a side plane of the pixel
-        // range u, v in [-1/2, W - 1/2) x [-1/2, H - 1/2).
-        const float h = 4.0f * P.vs32;
-        const float cw[3] = {P.o32[0] + (8 * bx + 4) * P.vs32, P.o32[1] + (8 * by + 4) * P.vs32,
-                             P.o32[2] + (8 * bz + 4) * P.vs32};
-        float c[3];
-        for (int r = 0; r < 3; ++r) c[r] = sM[3 * r] * cw[0] + sM[3 * r + 1] * cw[1] + sM[3 * r + 2] * cw[2] + sb[r];
-        const float rad = 1.7321f * h * 1.001f + 1e-4f;
-        bool out = c[2] < -rad;
-        auto plane = [&](float a, float b) {   // half-space a * x_axis + b * z >= 0, unit-normalised
-            return rsqrtf(a * a + b * b);
-        };
-        float l0 = P.cx32 + 0.5f, l1 = (float)P.W - 0.5f - P.cx32;
-        float t0 = P.cy32 + 0.5f, t1 = (float)P.H - 0.5f - P.cy32;
-        out = out || (P.fx32 * c[0] + l0 * c[2]) * plane(P.fx32, l0) < -rad;
-        out = out || (-P.fx32 * c[0] + l1 * c[2]) * plane(P.fx32, l1) < -rad;
-        out = out || (P.fy32 * c[1] + t0 * c[2]) * plane(P.fy32, t0) < -rad;
-        out = out || (-P.fy32 * c[1] + t1 * c[2]) * plane(P.fy32, t1) < -rad;
-        s_skip = out;
+    if (CULL) {
+        if (threadIdx.x == 0) s_skip = tile_outside_frustum(P, sM, sb, bx, by, bz);
+        __syncthreads();
+        if (s_skip) return;
     }
-    __syncthreads();
-    if (s_skip) return;
     const float fW1 = (float)(P.W - 1), fH1 = (float)(P.H - 1);
     unsigned int n_occ = 0, n_col = 0;
 #pragma unroll

@@ -117,6 +117,8 @@ struct prism_ctx {
     DevState* dstate = nullptr;
     DevStats* dstats = nullptr;
     float* partials = nullptr;
+    int* fuse_list = nullptr;
+    unsigned int* fuse_ctr = nullptr;
     unsigned int* counter = nullptr;
     int max_blocks = 0;
     double* d_imu = nullptr;
@@ -230,7 +232,7 @@ void collect_timing(prism_handle h) {
 
 void free_all(prism_handle h) {
     void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->o_mask,
-                    h->dstate, h->dstats, h->partials, h->counter, h->d_imu};
+                    h->dstate, h->dstats, h->partials, h->counter, h->d_imu, h->fuse_list, h->fuse_ctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -347,7 +349,10 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb, b
 prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool mask_ready) {
     PhaseTimer t(h, PH_FUSE);
     if (!mask_ready) LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
-    LAUNCH(h, launch_fuse(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->stream), "fuse");
+    LAUNCH(h, launch_fuse_listed(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->fuse_list,
+                                 h->fuse_ctr, h->stream),
+           "fuse");
+    ++h->launches;   // (two kernels: the frustum list and the update)
     if (h->kp.skip) LAUNCH(h, launch_brick_bounds(h->kp, h->map, h->stream), "brick bounds");
     return PRISM_OK;
 }
@@ -516,7 +521,9 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         dalloc(h, &h->a0, npix * 16) || dalloc(h, &h->a1, npix * 16) || dalloc(h, &h->o_mask, npix) ||
         dalloc(h, &h->dstate, sizeof(DevState)) || dalloc(h, &h->dstats, sizeof(DevStats)) ||
         dalloc(h, &h->partials, (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(float)) ||
-        dalloc(h, &h->counter, sizeof(unsigned int)))
+        dalloc(h, &h->counter, sizeof(unsigned int)) ||
+        dalloc(h, &h->fuse_list, (size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(int)) ||
+        dalloc(h, &h->fuse_ctr, 2 * sizeof(unsigned int)))
         return cleanup(PRISM_ENOMEM, "device allocation failed");
     cudaGetLastError();
     {   // the prediction stream (high priority: its one block is scheduled ahead of waiting fuse tiles)
@@ -536,6 +543,7 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         return cleanup(PRISM_ECUDA, std::string("map fill: ") + cudaGetErrorString(e));
     if ((e = cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->fuse_ctr, 0, 2 * sizeof(unsigned int), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->dstate, 0, sizeof(DevState), h->stream)) != cudaSuccess)
         return cleanup(PRISM_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
     prism_state init;

@@ -297,35 +297,41 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         else if (tid >= 167 && tid < 170) st[tid] = dev->pw[tid - 167];
         else if (tid == 170) s_nloc = dev->n_localised;
     }
-    // Fixed-order sum of the partials: warp w takes values w, w + 8, ...;
-    // lane l adds blocks l, l + 32, ... into two alternating accumulators,
-    // then a fixed shuffle tree; the order never depends on scheduling.
-    // All of a lane's loads are issued before the first add (the loop below
-    // is fully unrolled; G <= 32 * kMaxPerLane is checked at launch).
-    // Warp w sums rows v = w, w + 8, ... (at most kRows); the loads of all its
-    // rows are issued before the first add.
+    // Fixed-order sum of the partials: warp w sums rows v = w, w + 8, ...
+    // (at most kRows); lane l adds blocks 4l .. 4l + 3, then 4 (l + 32) .., in
+    // order, then a fixed shuffle tree; the order never depends on scheduling.
+    // All of a warp's (float4) loads are issued before the first add (the
+    // loops are fully unrolled; G <= 32 * kMaxPerLane is checked at launch).
     // The sums stay FP32 (a GB300 SM retires about two FP64 adds per clock,
     // so ~9,000 of them would dominate this block's tail; FP32 keeps the
     // sums to ~1e-6 relative, far inside what a Gauss-Newton step or the
     // Laplace covariance needs) and are widened to FP64 for the finish.
     const int G = nvb;
     constexpr int kRows = (N + kWarps - 1) / kWarps;
-    float x[kRows][kMaxPerLane];
+    constexpr int kQuads = kMaxPerLane / 4;   // float4 loads per row and lane (rows are 16-byte aligned)
+    float4 x[kRows][kQuads];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
         const int v = warp + kWarps * q;
-        const float* row = partials + (size_t)(v < N ? v : 0) * pstride;
+        const float4* row = reinterpret_cast<const float4*>(partials + (size_t)(v < N ? v : 0) * pstride);
 #pragma unroll
-        for (int j = 0; j < kMaxPerLane; ++j) {
-            const int b = lane + 32 * j;
-            x[q][j] = (v < N && b < G) ? __ldcg(row + b) : 0.0f;
+        for (int j = 0; j < kQuads; ++j) {
+            const int b = 4 * (lane + 32 * j);
+            float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (v < N && b < G) {
+                t = __ldcg(row + lane + 32 * j);
+                if (b + 1 >= G) t.y = 0.0f;
+                if (b + 2 >= G) t.z = 0.0f;
+                if (b + 3 >= G) t.w = 0.0f;
+            }
+            x[q][j] = t;
         }
     }
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
-        float s = x[q][0];
+        float s = 0.0f;
 #pragma unroll
-        for (int j = 1; j < kMaxPerLane; ++j) s += x[q][j];
+        for (int j = 0; j < kQuads; ++j) s = (((s + x[q][j].x) + x[q][j].y) + x[q][j].z) + x[q][j].w;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const int v = warp + kWarps * q;
