@@ -12,7 +12,10 @@ __global__ void __launch_bounds__(256) k_fuse(KParams P, MapPlanes M, const floa
                                               const float* __restrict__ depth, const float* __restrict__ rgb,
                                               const uint8_t* __restrict__ mask, DevStats* __restrict__ stats) {
     pdl_enter();
-    fuse_tile<BF16>(P, M, w2c, depth, rgb, mask, stats, blockIdx.x);
+    __shared__ float sM[9], sb[3];
+    load_w2c(w2c, sM, sb);
+    __syncthreads();
+    fuse_tile<BF16>(P, M, sM, sb, depth, rgb, mask, stats, blockIdx.x);
 }
 
 // The tiles in the frustum, appended to `list` (ctr[0] counts them; the
@@ -21,10 +24,7 @@ __global__ void __launch_bounds__(256) k_fuse_cull(KParams P, const float* __res
                                                    unsigned int* __restrict__ ctr) {
     pdl_enter();
     __shared__ float sM[9], sb[3];
-    if (threadIdx.x < 12) {
-        if (threadIdx.x < 9) sM[threadIdx.x] = w2c[threadIdx.x];
-        else sb[threadIdx.x - 9] = w2c[threadIdx.x];
-    }
+    load_w2c(w2c, sM, sb);
     __syncthreads();
     const int n = P.nbx * P.nby * P.nbz;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,10 +46,13 @@ __global__ void __launch_bounds__(256) k_fuse_list(KParams P, MapPlanes M, const
                                                    const uint8_t* __restrict__ mask, DevStats* __restrict__ stats,
                                                    const int* __restrict__ list, unsigned int* __restrict__ ctr) {
     pdl_enter();
+    __shared__ float sM[9], sb[3];
+    load_w2c(w2c, sM, sb);
+    __syncthreads();
     const unsigned int count = ctr[0];
     for (unsigned int i = blockIdx.x; i < count; i += gridDim.x) {
-        fuse_tile<BF16, false>(P, M, w2c, depth, rgb, mask, stats, (uint32_t)list[i]);
-        __syncthreads();   // the tile's shared matrices are reused by the next item
+        fuse_tile<BF16, false>(P, M, sM, sb, depth, rgb, mask, stats, (uint32_t)list[i]);
+        __syncthreads();   // the tile's shared reduction scratch is reused by the next item
     }
     __shared__ int s_last;
     if (threadIdx.x == 0) {

@@ -71,21 +71,25 @@ __device__ __forceinline__ bool tile_outside_frustum(const KParams& P, const flo
     return out;
 }
 
-// One 8x8x8 tile (256 threads); CULL: test the frustum first (else the
-// caller has listed only tiles that pass it).
-template <bool BF16, bool CULL = true>
-__device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, const float* __restrict__ w2c,
-                                          const float* __restrict__ depth, const float* __restrict__ rgb,
-                                          const uint8_t* __restrict__ mask, DevStats* __restrict__ stats,
-                                          uint32_t tile) {
-    __shared__ float sM[9], sb[3];
-    __shared__ int s_skip;
-    const int bx = tile % P.nbx, by = (tile / P.nbx) % P.nby, bz = tile / (P.nbx * P.nby);
+// The world-to-camera matrices into shared memory (12 threads; the caller
+// synchronises before use).
+__device__ __forceinline__ void load_w2c(const float* __restrict__ w2c, float* sM, float* sb) {
     if (threadIdx.x < 12) {
         if (threadIdx.x < 9) sM[threadIdx.x] = w2c[threadIdx.x];
         else sb[threadIdx.x - 9] = w2c[threadIdx.x];
     }
-    __syncthreads();
+}
+
+// One 8x8x8 tile (256 threads); sM / sb: the world-to-camera matrices in
+// shared memory, loaded by the caller; CULL: test the frustum first (else the
+// caller has listed only tiles that pass it).
+template <bool BF16, bool CULL = true>
+__device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, const float* sM, const float* sb,
+                                          const float* __restrict__ depth, const float* __restrict__ rgb,
+                                          const uint8_t* __restrict__ mask, DevStats* __restrict__ stats,
+                                          uint32_t tile) {
+    __shared__ int s_skip;
+    const int bx = tile % P.nbx, by = (tile / P.nbx) % P.nby, bz = tile / (P.nbx * P.nby);
     if (CULL) {
         if (threadIdx.x == 0) s_skip = tile_outside_frustum(P, sM, sb, bx, by, bz);
         __syncthreads();

@@ -262,6 +262,25 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// Warp reduce-scatter of 32 values per lane: on return v[0] of lane l holds
+// the warp's sum of value l.  A butterfly: at offset w each lane keeps the
+// half of its live values selected by bit w of its lane index and adds the
+// partner's copy of that half (31 shuffles instead of 32 x 5 for 32 separate
+// sums; the order of the additions is fixed).
+__device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            const float send = upper ? v[i] : v[i + w];
+            const float keep = upper ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+}
+
 // Block-wide (max v, max a) over a 256-thread block, stored by thread 0 as
 // the tile bound of `tile` (every thread must call it).
 __device__ __forceinline__ void tile_bound_store(float2* tb, uint32_t tile, float v, float a) {

@@ -103,12 +103,15 @@ __global__ void __launch_bounds__(256, 2) kb_track(const SlotDesc* __restrict__ 
 template <bool BF16>
 __global__ void __launch_bounds__(256) kb_fuse(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
     pdl_enter();
+    __shared__ float sM[9], sb[3];
     const int total = b->fuse_off[b->n];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int i = find_member(b->fuse_off, b->n, item);
         const SlotDesc& S = slots[b->m[i].slot];
-        fuse_tile<BF16>(S.P, S.M, S.dev->w2c, S.depth, S.rgb, S.o_mask, S.stats, (uint32_t)(item - b->fuse_off[i]));
-        __syncthreads();   // the tile's shared matrices and cull flag are reused by the next item
+        load_w2c(S.dev->w2c, sM, sb);
+        __syncthreads();
+        fuse_tile<BF16>(S.P, S.M, sM, sb, S.depth, S.rgb, S.o_mask, S.stats, (uint32_t)(item - b->fuse_off[i]));
+        __syncthreads();   // the shared matrices, cull flag and reduction scratch are reused by the next item
     }
 }
 

@@ -248,11 +248,14 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         track_eval<MODE>(P, sb, q1, acc);
     }
 
-    // ---- block reduction: FP32, in a fixed order (warp shuffles, then warps 0..7) ----
+    // ---- block reduction: FP32, in a fixed order (warp reduce-scatter, then warps 0..7) ----
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        float s = warp_sum(acc[i]);
-        if (lane == 0) swarp[warp][i] = s;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = c0 + i < N ? acc[c0 + i] : 0.0f;
+        warp_reduce_scatter32(v);
+        if (c0 + lane < N) swarp[warp][c0 + lane] = v[0];
     }
     __syncthreads();
     if (tid < N) {   // partials are stored value-major: partials[v * pstride + block]
