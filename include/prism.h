@@ -224,9 +224,9 @@ prism_status prism_normal_equations(prism_handle h, const double* pose7, const f
  * a HOST array of 80 doubles laid out as for prism_normal_equations.  Only
  * cfg's image size, intrinsics, gates, scales, floors and disc are used.
  *
- * All scratch (packed anchor, validity masks, per-block partial sums, ticket
- * counter, device state) lives in one static device array of
- * PRISM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * All scratch (packed anchor, the observation's validity mask, per-block
+ * partial sums, ticket counter, device state) lives in one static device
+ * array of PRISM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
  * until the process exits; the call allocates and frees nothing.  Images
  * larger than PRISM_NOALLOC_MAX_PIXELS are rejected with PRISM_EINVAL.
  * The first call on a device looks up the array's device address

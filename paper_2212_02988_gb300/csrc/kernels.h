@@ -22,7 +22,9 @@ enum PrepKind : int {
     PREP_STATE = 0,   // c2w and w2c of the state mean
     PREP_AUX_C2W = 1, // aux = camera-to-world of the pose argument
     PREP_AUX_REL = 2, // aux = pose argument -> anchor camera
-    PREP_REL = 3      // rel = Gauss-Newton pose -> anchor camera
+    PREP_REL = 3,     // rel = Gauss-Newton pose -> anchor camera
+    PREP_REL_NEXT = 4 // as PREP_REL with the state mean's pose as the anchor's (the
+                      // anchor rendered at the current mean, which may still be in flight)
 };
 
 // The six map planes (f32 or bf16 elements), each linear with a ghost border.
@@ -50,8 +52,9 @@ cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& 
 cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s);
 // The render's compile-time plane-stride specialisation for P (0: none).
 int render_px_specialisation(const KParams& P);
-cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, const uint8_t* mask,
-                               float4* a0, float4* a1, cudaStream_t s);
+// The anchor's depth validity and packing in one pass.
+cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, float4* a0, float4* a1,
+                               cudaStream_t s);
 
 // track.cu — normal-equation passes of the localisation.
 enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2 };
@@ -61,7 +64,7 @@ enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2 };
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
-                         DevStats* stats, cudaStream_t s);
+                         DevStats* stats, cudaStream_t s, bool pdl = true);
 int track_grid(const KParams& P, int max_blocks);
 // The grid launch_track uses for `mode` (one wave of the device at most).
 int track_launch_grid(const KParams& P, int mode, int max_blocks);
@@ -73,6 +76,10 @@ constexpr int TRACK_NV_MAX = 50;   // FP32 values per block partial
 cudaError_t launch_predict(const KParams& P, DevState* dev, const double* imu, int n, double dt,
                            cudaStream_t s, bool pdl = true);
 cudaError_t launch_prep(DevState* dev, int kind, const PoseArg& pose, cudaStream_t s, bool pdl = true);
+// The prediction followed, in the same block, by the PREP_REL_NEXT matrices of
+// the prior's mean (a plain launch).
+cudaError_t launch_predict_prep(const KParams& P, DevState* dev, const double* imu, int n, double dt,
+                                cudaStream_t s);
 
 // fuse.cu — the per-voxel map update with the world-to-camera matrices
 // `w2c` (12 FP32 on the device, DevState::w2c).

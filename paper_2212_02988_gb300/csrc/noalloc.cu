@@ -6,8 +6,8 @@
 // It runs the same kernels as prism_anchor_load + prism_normal_equations
 // (depth validity, anchor packing, pose matrices, the reduction pass), but
 // every buffer those kernels need beyond the caller's inputs and outputs —
-// the packed anchor, both validity masks, the per-block partial sums, the
-// ticket counter, the device state — lives in one file-scope static device
+// the packed anchor, the observation's validity mask, the per-block partial
+// sums, the ticket counter, the device state — lives in one file-scope static device
 // array, g_noalloc_scratch, of PRISM_NOALLOC_SCRATCH_BYTES.  Each GPU that
 // loads the library holds that array until the process exits.
 //
@@ -39,8 +39,7 @@ constexpr size_t kOffCounter = align_up(kOffState + sizeof(DevState));
 constexpr size_t kOffPartials = align_up(kOffCounter + sizeof(unsigned int));
 constexpr size_t kOffA0 = align_up(kOffPartials + sizeof(float) * TRACK_NV_MAX * kMaxBlocks);
 constexpr size_t kOffA1 = align_up(kOffA0 + 16 * kPix);
-constexpr size_t kOffAMask = align_up(kOffA1 + 16 * kPix);
-constexpr size_t kOffOMask = align_up(kOffAMask + kPix);
+constexpr size_t kOffOMask = align_up(kOffA1 + 16 * kPix);
 constexpr size_t kScratchBytes = align_up(kOffOMask + kPix);
 static_assert(kScratchBytes <= PRISM_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
 
@@ -135,15 +134,13 @@ prism_status prism_normal_equations_noalloc(const prism_config* cfg, const doubl
     float* partials = (float*)(base + kOffPartials);
     float4* a0 = (float4*)(base + kOffA0);
     float4* a1 = (float4*)(base + kOffA1);
-    uint8_t* a_mask = base + kOffAMask;
     uint8_t* o_mask = base + kOffOMask;
     // the ticket counter must start at zero; the rest is fully overwritten
     NA_CK(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s), "clear counter");
     double anc[7];
     normalise_pose(anchor_pose7, anc);
     NA_CK(cudaMemcpyAsync(ds->anchor_pose, anc, sizeof(anc), cudaMemcpyHostToDevice, s), "anchor pose");
-    NA_CK(launch_depth_mask(P, anchor_depth, a_mask, s), "anchor mask");
-    NA_CK(launch_anchor_pack(P, anchor_depth, anchor_rgb, a_mask, a0, a1, s), "anchor pack");
+    NA_CK(launch_anchor_pack(P, anchor_depth, anchor_rgb, a0, a1, s), "anchor pack");
     NA_CK(launch_depth_mask(P, depth, o_mask, s), "observation mask");
     PoseArg pa{};
     normalise_pose(pose7, pa.p);

@@ -110,7 +110,6 @@ struct prism_ctx {
     void* map_block = nullptr;
     float* a_depth = nullptr;
     float* a_rgb = nullptr;
-    uint8_t* a_mask = nullptr;
     float4* a0 = nullptr;
     float4* a1 = nullptr;
     uint8_t* o_mask = nullptr;
@@ -134,6 +133,7 @@ struct prism_ctx {
     int h_imu_cap = 0;
     int imu_slot = 0;
     bool has_anchor = false;
+    bool anchor_at_mean = false;   // the anchor was rendered at the current state mean
     bool has_prior = false;
     int64_t steps = 0;
     int64_t bytes = 0;
@@ -231,7 +231,7 @@ void collect_timing(prism_handle h) {
 }
 
 void free_all(prism_handle h) {
-    void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->o_mask,
+    void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a0, h->a1, h->o_mask,
                     h->dstate, h->dstats, h->partials, h->counter, h->d_imu, h->fuse_list, h->fuse_ctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -308,6 +308,7 @@ prism_status write_state(prism_handle h, const prism_state* s) {
     LAUNCH(h, launch_prep(h->dstate, PREP_STATE, pa, h->stream), "pose matrices");
     CK(h, cudaEventRecord(h->ev_state, h->stream), "state event");
     h->has_prior = false;
+    h->anchor_at_mean = false;
     return PRISM_OK;
 }
 
@@ -320,29 +321,32 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
                "render");
     }
     PhaseTimer t(h, PH_ANCHOR);
-    LAUNCH(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
-    LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
+    LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a0, h->a1, h->stream), "anchor pack");
     h->has_anchor = true;
+    h->anchor_at_mean = true;
     return PRISM_OK;
 }
 
-// after_side: the prior was predicted on the side stream (prism_step); the
-// pose matrices wait for it.
-prism_status do_localise(prism_handle h, const float* depth, const float* rgb, bool after_side = false) {
+// after_side: the prior was predicted on the side stream (prism_step) and the
+// passes wait for it; prepped: that prediction also left the Gauss-Newton
+// start matrices (the anchor is the one rendered at the state mean).
+prism_status do_localise(prism_handle h, const float* depth, const float* rgb, bool after_side = false,
+                         bool prepped = false) {
     PhaseTimer t(h, PH_LOCALISE);
     LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
     PoseArg pa{};
     if (after_side) CK(h, cudaStreamWaitEvent(h->stream, h->ev_pred, 0), "wait for the prior");
-    LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream, !after_side), "pose matrices");
+    if (!prepped) LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream, !after_side), "pose matrices");
     for (int it = 0; it < h->cfg.n_gn; ++it)
         LAUNCH(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
-                           h->counter, h->max_blocks, h->dstats, h->stream),
+                           h->counter, h->max_blocks, h->dstats, h->stream, !(prepped && it == 0)),
            "Gauss-Newton pass");
     LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                        h->counter, h->max_blocks, h->dstats, h->stream),
        "Laplace pass");
     CK(h, cudaEventRecord(h->ev_state, h->stream), "state event");
     h->has_prior = false;
+    h->anchor_at_mean = false;
     return PRISM_OK;
 }
 
@@ -382,7 +386,9 @@ prism_status do_predict(prism_handle h, const double* imu, int32_t n, double dt)
 // prism_step's prediction: on the side stream once the posterior is final
 // (it then overlaps the previous step's fuse and render), the IMU window
 // staged through a ring of pinned buffers so that the upload is asynchronous.
-prism_status do_predict_side(prism_handle h, const double* imu, int32_t n, double dt) {
+// prep: the same kernel also derives the Gauss-Newton start matrices against
+// the state mean's camera (valid when the anchor is rendered there).
+prism_status do_predict_side(prism_handle h, const double* imu, int32_t n, double dt, bool prep) {
     if (n > h->imu_cap || n > h->h_imu_cap) {
         CK(h, cudaStreamSynchronize(h->side), "stream synchronize");
         CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
@@ -420,7 +426,8 @@ prism_status do_predict_side(prism_handle h, const double* imu, int32_t n, doubl
                                   h->side),
                "IMU upload");
         CK(h, cudaEventRecord(h->ev_imu[k], h->side), "IMU event");
-        LAUNCH(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->side, false), "predict");
+        if (prep) LAUNCH(h, launch_predict_prep(h->kp, h->dstate, h->d_imu, n, dt, h->side), "predict");
+        else LAUNCH(h, launch_predict(h->kp, h->dstate, h->d_imu, n, dt, h->side, false), "predict");
     }
     CK(h, cudaEventRecord(h->ev_pred, h->side), "prior event");
     h->has_prior = true;
@@ -517,7 +524,7 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
     h->map.b = base + 3 * plane;
     h->map.var_occ = base + 4 * plane;
     h->map.var_rgb = base + 5 * plane;
-    if (dalloc(h, &h->a_depth, npix * 4) || dalloc(h, &h->a_rgb, npix * 12) || dalloc(h, &h->a_mask, npix) ||
+    if (dalloc(h, &h->a_depth, npix * 4) || dalloc(h, &h->a_rgb, npix * 12) ||
         dalloc(h, &h->a0, npix * 16) || dalloc(h, &h->a1, npix * 16) || dalloc(h, &h->o_mask, npix) ||
         dalloc(h, &h->dstate, sizeof(DevState)) || dalloc(h, &h->dstats, sizeof(DevStats)) ||
         dalloc(h, &h->partials, (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(float)) ||
@@ -631,8 +638,9 @@ prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
         std::string why;
         if (!imu_ok(imu, n, dt, why)) return fail(h, PRISM_EINVAL, why);
         if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
-        if ((st = do_predict_side(h, imu, n, dt)) != PRISM_OK) return st;
-        if ((st = do_localise(h, depth, rgb, true)) != PRISM_OK) return st;
+        const bool prep = h->anchor_at_mean;
+        if ((st = do_predict_side(h, imu, n, dt, prep)) != PRISM_OK) return st;
+        if ((st = do_localise(h, depth, rgb, true, prep)) != PRISM_OK) return st;
         mask_ready = true;
     }
     if ((st = do_fuse(h, depth, rgb, mask_ready)) != PRISM_OK) return st;
@@ -730,9 +738,9 @@ prism_status prism_anchor_load(prism_handle h, const double* pose7, const float*
     CK(h, cudaMemcpyAsync(h->dstate->anchor_pose, pn, 7 * sizeof(double), cudaMemcpyHostToDevice, h->stream),
        "anchor pose");
     PhaseTimer t(h, PH_ANCHOR);
-    LAUNCH(h, launch_depth_mask(h->kp, h->a_depth, h->a_mask, h->stream), "anchor mask");
-    LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a_mask, h->a0, h->a1, h->stream), "anchor pack");
+    LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a0, h->a1, h->stream), "anchor pack");
     h->has_anchor = true;
+    h->anchor_at_mean = false;
     return PRISM_OK;
 }
 

@@ -29,11 +29,10 @@ __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t
 }
 
 __global__ void k_anchor_pack(KParams P, const float* __restrict__ depth, const float* __restrict__ rgb,
-                              const uint8_t* __restrict__ mask, float4* __restrict__ a0,
-                              float4* __restrict__ a1) {
+                              float4* __restrict__ a0, float4* __restrict__ a1) {
     pdl_enter();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P.W * P.H) anchor_pack_px(P, depth, rgb, mask, a0, a1, p);
+    if (p < P.W * P.H) anchor_pack_px(P, depth, rgb, a0, a1, p);
 }
 
 // ----------------------------------------------------------------- launchers
@@ -76,11 +75,10 @@ cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mas
     return cudaGetLastError();
 }
 
-cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, const uint8_t* mask,
-                               float4* a0, float4* a1, cudaStream_t s) {
-    int n = P.W * P.H;
-    launch_pdl(k_anchor_pack, (n + 255) / 256, 256, s, P, depth, rgb, mask, a0, a1);
-    return cudaGetLastError();
+cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, float4* a0, float4* a1,
+                               cudaStream_t s) {
+    const int n = P.W * P.H;
+    return launch_pdl(k_anchor_pack, (n + 255) / 256, 256, s, P, depth, rgb, a0, a1);
 }
 
 }  // namespace prism

@@ -293,28 +293,35 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
 
 // Depth validity (App. F.3, reading R19): valid iff d > 0, finite, and every
 // in-image 4-neighbour dn has |d - dn| <= disc (FP32).
-__device__ __forceinline__ void depth_mask_px(const KParams& P, const float* __restrict__ depth,
-                                              uint8_t* __restrict__ mask, int p) {
-    int u = p % P.W, v = p / P.W;
-    float d = depth[p];
+__device__ __forceinline__ bool depth_valid(const KParams& P, const float* __restrict__ depth, int u, int v) {
+    const int p = v * P.W + u;
+    const float d = depth[p];
     bool ok = (d > 0.0f) && isfinite(d);
     if (ok && u > 0) ok = fabsf(__fsub_rn(d, depth[p - 1])) <= P.disc32;
     if (ok && u < P.W - 1) ok = fabsf(__fsub_rn(d, depth[p + 1])) <= P.disc32;
     if (ok && v > 0) ok = fabsf(__fsub_rn(d, depth[p - P.W])) <= P.disc32;
     if (ok && v < P.H - 1) ok = fabsf(__fsub_rn(d, depth[p + P.W])) <= P.disc32;
-    mask[p] = (uint8_t)ok;
+    return ok;
+}
+
+__device__ __forceinline__ void depth_mask_px(const KParams& P, const float* __restrict__ depth,
+                                              uint8_t* __restrict__ mask, int p) {
+    mask[p] = (uint8_t)depth_valid(P, depth, p % P.W, p / P.W);
 }
 
 // Anchor packing (App. E.3, reading R18): per pixel
 //   a0 = (n_x, n_y, n_z, z)  with z = 0 where the normal is invalid,
 //   a1 = (r, g, b, 1 if the depth is valid else 0).
 // n = normalize((P(u+1,v) - P(u-1,v)) x (P(u,v+1) - P(u,v-1))), facing the camera.
+// The depth validity of the pixel and of its four neighbours is evaluated
+// here (depth_valid), so no mask pass runs before the packing.
 __device__ __forceinline__ void anchor_pack_px(const KParams& P, const float* __restrict__ depth,
-                                               const float* __restrict__ rgb, const uint8_t* __restrict__ mask,
-                                               float4* __restrict__ a0, float4* __restrict__ a1, int p) {
-    int u = p % P.W, v = p / P.W, W = P.W;
-    bool ok = u >= 1 && u <= P.W - 2 && v >= 1 && v <= P.H - 2 && mask[p] && mask[p - 1] && mask[p + 1] &&
-              mask[p - W] && mask[p + W];
+                                               const float* __restrict__ rgb, float4* __restrict__ a0,
+                                               float4* __restrict__ a1, int p) {
+    const int u = p % P.W, v = p / P.W, W = P.W;
+    const bool mc = depth_valid(P, depth, u, v);
+    bool ok = u >= 1 && u <= P.W - 2 && v >= 1 && v <= P.H - 2 && mc && depth_valid(P, depth, u - 1, v) &&
+              depth_valid(P, depth, u + 1, v) && depth_valid(P, depth, u, v - 1) && depth_valid(P, depth, u, v + 1);
     float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
     if (ok) {
         float a[3], b[3], c[3], d[3], pc[3];
@@ -341,7 +348,7 @@ __device__ __forceinline__ void anchor_pack_px(const KParams& P, const float* __
     }
     if (!ok) n0 = n1 = n2 = 0.0f;
     a0[p] = make_float4(n0, n1, n2, ok ? depth[p] : 0.0f);
-    a1[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], mask[p] ? 1.0f : 0.0f);
+    a1[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], mc ? 1.0f : 0.0f);
 }
 
 }  // namespace prism

@@ -45,7 +45,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Byte layout of one stream's single device allocation.
 struct StreamLayout {
-    size_t plane, off_map, off_tb, off_bb, off_depth, off_rgb, off_omask, off_adepth, off_argb, off_amask, off_a0, off_a1,
+    size_t plane, off_map, off_tb, off_bb, off_depth, off_rgb, off_omask, off_adepth, off_argb, off_a0, off_a1,
         off_dev, off_stats, off_partials, off_counter, total;
     int max_blocks;
 };
@@ -73,7 +73,6 @@ StreamLayout layout_of(const prism_config* c, int storage, int sms) {
     L.off_omask = take(npix);
     L.off_adepth = take(npix * 4);
     L.off_argb = take(npix * 12);
-    L.off_amask = take(npix);
     L.off_a0 = take(npix * 16);
     L.off_a1 = take(npix * 16);
     L.off_dev = take(sizeof(DevState));
@@ -227,7 +226,6 @@ cudaError_t setup_stream(prism_server* S, Stream* st, int slot, int* kernels) {
     d.o_mask = (uint8_t*)(b + L.off_omask);
     d.a_depth = (float*)(b + L.off_adepth);
     d.a_rgb = (float*)(b + L.off_argb);
-    d.a_mask = (uint8_t*)(b + L.off_amask);
     d.a0 = (float4*)(b + L.off_a0);
     d.a1 = (float4*)(b + L.off_a1);
     d.partials = (float*)(b + L.off_partials);
@@ -397,7 +395,7 @@ void run_batch(prism_server* S, std::unique_lock<std::mutex>& lk) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(R.out, S->d_out, sizeof(ServeOut) * B.n, cudaMemcpyDeviceToHost, S->stream);
     if (e == cudaSuccess) e = cudaEventRecord(R.done, S->stream);
     lk.lock();
-    S->launches += 9 + n_gn;
+    S->launches += 8 + n_gn;
     if (use_graph) S->graph_launches += 1;
     if (e != cudaSuccess) set_failed(S, std::string("batch launch: ") + cudaGetErrorString(e));
     S->cv_done.notify_all();   // wakes the completion thread

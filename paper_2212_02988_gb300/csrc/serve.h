@@ -35,7 +35,6 @@ struct SlotDesc {
     uint8_t* o_mask;
     float* a_depth;
     float* a_rgb;
-    uint8_t* a_mask;
     float4* a0;
     float4* a1;
     float* partials;           // localisation partials, value-major with stride pstride
@@ -85,7 +84,7 @@ struct BatchGrids {
 
 cudaError_t batch_grids(bool bf16, BatchGrids* g);
 
-// Enqueues the batched step (9 + n_gn kernels) on s.
+// Enqueues the batched step (8 + n_gn kernels) on s.
 cudaError_t launch_batch_step(const SlotDesc* slots, BatchDesc* batch, const double* imu, ServeOut* out, int n_gn,
                               bool bf16, const BatchGrids& g, cudaStream_t s);
 

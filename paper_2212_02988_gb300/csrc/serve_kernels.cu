@@ -54,20 +54,15 @@ __global__ void __launch_bounds__(256) kb_predict(const SlotDesc* __restrict__ s
     }
 }
 
-// Depth validity of the observed frames (which = 0) or of the rendered
-// anchors (which = 1).
-__global__ void __launch_bounds__(256) kb_mask(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b,
-                                               int which) {
+// Depth validity of the observed frames.
+__global__ void __launch_bounds__(256) kb_mask(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
     pdl_enter();
     const int total = b->pix_off[b->n];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int i = find_member(b->pix_off, b->n, item);
         const SlotDesc& S = slots[b->m[i].slot];
         const int p = (item - b->pix_off[i]) * 256 + threadIdx.x;
-        if (p < S.P.W * S.P.H) {
-            if (which == 0) depth_mask_px(S.P, S.depth, S.o_mask, p);
-            else depth_mask_px(S.P, S.a_depth, S.a_mask, p);
-        }
+        if (p < S.P.W * S.P.H) depth_mask_px(S.P, S.depth, S.o_mask, p);
     }
 }
 
@@ -78,7 +73,7 @@ __global__ void __launch_bounds__(256) kb_pack(const SlotDesc* __restrict__ slot
         const int i = find_member(b->pix_off, b->n, item);
         const SlotDesc& S = slots[b->m[i].slot];
         const int p = (item - b->pix_off[i]) * 256 + threadIdx.x;
-        if (p < S.P.W * S.P.H) anchor_pack_px(S.P, S.a_depth, S.a_rgb, S.a_mask, S.a0, S.a1, p);
+        if (p < S.P.W * S.P.H) anchor_pack_px(S.P, S.a_depth, S.a_rgb, S.a0, S.a1, p);
     }
 }
 
@@ -212,7 +207,7 @@ cudaError_t launch_batch_step(const SlotDesc* slots, BatchDesc* batch, const dou
         if ((e = (call)) != cudaSuccess) return e; \
     } while (0)
     PRISM_BK(launch_pdl(kb_predict, kServeMaxSlots, 256, s, slots, batch, imu));
-    PRISM_BK(launch_pdl(kb_mask, g.pix, 256, s, slots, batch, 0));
+    PRISM_BK(launch_pdl(kb_mask, g.pix, 256, s, slots, batch));
     for (int it = 0; it < n_gn; ++it) PRISM_BK(launch_pdl(kb_track<TRACK_GN>, g.track_gn, 256, s, slots, batch, it));
     PRISM_BK(launch_pdl(kb_track<TRACK_LAPLACE>, g.track_lap, 256, s, slots, batch, n_gn));
     if (bf16) PRISM_BK(launch_pdl(kb_fuse<true>, g.fuse, 256, s, slots, batch));
@@ -220,7 +215,6 @@ cudaError_t launch_batch_step(const SlotDesc* slots, BatchDesc* batch, const dou
     PRISM_BK(launch_pdl(kb_bricks, g.pix, 256, s, slots, batch));
     if (bf16) PRISM_BK(launch_pdl(kb_render<true>, g.render, 128, s, slots, batch, n_gn + 1));
     else PRISM_BK(launch_pdl(kb_render<false>, g.render, 128, s, slots, batch, n_gn + 1));
-    PRISM_BK(launch_pdl(kb_mask, g.pix, 256, s, slots, batch, 1));
     PRISM_BK(launch_pdl(kb_pack, g.pix, 256, s, slots, batch));
     PRISM_BK(launch_pdl(kb_out, kServeMaxSlots, 256, s, slots, batch, out));
 #undef PRISM_BK

@@ -202,10 +202,12 @@ __device__ __forceinline__ void prep_mats_warp(DevState* dev, int kind, const Po
             warp_mats_rel(pose.p, dev->anchor_pose, dev->aux);
             break;
         default: {
-            warp_mats_rel(dev->cur_pose, dev->anchor_pose, dev->rel);
+            // t[3] and q[4] are contiguous: the state mean's pose
+            const double* anchor = kind == PREP_REL_NEXT ? dev->t : dev->anchor_pose;
+            warp_mats_rel(dev->cur_pose, anchor, dev->rel);
             // C0 = Ra^T, C1 = Ra^T J_l(xi_theta): lanes 0..8 hold Ra entries,
             // lanes 9..17 J_l entries; lanes 18..23 L xi
-            const double* qa = dev->anchor_pose + 3;
+            const double* qa = anchor + 3;
             const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0);
             const double ra = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], e);
             const double jl = so3_jl_entry(dev->xi + 3, e / 3, e % 3);

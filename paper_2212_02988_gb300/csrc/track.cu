@@ -50,10 +50,15 @@ int track_launch_grid(const KParams& P, int mode, int max_blocks) {
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
-                         DevStats* stats, cudaStream_t s) {
+                         DevStats* stats, cudaStream_t s, bool pdl) {
     const int grid = track_launch_grid(P, mode, max_blocks);
     switch (mode) {
         case TRACK_GN:
+            if (!pdl) {
+                k_track<TRACK_GN><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+                                                            max_blocks, counter, stats);
+                break;
+            }
             launch_pdl(k_track<TRACK_GN>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                                                         max_blocks, counter, stats);
             break;
