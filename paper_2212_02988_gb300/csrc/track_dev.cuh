@@ -58,25 +58,75 @@ struct Layout {
     static constexpr int oCount = oCost + 1;
 };
 
+// One residual r with Jacobian J: H += w J J^T, g += w r J, Ht += J J^T / b^2,
+// with sw = sqrt(w) (the IRLS weight) and ib = 1 / b (the Laplace scale)
+// folded into J first, so that every matrix entry is one FMA.
 template <int MODE>
-__device__ __forceinline__ void accumulate(float* acc, const float J[6], float r, float w, float ib2, float cost) {
+__device__ __forceinline__ void accumulate(float* acc, const float J[6], float r, float sw, float ib, float cost) {
     using L = Layout<MODE>;
+    float Js[6], Jt[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        Js[i] = J[i] * sw;
+        Jt[i] = J[i] * ib;
+    }
     int e = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = i; j < 6; ++j, ++e) {
-            float jj = J[i] * J[j];
-            if (L::H) acc[L::oH + e] = fmaf(w, jj, acc[L::oH + e]);
-            if (L::HT) acc[L::oHT + e] = fmaf(ib2, jj, acc[L::oHT + e]);
+            if (L::H) acc[L::oH + e] = fmaf(Js[i], Js[j], acc[L::oH + e]);
+            if (L::HT) acc[L::oHT + e] = fmaf(Jt[i], Jt[j], acc[L::oHT + e]);
         }
     if (L::G) {
-        float wr = w * r;
+        const float swr = sw * r;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) acc[L::oG + i] = fmaf(wr, J[i], acc[L::oG + i]);
+        for (int i = 0; i < 6; ++i) acc[L::oG + i] = fmaf(swr, Js[i], acc[L::oG + i]);
     }
     acc[L::oCost] += cost;
 }
+
+// The FP64 state the finish reads, slot e of the staging array: prec_pp
+// 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55; Gauss-Newton also
+// the tangent map C 56..73 and L xi 74..79; Laplace also D 56..91, the pose
+// block of the previous covariance 92..127, cov_vel 128..163, pv 164..166,
+// pw 167..169.  nullptr past the mode's last slot.
+template <int MODE>
+__device__ __forceinline__ const double* stage_src(const DevState* dev, int e) {
+    if (e < 36) return dev->prec_pp + e;
+    if (e < 42) return dev->xi + (e - 36);
+    if (e < 49) return dev->anchor_pose + (e - 42);
+    if (e < 53) return dev->pq + (e - 49);
+    if (e < 56) return dev->pt + (e - 53);
+    if (MODE == TRACK_GN) {
+        if (e < 74) return dev->gn_C + (e - 56);
+        if (e < 80) return dev->gn_Lxi + (e - 74);
+    }
+    if (MODE == TRACK_LAPLACE) {
+        if (e < 92) return dev->D + (e - 56);
+        if (e < 128) return dev->cov + 12 * ((e - 92) / 6) + (e - 92) % 6;
+        if (e < 164) return dev->cov_vel + (e - 128);
+        if (e < 167) return dev->pv + (e - 164);
+        if (e < 170) return dev->pw + (e - 167);
+    }
+    return nullptr;
+}
+constexpr int kStage = 176;
+
+// Asynchronous global -> shared copies (no registers held, no stall until
+// the wait).
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const size_t g = __cvta_generic_to_global(gmem);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Reciprocals of the Laplace scales, computed once per thread.
+struct EvalConst {
+    float ib_geo, ib_rgb;
+};
 
 // A_world = T A' T^T with T = diag(Ra, Ra), one element per thread
 __device__ inline void rotate_to_world(const double* Ra, const double* Ap, double* Aw) {
@@ -142,7 +192,8 @@ __device__ __forceinline__ void track_fetch(const KParams& P, const float* sM, c
 // The remaining gates of a fetched pixel (valid anchor depth and colour taps,
 // |r_geo|, |r_rgb|) and, if kept, its four residuals and Jacobians into acc.
 template <int MODE>
-__device__ __forceinline__ void track_eval(const KParams& P, const float* sb, const TrackPix& q, float* acc) {
+__device__ __forceinline__ void track_eval(const KParams& P, const EvalConst& k, const float* sb, const TrackPix& q,
+                                           float* acc) {
     using L = Layout<MODE>;
     if (!q.ok) return;
     const float4 A = q.A, I00 = q.I00, I10 = q.I10, I01 = q.I01, I11 = q.I11;
@@ -172,13 +223,12 @@ __device__ __forceinline__ void track_eval(const KParams& P, const float* sb, co
         J[0] = ax; J[1] = ay; J[2] = az;
         J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
         const float ar = fabsf(rgeo);
-        const float w = 1.0f / (P.b_geo32 * fmaxf(ar, P.floor_geo32));
-        accumulate<MODE>(acc, J, rgeo, w, 1.0f / (P.b_geo32 * P.b_geo32), ar / P.b_geo32);
+        const float sw = rsqrtf(P.b_geo32 * fmaxf(ar, P.floor_geo32));
+        accumulate<MODE>(acc, J, rgeo, sw, k.ib_geo, ar * k.ib_geo);
     }
     const float iz = q.iz, izz = iz * iz;
     const float du0 = P.fx32 * iz, du2 = -P.fx32 * q.X0 * izz;
     const float dv1 = P.fy32 * iz, dv2 = -P.fy32 * q.X1 * izz;
-    const float wb = 1.0f / (P.b_rgb32 * P.b_rgb32);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float i00 = c == 0 ? I00.x : (c == 1 ? I00.y : I00.z);
@@ -191,8 +241,8 @@ __device__ __forceinline__ void track_eval(const KParams& P, const float* sb, co
         J[0] = ax; J[1] = ay; J[2] = az;
         J[3] = fmaf(ya1, az, -(ya2 * ay)); J[4] = fmaf(ya2, ax, -(ya0 * az)); J[5] = fmaf(ya0, ay, -(ya1 * ax));
         const float ar = fabsf(rr[c]);
-        const float w = 1.0f / (P.b_rgb32 * fmaxf(ar, P.floor_rgb32));
-        accumulate<MODE>(acc, J, rr[c], w, wb, ar / P.b_rgb32);
+        const float sw = rsqrtf(P.b_rgb32 * fmaxf(ar, P.floor_rgb32));
+        accumulate<MODE>(acc, J, rr[c], sw, k.ib_rgb, ar * k.ib_rgb);
     }
     acc[L::oCount] += 1.0f;
 }
@@ -221,7 +271,17 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     __shared__ double sm[8][36];
     __shared__ double sx[8][36];
     __shared__ int s_last, s_ok;
+    __shared__ double st[kStage];
+    __shared__ int s_nloc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Every block starts copying the state the last block's finish will need
+    // (written by earlier kernels), so that it is in shared memory when the
+    // last ticket is drawn.
+    if (tid < kStage) {
+        const double* src = stage_src<MODE>(dev, tid);
+        if (src) cp_async(&st[tid], src, 8);
+        else if (MODE == TRACK_LAPLACE && tid == 170) cp_async(&s_nloc, &dev->n_localised, 4);
+    }
     if (tid < 12) {
         const float* mats = MODE == TRACK_EXPORT ? dev->aux : dev->rel;
         if (tid < 9) sM[tid] = mats[tid];
@@ -232,6 +292,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     float acc[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) acc[i] = 0.0f;
+    const EvalConst kc{1.0f / P.b_geo32, 1.0f / P.b_rgb32};
     const int W = P.W, Hh = P.H, NP = W * Hh;
     const float fW1 = (float)(W - 1), fH1 = (float)(Hh - 1), fW2 = (float)(W - 2), fH2 = (float)(Hh - 2);
     // Two pixels per iteration: both are fetched (all their loads in flight)
@@ -244,9 +305,10 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         const bool two = p + stride < NP;
         if (two) track_fetch(P, sM, sb, od, orgb, om, a0, a1, p + stride, W, fW1, fH1, fW2, fH2, q1);
         else q1.ok = false;
-        track_eval<MODE>(P, sb, q0, acc);
-        track_eval<MODE>(P, sb, q1, acc);
+        track_eval<MODE>(P, kc, sb, q0, acc);
+        track_eval<MODE>(P, kc, sb, q1, acc);
     }
+    cp_async_wait_all();   // this thread's staging copies (visible to the block after the barriers below)
 
     // ---- block reduction: FP32, in a fixed order (warp reduce-scatter, then warps 0..7) ----
 #pragma unroll
@@ -274,32 +336,9 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (!s_last) return;
 
     // ---- last block ----
-    // Stage the FP64 state the finish needs into shared memory in one
-    // parallel round (GB300's FP64 pipe has ~64-cycle latency, so the tail
-    // is a latency chain; every global round trip on it costs ~600 cycles).
-    // prec_pp 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55; Gauss-Newton
-    // also the tangent map C 56..73 and L xi 74..79; Laplace also D 56..91, pose
-    // block of the previous covariance 92..127, cov_vel 128..163, pv 164..166,
-    // pw 167..169
-    __shared__ double st[176];
-    __shared__ int s_nloc;
-    if (tid < 36) st[tid] = dev->prec_pp[tid];
-    else if (tid < 42) st[tid] = dev->xi[tid - 36];
-    else if (tid < 49) st[tid] = dev->anchor_pose[tid - 42];
-    else if (tid < 53) st[tid] = dev->pq[tid - 49];
-    else if (tid < 56) st[tid] = dev->pt[tid - 53];
-    if (MODE == TRACK_GN) {
-        if (tid >= 56 && tid < 74) st[tid] = dev->gn_C[tid - 56];
-        else if (tid >= 74 && tid < 80) st[tid] = dev->gn_Lxi[tid - 74];
-    }
-    if (MODE == TRACK_LAPLACE) {
-        if (tid >= 56 && tid < 92) st[tid] = dev->D[tid - 56];
-        else if (tid >= 92 && tid < 128) st[tid] = dev->cov[12 * ((tid - 92) / 6) + (tid - 92) % 6];
-        else if (tid >= 128 && tid < 164) st[tid] = dev->cov_vel[tid - 128];
-        else if (tid >= 164 && tid < 167) st[tid] = dev->pv[tid - 164];
-        else if (tid >= 167 && tid < 170) st[tid] = dev->pw[tid - 167];
-        else if (tid == 170) s_nloc = dev->n_localised;
-    }
+    // The staged FP64 state (st, s_nloc) arrived during the pixel loop: GB300's
+    // FP64 pipe has ~64-cycle latency, so the tail is a latency chain and
+    // every global round trip on it costs ~600 cycles.
     // Fixed-order sum of the partials: warp w sums rows v = w, w + 8, ...
     // (at most kRows); lane l adds blocks 4l .. 4l + 3, then 4 (l + 32) .., in
     // order, then a fixed shuffle tree; the order never depends on scheduling.

@@ -40,3 +40,21 @@ def make_pair(w, O, storage="f32", map_arrays=None, s1_pose=None, vel=None, **ov
 def quat_angle_deg(q1, q2):
     d = abs(float(np.dot(q1 / np.linalg.norm(q1), q2 / np.linalg.norm(q2))))
     return np.degrees(2 * np.arccos(min(1.0, d)))
+
+
+def world_frame_scale(H, anchor_pose7):
+    """Error scale of a world-frame 6x6 sum H = T H' T^T, T = diag(Ra, Ra),
+    whose camera-frame terms H' the kernels add in FP32 (App. E.3): each H'_kl
+    is off by at most a multiple of eps32 * sqrt(H'_kk H'_ll) (Cauchy-Schwarz
+    over the pixels), so H_ij is off by at most that multiple of
+    sigma_i sigma_j with sigma_i = sum_k |T_ik| sqrt(H'_kk) (>= sqrt(H_ii)).
+    Returns the matrix sigma sigma^T."""
+    from scipy.spatial.transform import Rotation
+    w, x, y, z = anchor_pose7[3:]
+    Ra = Rotation.from_quat([x, y, z, w]).as_matrix()
+    T = np.zeros((6, 6))
+    T[:3, :3] = Ra
+    T[3:, 3:] = Ra
+    Hc = T.T @ H @ T
+    sigma = np.abs(T) @ np.sqrt(np.clip(np.diag(Hc), 0.0, None))
+    return np.outer(sigma, sigma)

@@ -4,13 +4,15 @@ one evaluation of the normal equations (App. E.3), the prediction step
 
 Bars: kept-pixel count exact (the decisions are bit-identical at a given
 pose); sums within 2e-4 of their scale (FP32 per-pixel arithmetic against
-FP64); poses within 1 mm / 0.05 deg; covariances within 1e-3 relative."""
+FP64; for the world-frame matrices the scale of the camera-frame sums they
+are rotated from, gpu_helpers.world_frame_scale); poses within 1 mm / 0.05
+deg; covariances within 1e-3 relative."""
 import numpy as np
 import pytest
 from scipy.spatial.transform import Rotation
 
 import synth
-from gpu_helpers import make_pair, quat_angle_deg, t
+from gpu_helpers import make_pair, quat_angle_deg, t, world_frame_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +45,7 @@ def test_normal_equations_match_oracle(oracle_mod, name):
         assert got["count"] == ref["count"] > 0.5 * w.width * w.height
         assert got["cost"] == pytest.approx(ref["cost"], rel=1e-5)
         for k in ("H", "Ht"):
-            scale = np.sqrt(np.outer(np.diag(ref[k]), np.diag(ref[k])))
+            scale = world_frame_scale(ref[k], A)
             assert np.all(np.abs(got[k] - ref[k]) <= 2e-4 * scale), (k, np.abs(got[k] - ref[k]) / scale)
         gscale = np.sqrt(np.diag(ref["H"]) * ref["cost"])
         assert np.all(np.abs(got["g"] - ref["g"]) <= 2e-4 * gscale)
