@@ -72,7 +72,7 @@ typedef struct {
     int32_t storage;             /* PRISM_STORAGE_F32 or PRISM_STORAGE_BF16 (map means and variances) */
     int32_t width, height;       /* frame size, pixels (>= 3 each) */
     int32_t n_gn;                /* Gauss-Newton iterations per frame (>= 1) */
-    int32_t skip_empty;          /* 1: rays skip 8^3 bricks whose occupancy bound stays below tau
+    int32_t skip_empty;          /* 1: rays skip 4^3 bricks whose occupancy bound stays below tau
                                     (same outputs, fewer samples); 0: every sample is evaluated */
     double voxel;                /* voxel edge length vs, metres */
     double origin[3];            /* world position of the grid's minimum corner */

@@ -159,18 +159,18 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
             ++n_col;
         }
     }
-    // the tile's occupancy bound after this update (the render's brick skipping)
+    // the occupancy bounds of the tile's 4^3 sub-tiles after this update (the
+    // render's brick skipping)
     {
-        float m = -INFINITY, am = 0.0f;
+        float m[2], am[2];
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int within = threadIdx.x + 256 * half;
-            const float v = map_load_rw<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
-                                                               bz * 8 + (within >> 6)));
-            m = fmaxf(m, v);
-            am = fmaxf(am, fabsf(v));
+            m[half] = map_load_rw<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
+                                                         bz * 8 + (within >> 6)));
+            am[half] = fabsf(m[half]);
         }
-        tile_bound_store(M.tb, tile, m, am);
+        subtile_bounds_store(P, M.tb, bx, by, bz, m, am);
     }
     if (stats) {
         unsigned int a = (unsigned int)warp_sum_u64(n_occ), b = (unsigned int)warp_sum_u64(n_col);

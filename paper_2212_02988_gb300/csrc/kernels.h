@@ -35,10 +35,11 @@ struct MapPlanes {
     void* b;
     void* var_occ;
     void* var_rgb;
-    // per 8^3 tile: (max occupancy mean, max |occupancy mean|) over its voxels,
-    // kept current by the fuse and by map fill / load; per brick b (the cells
-    // whose lower corner lies in tile b): the same over tiles b + {0, 1}^3,
-    // derived from tb by launch_brick_bounds (render_dev.cuh)
+    // per 4^3 sub-tile: (max occupancy mean, max |occupancy mean|) over its
+    // voxels, kept current by the fuse and by map fill / load; per 4^3 brick b
+    // (the cells whose lower corner lies in sub-tile b): the same over
+    // sub-tiles b + {0, 1}^3, derived from tb by launch_brick_bounds
+    // (render_dev.cuh)
     float2* tb;
     float2* bb;
 };

@@ -60,32 +60,29 @@ __global__ void k_map_store(KParams P, MapPlanes M, float* __restrict__ occ, flo
     }
 }
 
-// One block per 8^3 tile: (max, max |.|) of the tile's occupancy means.
+// One block per 8^3 tile: (max, max |.|) of the occupancy means of each of
+// its 4^3 sub-tiles.
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_tile_bounds(KParams P, MapPlanes M) {
     pdl_enter();
     const uint32_t tile = blockIdx.x;
     const int bx = tile % P.nbx, by = (tile / P.nbx) % P.nby, bz = tile / (P.nbx * P.nby);
-    float m = -INFINITY, a = 0.0f;
+    float m[2], a[2];
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int within = threadIdx.x + 256 * half;
-        const float v = map_load<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
-                                                         bz * 8 + (within >> 6)));
-        m = fmaxf(m, v);
-        a = fmaxf(a, fabsf(v));
+        m[half] = map_load<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
+                                                  bz * 8 + (within >> 6)));
+        a[half] = fabsf(m[half]);
     }
-    tile_bound_store(M.tb, tile, m, a);
+    subtile_bounds_store(P, M.tb, bx, by, bz, m, a);
 }
 
-// One thread per brick: the bound of tiles b + {0, 1}^3 (render_dev.cuh).
-__global__ void __launch_bounds__(256) k_brick_bounds(KParams P, MapPlanes M) {
+// One block per top-level brick: the brick bounds of every level below it
+// (render_dev.cuh).
+__global__ void __launch_bounds__(512) k_brick_bounds(KParams P, MapPlanes M) {
     pdl_enter();
-    const int n = P.nbx * P.nby * P.nbz;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n; b += gridDim.x * blockDim.x) {
-        const int bx = b % P.nbx, by = (b / P.nbx) % P.nby, bz = b / (P.nbx * P.nby);
-        M.bb[b] = render_detail::brick_bound(P, M.tb, bx, by, bz);
-    }
+    render_detail::brick_pyramid_block(P, M, blockIdx.x);
 }
 
 static unsigned int io_grid(uint32_t n) {
@@ -126,8 +123,8 @@ cudaError_t launch_tile_bounds(const KParams& P, const MapPlanes& M, cudaStream_
 }
 
 cudaError_t launch_brick_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s) {
-    const unsigned int n = (unsigned int)(P.nbx * P.nby * P.nbz);
-    return launch_pdl(k_brick_bounds, (n + 255) / 256, 256, s, P, M);
+    const unsigned int top = (unsigned int)(P.bb_len - P.bb_off[P.nlev]);
+    return launch_pdl(k_brick_bounds, top, 512, s, P, M);
 }
 
 }  // namespace prism

@@ -46,6 +46,19 @@ void fill_kparams(const prism_config* c, KParams& k) {
     k.W = c->width; k.H = c->height;
     k.bf16 = c->storage == PRISM_STORAGE_BF16;
     k.skip = c->skip_empty;
+    // brick levels: level l + 1 halves level l's brick counts while all three are even
+    {
+        int dx = c->nx / 4, dy = c->ny / 4, dz = c->nz / 4, off = 0;
+        k.nlev = 0;
+        for (int l = 0;; ++l) {
+            k.bb_off[l] = off;
+            off += dx * dy * dz;
+            if (l == 3 || ((dx | dy | dz) & 1)) break;
+            dx /= 2; dy /= 2; dz /= 2;
+            k.nlev = l + 1;
+        }
+        k.bb_len = off;
+    }
     // the march cannot take more than (nx + ny + nz) vs / eps in-grid samples
     double kcap = 2.0 * (c->nx + c->ny + c->nz) * c->voxel / c->eps + 2.0;
     double kuser = c->max_depth > 0 ? std::floor(c->max_depth / c->eps) : kcap;
@@ -512,8 +525,9 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         delete h;
         return fail(nullptr, st, m);
     };
-    const size_t tbytes = (((size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(float2) + 255) / 256) * 256;
-    if (dalloc(h, &h->map_block, 6 * plane + 2 * tbytes) != cudaSuccess)
+    const size_t tbytes = ((8 * (size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(float2) + 255) / 256) * 256;
+    const size_t bbytes = (((size_t)h->kp.bb_len * sizeof(float2) + 255) / 256) * 256;
+    if (dalloc(h, &h->map_block, 6 * plane + tbytes + bbytes) != cudaSuccess)
         return cleanup(PRISM_ENOMEM, "map allocation failed");
     char* base = (char*)h->map_block;
     h->map.tb = (float2*)(base + 6 * plane);

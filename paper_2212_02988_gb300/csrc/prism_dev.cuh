@@ -52,6 +52,9 @@ struct KParams {
     int kmax;                  // last ray sample index
     int bf16;                  // map storage is bf16
     int skip;                  // rays skip bricks whose occupancy bound stays below tau
+    int nlev;                  // brick levels above the 4^3 bricks (0..3): level l has edge 4 * 2^l
+    int bb_off[4];             // offset of level l's brick bounds in MapPlanes::bb
+    int bb_len;                // brick bounds of all levels
     float o32[3];              // grid origin
     float vs32, inv_vs32;      // voxel size and its inverse
     float eps32, tau32, trunc32, disc32;
@@ -281,21 +284,42 @@ __device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32]) {
     }
 }
 
-// Block-wide (max v, max a) over a 256-thread block, stored by thread 0 as
-// the tile bound of `tile` (every thread must call it).
-__device__ __forceinline__ void tile_bound_store(float2* tb, uint32_t tile, float v, float a) {
-    __shared__ float s_v[8], s_a[8];
+// The occupancy bounds (max v, max |v|) of the eight 4^3 sub-tiles of the
+// 8^3 tile (bx, by, bz), from a 256-thread block whose thread t holds the
+// voxel (t & 7, (t >> 3) & 7, (t >> 6) + 4 h) of the tile in v[h], a[h]
+// (every thread must call it).  Sub-tile (sx, sy, sz) of the map's grid of
+// 4^3 sub-tiles is stored at sx + 2 nbx (sy + 2 nby sz).  Warp w holds the
+// y rows 4 (w & 1) .. + 3 of z layer w >> 1 of each half, and lane bit 2 is
+// the x half: the other lane bits are reduced by shuffles, the four z layers
+// of a half through shared memory.
+__device__ __forceinline__ void subtile_bounds_store(const KParams& P, float2* tb, int bx, int by, int bz,
+                                                     const float* v, const float* a) {
+    __shared__ float s_v[2][8][2], s_a[2][8][2];   // [z half][warp][x half]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    for (int h = 0; h < 2; ++h) {
+        float m = v[h], am = a[h];
+#pragma unroll
+        for (int o = 1; o <= 16; o <<= 1) {
+            if (o == 4) continue;
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        }
+        if ((lane & ~4) == 0) {
+            s_v[h][w][lane >> 2] = m;
+            s_a[h][w][lane >> 2] = am;
+        }
     }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_v[w] = v; s_a[w] = a; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < 8; ++i) { v = fmaxf(v, s_v[i]); a = fmaxf(a, s_a[i]); }
-        tb[tile] = make_float2(v, a);
+    if (threadIdx.x < 8) {
+        const int sx = threadIdx.x & 1, sy = (threadIdx.x >> 1) & 1, sz = threadIdx.x >> 2;
+        float m = -INFINITY, am = 0.0f;
+#pragma unroll
+        for (int zl = 0; zl < 4; ++zl) {
+            m = fmaxf(m, s_v[sz][2 * zl + sy][sx]);
+            am = fmaxf(am, s_a[sz][2 * zl + sy][sx]);
+        }
+        tb[(2 * bx + sx) + 2 * P.nbx * ((2 * by + sy) + 2 * P.nby * (2 * bz + sz))] = make_float2(m, am);
     }
 }
 

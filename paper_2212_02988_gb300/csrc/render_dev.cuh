@@ -86,25 +86,66 @@ __device__ __forceinline__ Sample cell_of(uint32_t px, uint32_t pxy, float gx, f
     return s;
 }
 
-// Brick skipping.  A cell whose lower corner x0 lies in brick b = max(x0, 0) / 8
-// (per axis) reads corners from tiles b and b + 1 only; brick_bound is the
-// bound of those 8 tiles (MapPlanes::bb).  A trilinear value is a convex
+// Brick skipping.  A cell whose lower corner x0 lies in brick b = max(x0, 0) / 4
+// (per axis) reads corners from the 4^3 sub-tiles b and b + 1 only; brick_bound
+// is the bound of those 8 sub-tiles (MapPlanes::bb).  A trilinear value is a convex
 // combination of its corners, so if the bound is below tau by more than the
 // lerps' rounding (7 lerps, each within ~3 2^-24 of the corners' magnitude:
 // 2^-18 (1 + max |corner|) is a safe margin), no sample in the brick can be a
 // hit and the march may jump over it.
 __device__ __forceinline__ float2 brick_bound(const KParams& P, const float2* __restrict__ tb, int bx, int by,
                                               int bz) {
-    const int bx1 = min(bx + 1, P.nbx - 1), by1 = min(by + 1, P.nby - 1), bz1 = min(bz + 1, P.nbz - 1);
+    const int sx = 2 * P.nbx, sy = 2 * P.nby, sz = 2 * P.nbz;
+    const int bx1 = min(bx + 1, sx - 1), by1 = min(by + 1, sy - 1), bz1 = min(bz + 1, sz - 1);
     float m = -INFINITY, a = 0.0f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int x = c & 1 ? bx1 : bx, y = c & 2 ? by1 : by, z = c & 4 ? bz1 : bz;
-        const float2 t = tb[x + P.nbx * (y + P.nby * z)];
+        const float2 t = tb[x + sx * (y + sy * z)];
         m = fmaxf(m, t.x);
         a = fmaxf(a, t.y);
     }
     return make_float2(m, a);
+}
+
+// The brick bounds below one top-level brick (level P.nlev, index `top`),
+// one 512-thread block: level 0 from the sub-tile bounds (brick_bound), level
+// l + 1 as the max of its 8 children at level l.  A level-l brick covers the
+// cells whose lower corner lies in its (4 * 2^l)^3 box, and each child bound
+// already includes the sub-tiles one step beyond it, so the max is the bound
+// of the sub-tiles those cells read.
+__device__ __forceinline__ void brick_pyramid_block(const KParams& P, const MapPlanes& M, int top) {
+    __shared__ float2 s_b[2][512];
+    const int N = P.nlev, s = 1 << N, t = threadIdx.x;
+    const int d0x = 2 * P.nbx, d0y = 2 * P.nby;
+    const int dNx = d0x >> N, dNy = d0y >> N;
+    const int Tx = top % dNx, Ty = (top / dNx) % dNy, Tz = top / (dNx * dNy);
+    if (t < s * s * s) {
+        const int x = Tx * s + t % s, y = Ty * s + (t / s) % s, z = Tz * s + t / (s * s);
+        const float2 b = brick_bound(P, M.tb, x, y, z);
+        M.bb[x + d0x * (y + d0y * z)] = b;
+        s_b[0][t] = b;
+    }
+    for (int l = 1; l <= N; ++l) {
+        __syncthreads();
+        const int sl = s >> l, sc = 2 * sl;   // level-l bricks and their children per axis in this block
+        if (t < sl * sl * sl) {
+            const int lx = t % sl, ly = (t / sl) % sl, lz = t / (sl * sl);
+            const float2* ch = s_b[(l - 1) & 1];
+            float m = -INFINITY, a = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float2 v = ch[(2 * lx + (c & 1)) + sc * ((2 * ly + ((c >> 1) & 1)) + sc * (2 * lz + (c >> 2)))];
+                m = fmaxf(m, v.x);
+                a = fmaxf(a, v.y);
+            }
+            const float2 r = make_float2(m, a);
+            const int dlx = d0x >> l, dly = d0y >> l;
+            M.bb[P.bb_off[l] + (Tx * sl + lx) + dlx * ((Ty * sl + ly) + dly * (Tz * sl + lz))] = r;
+            s_b[l & 1][t] = r;
+        }
+    }
+    __syncthreads();   // the shared levels are reused by the block's next item
 }
 
 __device__ __forceinline__ bool brick_skippable(const KParams& P, const float2* __restrict__ bb, int brick) {
@@ -112,23 +153,25 @@ __device__ __forceinline__ bool brick_skippable(const KParams& P, const float2* 
     return t.x < P.tau32 - 0x1p-18f * (1.0f + t.y);
 }
 
-// The first sample index at or after which the ray may leave brick (bx, by, bz):
-// the exit distance of the brick's cell-corner box [8b, 8b + 8) (lower bound -1
-// for b = 0), pulled 1e-3 voxels inside, over eps, plus one.  irg are the
+// The first sample index at or after which the ray may leave the level-lv
+// brick (bx, by, bz): the exit distance of its cell-corner box [e b, e b + e),
+// e = 4 * 2^lv (lower bound -1 for b = 0), pulled 1e-3 voxels inside, over
+// eps, plus one.  irg are the
 // reciprocals of the ray's grid direction (0 where it is 0) and ieps = 1 / eps;
 // the products stand in for the quotients, whose rounding (and that of the
 // sample positions) is far below the 1e-3 voxel margin.  Every sample before
 // the returned index has its cell in the brick.
-__device__ __forceinline__ int brick_exit(const KParams& P, int bx, int by, int bz, float irgx, float irgy,
+__device__ __forceinline__ int brick_exit(const KParams& P, int lv, int bx, int by, int bz, float irgx, float irgy,
                                           float irgz, float cgx, float cgy, float cgz, float ieps) {
     constexpr float m = 1e-3f;
+    const float e = (float)(4 << lv);
     float dmin = INFINITY;
     const int b3[3] = {bx, by, bz};
     const float ir3[3] = {irgx, irgy, irgz}, cg3[3] = {cgx, cgy, cgz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float lo = b3[a] == 0 ? -1.0f : 8.0f * (float)b3[a];
-        const float hi = 8.0f * (float)(b3[a] + 1);
+        const float lo = b3[a] == 0 ? -1.0f : e * (float)b3[a];
+        const float hi = e * (float)(b3[a] + 1);
         if (ir3[a] > 0.0f) dmin = fminf(dmin, (hi - m - cg3[a]) * ir3[a]);
         else if (ir3[a] < 0.0f) dmin = fminf(dmin, (lo + m - cg3[a]) * ir3[a]);
     }
@@ -146,7 +189,7 @@ __device__ __forceinline__ int brick_exit(const KParams& P, int bx, int by, int 
 // The march tests the grid bounds only for samples after k_safe, which a
 // conservative FP32 bound (one voxel of margin, far above the rounding of the
 // bound and of the sample positions) keeps inside the grid, and (with
-// P.skip) jumps over 8^3 bricks whose occupancy bound shows that no sample
+// P.skip) jumps over 4^3 bricks whose occupancy bound shows that no sample
 // in them can be a hit.  The samples evaluated, their corner indices and
 // the hit index are those of the one-loop march over every sample; the
 // value of a jumped-over sample k - 1 is recomputed at the hit.
@@ -216,14 +259,24 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
             if (k > k_safe && !(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
             cur = render_detail::cell_of(px, pxy, gx, gy, gz);
             if (skip) {
-                const int bx = max(cur.ix, 0) >> 3, by = max(cur.iy, 0) >> 3, bz = max(cur.iz, 0) >> 3;
-                const int brick = bx + P.nbx * (by + P.nby * bz);
+                const int bx = max(cur.ix, 0) >> 2, by = max(cur.iy, 0) >> 2, bz = max(cur.iz, 0) >> 2;
+                const int brick = bx + 2 * P.nbx * (by + 2 * P.nby * bz);
                 if (brick != cur_brick) {
                     cur_brick = brick;
                     cur_skip = render_detail::brick_skippable(P, M.bb, brick);
                 }
-                if (cur_skip) {   // no sample of this brick can be a hit: jump past it
-                    const int kn = render_detail::brick_exit(P, bx, by, bz, irgx, irgy, irgz, cgx, cgy, cgz, ieps);
+                if (cur_skip) {   // no sample of this brick can be a hit: jump past it, or past
+                                  // the largest skippable brick above it
+                    int lv = 0, ex = bx, ey = by, ez = bz;
+                    while (lv < P.nlev) {
+                        const int qx = ex >> 1, qy = ey >> 1, qz = ez >> 1;
+                        const int dlx = (2 * P.nbx) >> (lv + 1), dly = (2 * P.nby) >> (lv + 1);
+                        if (!render_detail::brick_skippable(P, M.bb + P.bb_off[lv + 1], qx + dlx * (qy + dly * qz)))
+                            break;
+                        ex = qx; ey = qy; ez = qz;
+                        ++lv;
+                    }
+                    const int kn = render_detail::brick_exit(P, lv, ex, ey, ez, irgx, irgy, irgz, cgx, cgy, cgz, ieps);
                     k = kn > k ? kn : k + 1;
                     kf = (float)k;
                     prev_ok = false;

@@ -66,8 +66,10 @@ StreamLayout layout_of(const prism_config* c, int storage, int sms) {
     auto take = [&](size_t bytes) { const size_t at = o; o += align256(bytes); return at; };
     L.plane = align256(npad * es);
     L.off_map = take(6 * L.plane);
-    L.off_tb = take((size_t)(c->nx / 8) * (c->ny / 8) * (c->nz / 8) * sizeof(float2));
-    L.off_bb = take((size_t)(c->nx / 8) * (c->ny / 8) * (c->nz / 8) * sizeof(float2));
+    L.off_tb = take((size_t)(c->nx / 4) * (c->ny / 4) * (c->nz / 4) * sizeof(float2));
+    KParams kp;
+    fill_kparams(c, kp);
+    L.off_bb = take((size_t)kp.bb_len * sizeof(float2));
     L.off_depth = take(npix * 4);
     L.off_rgb = take(npix * 12);
     L.off_omask = take(npix);
@@ -357,6 +359,7 @@ void run_batch(prism_server* S, std::unique_lock<std::mutex>& lk) {
         B.tiles_off[i + 1] = B.tiles_off[i] + d.tiles_x * ((st->kp.H + 7) / 8);
         B.pix_off[i + 1] = B.pix_off[i] + (npix + 255) / 256;
         B.fuse_off[i + 1] = B.fuse_off[i] + st->kp.nbx * st->kp.nby * st->kp.nbz;
+        B.brick_off[i + 1] = B.brick_off[i] + st->kp.bb_len - st->kp.bb_off[st->kp.nlev];
         ups.push_back({d.depth, d.rgb, q.depth, q.rgb, (size_t)npix});
         fl.ids[i] = id;
         fl.tags[i] = q.tag;

@@ -62,6 +62,7 @@ struct BatchDesc {
     int tiles_off[kServeMaxSlots + 1];      // prefix sums over members: render tiles
     int pix_off[kServeMaxSlots + 1];        // 256-pixel blocks
     int fuse_off[kServeMaxSlots + 1];       // 8^3 voxel tiles
+    int brick_off[kServeMaxSlots + 1];      // top-level bricks
     int gn_off[kServeMaxSlots + 1];         // over localising members: Gauss-Newton virtual blocks
     int lap_off[kServeMaxSlots + 1];        // Laplace virtual blocks
     BatchMember m[kServeMaxSlots];
@@ -79,7 +80,7 @@ struct ServeOut {
 // Persistent grid sizes of the batched kernels (blocks), from the occupancy
 // calculator at server creation.
 struct BatchGrids {
-    int pix, track_gn, track_lap, fuse, render;
+    int pix, track_gn, track_lap, fuse, render, bricks;
 };
 
 cudaError_t batch_grids(bool bf16, BatchGrids* g);

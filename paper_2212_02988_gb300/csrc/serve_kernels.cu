@@ -110,16 +110,15 @@ __global__ void __launch_bounds__(256) kb_fuse(const SlotDesc* __restrict__ slot
     }
 }
 
-// The brick bounds of every member after its fuse (render_dev.cuh).
-__global__ void __launch_bounds__(256) kb_bricks(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
+// The brick bounds of every member after its fuse; item = one top-level
+// brick (render_dev.cuh).
+__global__ void __launch_bounds__(512) kb_bricks(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
     pdl_enter();
-    const int total = b->fuse_off[b->n];   // one brick per 8^3 tile
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        const int i = find_member(b->fuse_off, b->n, e);
+    const int total = b->brick_off[b->n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int i = find_member(b->brick_off, b->n, item);
         const SlotDesc& S = slots[b->m[i].slot];
-        const int br = e - b->fuse_off[i];
-        const int bx = br % S.P.nbx, by = (br / S.P.nbx) % S.P.nby, bz = br / (S.P.nbx * S.P.nby);
-        S.M.bb[br] = render_detail::brick_bound(S.P, S.M.tb, bx, by, bz);
+        render_detail::brick_pyramid_block(S.P, S.M, item - b->brick_off[i]);
     }
 }
 
@@ -192,6 +191,7 @@ int grid_of(K kern, int threads) {
 
 cudaError_t batch_grids(bool bf16, BatchGrids* g) {
     g->pix = grid_of(kb_mask, 256);
+    g->bricks = grid_of(kb_bricks, 512);
     g->track_gn = grid_of(kb_track<TRACK_GN>, 256);
     g->track_lap = grid_of(kb_track<TRACK_LAPLACE>, 256);
     g->fuse = bf16 ? grid_of(kb_fuse<true>, 256) : grid_of(kb_fuse<false>, 256);
@@ -212,7 +212,7 @@ cudaError_t launch_batch_step(const SlotDesc* slots, BatchDesc* batch, const dou
     PRISM_BK(launch_pdl(kb_track<TRACK_LAPLACE>, g.track_lap, 256, s, slots, batch, n_gn));
     if (bf16) PRISM_BK(launch_pdl(kb_fuse<true>, g.fuse, 256, s, slots, batch));
     else PRISM_BK(launch_pdl(kb_fuse<false>, g.fuse, 256, s, slots, batch));
-    PRISM_BK(launch_pdl(kb_bricks, g.pix, 256, s, slots, batch));
+    PRISM_BK(launch_pdl(kb_bricks, g.bricks, 512, s, slots, batch));
     if (bf16) PRISM_BK(launch_pdl(kb_render<true>, g.render, 128, s, slots, batch, n_gn + 1));
     else PRISM_BK(launch_pdl(kb_render<false>, g.render, 128, s, slots, batch, n_gn + 1));
     PRISM_BK(launch_pdl(kb_pack, g.pix, 256, s, slots, batch));
