@@ -70,21 +70,34 @@ __device__ inline void so3_jl(const double w[3], double J[9]) {
     for (int i = 0; i < 9; ++i) J[i] = fma(b, K[i], fma(c, K2[i], i % 4 == 0 ? 1.0 : 0.0));
 }
 
+// Entries (i, j) of K = [w]_x and of K^2 = w w^T - |w|^2 I, by selection
+// (no indexed local array), for the lane-parallel Jacobians below.
+__device__ __forceinline__ double skew_entry(const double w[3], int i, int j) {
+    // K_ij = 0 on the diagonal, -w_k for j = i + 1 (mod 3), +w_k for j = i + 2, k = 3 - i - j
+    const int k = 3 - i - j;
+    const double wk = k == 0 ? w[0] : (k == 1 ? w[1] : w[2]);
+    return i == j ? 0.0 : (j == (i + 1) % 3 ? -wk : wk);
+}
+__device__ __forceinline__ double skew2_entry(const double w[3], double th2, int i, int j) {
+    const double wi = i == 0 ? w[0] : (i == 1 ? w[1] : w[2]);
+    const double wj = j == 0 ? w[0] : (j == 1 ? w[1] : w[2]);
+    return i == j ? fma(wi, wj, -th2) : wi * wj;
+}
+
 // Entry (i, j) of J_l(w) = I + b K + c K^2, K = [w]_x (the same operations
 // whichever thread or kernel evaluates it).
 __device__ inline double so3_jl_entry(const double w[3], int i, int j) {
     double a, b, c;
-    so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
-    double K[9];
-    skew3(w, K);
-    const double k2 = fdot3(K[3 * i], K[j], K[3 * i + 1], K[3 + j], K[3 * i + 2], K[6 + j]);
-    return fma(b, K[3 * i + j], fma(c, k2, i == j ? 1.0 : 0.0));
+    const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
+    so3_coeffs(th2, a, b, c);
+    return fma(b, skew_entry(w, i, j), fma(c, skew2_entry(w, th2, i, j), i == j ? 1.0 : 0.0));
 }
 
-// Inverse left Jacobian of SO(3): I - K/2 + c K^2 with
+// Entry (i, j) of the inverse left Jacobian of SO(3), I - K/2 + c K^2 with
 // c = 1/th^2 - (1 + cos th) / (2 th sin th); for th < 1/4 its Taylor series
-// 1/12 + th^2/720 + th^4/30240 + th^6/1209600 + th^8/47900160.
-__device__ inline void so3_jl_inv(const double w[3], double J[9]) {
+// 1/12 + th^2/720 + th^4/30240 + th^6/1209600 + th^8/47900160 (the same
+// operations in every lane).
+__device__ inline double so3_jl_inv_entry(const double w[3], int i, int j) {
     const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
     double c;
     if (th2 < 0.0625) {
@@ -93,10 +106,7 @@ __device__ inline void so3_jl_inv(const double w[3], double J[9]) {
         const double th = sqrt(th2);
         c = 1.0 / th2 - (1.0 + cos(th)) / (2.0 * th * sin(th));
     }
-    double K[9], K2[9];
-    skew3(w, K);
-    mat3mul(K, K, K2);
-    for (int i = 0; i < 9; ++i) J[i] = fma(-0.5, K[i], fma(c, K2[i], i % 4 == 0 ? 1.0 : 0.0));
+    return fma(-0.5, skew_entry(w, i, j), fma(c, skew2_entry(w, th2, i, j), i == j ? 1.0 : 0.0));
 }
 
 // Unit quaternion of Exp(w): (cos(th/2), sin(th/2)/th w), with the half-angle
@@ -177,53 +187,43 @@ __device__ inline void quat_to_R(const double* q, double* R) {
     R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
 }
 
-// Cholesky of an N x N SPD matrix held in registers (fully unrolled): the
-// lower factor replaces A, r holds the reciprocals of its diagonal; false if
-// not positive definite.
-template <int N>
-__device__ __forceinline__ bool cholesky_reg(double (&A)[N][N], double (&r)[N]) {
-    bool pd = true;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        double d = A[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d = fma(-A[j][k], A[j][k], d);
-        pd = pd && d > 0.0 && isfinite(d);
-        const double rj = rsqrt(d);
-        r[j] = rj;
-        A[j][j] = d * rj;
-#pragma unroll
-        for (int i = j + 1; i < N; ++i) {
-            double t = A[i][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t = fma(-A[i][k], A[j][k], t);
-            A[i][j] = t * rj;
-        }
-    }
-    return pd;
-}
-
 // Block-cooperative inverse of an N x N SPD matrix (A and Ainv in shared
-// or global memory): thread 0 factors in registers into the shared scratch
-// L / rdiag, then thread j solves for column j (unrolled); the result is
-// symmetrised.  Every thread of the block must call it.  Returns false (on
+// or global memory): warp 0 factors it (lane i holding row i) into the
+// shared scratch L / rdiag, then thread j solves for column j (unrolled);
+// the result is symmetrised.  Every thread of the block must call it.  Returns false (on
 // every thread) if not PD.
 template <int N>
 __device__ inline bool spd_inverse_block(const double* A, double* Ainv, double* L, double* rdiag, int* ok) {
-    if (threadIdx.x == 0) {
-        double a[N][N], r[N];
+    static_assert(N <= 32, "one row a lane");
+    if (threadIdx.x < 32) {
+        // right-looking Cholesky on warp 0, lane i holding row i: each step is
+        // one warp instruction for all rows (GB300's FP64 pipe is paced by
+        // warp instructions, not lanes)
+        const int lane = threadIdx.x, row = lane < N ? lane : N - 1;
+        double a[N], r[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) a[j] = A[row * N + j];
+        bool pd = true;
 #pragma unroll
-            for (int j = 0; j < N; ++j) a[i][j] = A[i * N + j];
-        const bool pd = cholesky_reg<N>(a, r);
+        for (int j = 0; j < N; ++j) {
+            const double d = __shfl_sync(0xffffffffu, a[j], j);
+            pd = pd && d > 0.0 && isfinite(d);
+            const double rj = rsqrt(d);
+            r[j] = rj;
+            if (lane > j) a[j] = a[j] * rj;   // L_ij
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            rdiag[i] = r[i];
-#pragma unroll
-            for (int j = 0; j <= i; ++j) L[i * N + j] = a[i][j];
+            for (int m = j + 1; m < N; ++m) {
+                const double lmj = __shfl_sync(0xffffffffu, a[j], m);
+                if (lane >= m) a[m] = fma(-a[j], lmj, a[m]);
+            }
         }
-        *ok = pd ? 1 : 0;
+        if (lane < N) {
+            rdiag[lane] = r[lane];
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+                if (j < lane) L[lane * N + j] = a[j];
+        }
+        if (lane == 0) *ok = pd ? 1 : 0;
     }
     __syncthreads();
     const bool good = *ok != 0;

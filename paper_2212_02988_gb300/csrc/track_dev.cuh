@@ -387,7 +387,11 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
 
     // sm[0]: Ra; sm[1]: H' (sym); sm[2]: Ht' (sym); sm[3], sm[4]: world-frame H, Ht
     double* Ra = sm[0];
-    if (MODE != TRACK_GN && tid == 0) quat_to_R(st + 45, Ra);
+    if (MODE != TRACK_GN && tid < 32) {   // the anchor rotation, one entry a lane
+        const double* qa = st + 45;
+        const double re = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], tid < 9 ? tid : 0);
+        if (tid < 9) Ra[tid] = re;
+    }
     if (L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
         const int e = tid - 32;
         int i = 0, r = e;
@@ -592,14 +596,10 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     double* DS = sx[6];
     double* Lf = sx[7];
     __shared__ double rdg[6];
-    if (tid == 0) {
-        double Jli[9];
-        so3_jl_inv(st + 39, Jli);
-        for (int i = 0; i < 36; ++i) Mi[i] = 0.0;
-        for (int i = 0; i < 3; ++i) {
-            Mi[6 * i + i] = 1.0;
-            for (int j = 0; j < 3; ++j) Mi[6 * (3 + i) + 3 + j] = Jli[3 * i + j];
-        }
+    if (tid < 64) {   // one entry a thread (warps 0 and 1)
+        const int i = tid / 6, j = tid % 6, bi = i < 3 ? 0 : i - 3, bj = j < 3 ? 0 : j - 3;
+        const double jv = so3_jl_inv_entry(st + 39, bi, bj);
+        if (tid < 36) Mi[tid] = (i < 3 || j < 3) ? (i == j ? 1.0 : 0.0) : jv;
     }
     __syncthreads();
     if (tid < 36) {   // T1 = L Mi
