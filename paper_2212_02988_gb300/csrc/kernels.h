@@ -65,7 +65,7 @@ enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2 };
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
-                         DevStats* stats, cudaStream_t s, bool pdl = true);
+                         DevStats* stats, cudaStream_t s, bool pdl = true, uint8_t* mask_out = nullptr);
 int track_grid(const KParams& P, int max_blocks);
 // The grid launch_track uses for `mode` (one wave of the device at most).
 int track_launch_grid(const KParams& P, int mode, int max_blocks);

@@ -346,13 +346,15 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
 prism_status do_localise(prism_handle h, const float* depth, const float* rgb, bool after_side = false,
                          bool prepped = false) {
     PhaseTimer t(h, PH_LOCALISE);
-    LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
     PoseArg pa{};
     if (after_side) CK(h, cudaStreamWaitEvent(h->stream, h->ev_pred, 0), "wait for the prior");
     if (!prepped) LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream, !after_side), "pose matrices");
+    // the first pass also evaluates the observation's depth validity into o_mask
+    // (read by the later passes and by the fuse)
     for (int it = 0; it < h->cfg.n_gn; ++it)
         LAUNCH(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
-                           h->counter, h->max_blocks, h->dstats, h->stream, !(prepped && it == 0)),
+                           h->counter, h->max_blocks, h->dstats, h->stream, !(prepped && it == 0),
+                           it == 0 ? h->o_mask : nullptr),
            "Gauss-Newton pass");
     LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                        h->counter, h->max_blocks, h->dstats, h->stream),

@@ -159,6 +159,19 @@ __device__ __forceinline__ void backproject_rn(const KParams& P, int u, int v, f
     out[2] = z;
 }
 
+// Depth validity (App. F.3, reading R19): valid iff d > 0, finite, and every
+// in-image 4-neighbour dn has |d - dn| <= disc (FP32).
+__device__ __forceinline__ bool depth_valid(const KParams& P, const float* __restrict__ depth, int u, int v) {
+    const int p = v * P.W + u;
+    const float d = depth[p];
+    bool ok = (d > 0.0f) && isfinite(d);
+    if (ok && u > 0) ok = fabsf(__fsub_rn(d, depth[p - 1])) <= P.disc32;
+    if (ok && u < P.W - 1) ok = fabsf(__fsub_rn(d, depth[p + 1])) <= P.disc32;
+    if (ok && v > 0) ok = fabsf(__fsub_rn(d, depth[p - P.W])) <= P.disc32;
+    if (ok && v < P.H - 1) ok = fabsf(__fsub_rn(d, depth[p + P.W])) <= P.disc32;
+    return ok;
+}
+
 // y_r = fma(M_r0, x0, fma(M_r1, x1, fma(M_r2, x2, b_r)))
 __device__ __forceinline__ void affine_rn(const float M[9], const float b[3], const float x[3], float y[3]) {
 #pragma unroll

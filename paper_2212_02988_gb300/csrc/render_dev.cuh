@@ -344,19 +344,6 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
     }
 }
 
-// Depth validity (App. F.3, reading R19): valid iff d > 0, finite, and every
-// in-image 4-neighbour dn has |d - dn| <= disc (FP32).
-__device__ __forceinline__ bool depth_valid(const KParams& P, const float* __restrict__ depth, int u, int v) {
-    const int p = v * P.W + u;
-    const float d = depth[p];
-    bool ok = (d > 0.0f) && isfinite(d);
-    if (ok && u > 0) ok = fabsf(__fsub_rn(d, depth[p - 1])) <= P.disc32;
-    if (ok && u < P.W - 1) ok = fabsf(__fsub_rn(d, depth[p + 1])) <= P.disc32;
-    if (ok && v > 0) ok = fabsf(__fsub_rn(d, depth[p - P.W])) <= P.disc32;
-    if (ok && v < P.H - 1) ok = fabsf(__fsub_rn(d, depth[p + P.W])) <= P.disc32;
-    return ok;
-}
-
 __device__ __forceinline__ void depth_mask_px(const KParams& P, const float* __restrict__ depth,
                                               uint8_t* __restrict__ mask, int p) {
     mask[p] = (uint8_t)depth_valid(P, depth, p % P.W, p / P.W);

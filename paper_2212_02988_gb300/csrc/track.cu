@@ -5,17 +5,17 @@
 namespace prism {
 
 // Two blocks per SM for the passes of every step (at most 128 registers).
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == TRACK_EXPORT ? 1 : 2) k_track(KParams P, const float* __restrict__ od,
-                                                    const float* __restrict__ orgb,
-                                                    const uint8_t* __restrict__ om,
-                                                    const float4* __restrict__ a0,
-                                                    const float4* __restrict__ a1, DevState* dev,
-                                                    float* __restrict__ partials, int pstride,
-                                                    unsigned int* __restrict__ counter,
-                                                    DevStats* __restrict__ stats) {
+// MASKGEN: the pass also evaluates the observation's depth validity and
+// writes it to om_out (the first Gauss-Newton pass of a localisation).
+template <int MODE, bool MASKGEN = false>
+__global__ void __launch_bounds__(kThreads, MODE == TRACK_EXPORT ? 1 : 2)
+    k_track(KParams P, const float* __restrict__ od, const float* __restrict__ orgb, const uint8_t* __restrict__ om,
+            const float4* __restrict__ a0, const float4* __restrict__ a1, DevState* dev,
+            float* __restrict__ partials, int pstride, unsigned int* __restrict__ counter,
+            DevStats* __restrict__ stats, uint8_t* __restrict__ om_out) {
     pdl_enter();
-    track_item<MODE>(P, od, orgb, om, a0, a1, dev, partials, pstride, counter, stats, blockIdx.x, gridDim.x);
+    track_item<MODE, MASKGEN>(P, od, orgb, om, a0, a1, dev, partials, pstride, counter, stats, blockIdx.x, gridDim.x,
+                              om_out);
 }
 
 // One wave: as many blocks as fit on the device at once (fewer partials for
@@ -50,25 +50,34 @@ int track_launch_grid(const KParams& P, int mode, int max_blocks) {
 cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
-                         DevStats* stats, cudaStream_t s, bool pdl) {
+                         DevStats* stats, cudaStream_t s, bool pdl, uint8_t* mask_out) {
     const int grid = track_launch_grid(P, mode, max_blocks);
+    if (mode == TRACK_GN && mask_out) {
+        if (!pdl) {
+            k_track<TRACK_GN, true><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+                                                              max_blocks, counter, stats, mask_out);
+            return cudaGetLastError();
+        }
+        return launch_pdl(k_track<TRACK_GN, true>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
+                          partials, max_blocks, counter, stats, mask_out);
+    }
     switch (mode) {
         case TRACK_GN:
             if (!pdl) {
                 k_track<TRACK_GN><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
-                                                            max_blocks, counter, stats);
+                                                            max_blocks, counter, stats, nullptr);
                 break;
             }
             launch_pdl(k_track<TRACK_GN>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
-                                                        max_blocks, counter, stats);
+                       max_blocks, counter, stats, (uint8_t*)nullptr);
             break;
         case TRACK_LAPLACE:
-            launch_pdl(k_track<TRACK_LAPLACE>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
-                                                             partials, max_blocks, counter, stats);
+            launch_pdl(k_track<TRACK_LAPLACE>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+                       max_blocks, counter, stats, (uint8_t*)nullptr);
             break;
         default:
-            launch_pdl(k_track<TRACK_EXPORT>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
-                                                            partials, max_blocks, counter, stats);
+            launch_pdl(k_track<TRACK_EXPORT>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+                       max_blocks, counter, stats, (uint8_t*)nullptr);
     }
     return cudaGetLastError();
 }

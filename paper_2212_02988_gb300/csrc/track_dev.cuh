@@ -152,12 +152,21 @@ struct TrackPix {
 // issued together (nearest normal/depth and the four bilinear colour taps)
 // as soon as the projection is known.  ok = the pixel passed the mask,
 // z > 0 and both image-range tests; the remaining gates are in track_eval.
+// MASKGEN: the pixel's depth validity is evaluated here (depth_valid) and
+// stored to om_out instead of read from om.
+template <bool MASKGEN>
 __device__ __forceinline__ void track_fetch(const KParams& P, const float* sM, const float* sb,
                                             const float* __restrict__ od, const float* __restrict__ orgb,
-                                            const uint8_t* __restrict__ om, const float4* __restrict__ a0,
-                                            const float4* __restrict__ a1, int p, int W, float fW1, float fH1,
-                                            float fW2, float fH2, TrackPix& q) {
-    const bool m = om[p] != 0;
+                                            const uint8_t* __restrict__ om, uint8_t* __restrict__ om_out,
+                                            const float4* __restrict__ a0, const float4* __restrict__ a1, int p,
+                                            int W, float fW1, float fH1, float fW2, float fH2, TrackPix& q) {
+    bool m;
+    if constexpr (MASKGEN) {
+        m = depth_valid(P, od, p % W, p / W);
+        om_out[p] = (uint8_t)m;
+    } else {
+        m = om[p] != 0;
+    }
     const float z = od[p];
     q.c0 = orgb[3 * p];
     q.c1 = orgb[3 * p + 1];
@@ -255,14 +264,16 @@ using namespace track_detail;
 // vb * 256 + t, stepping by nvb * 256), its partial, the ticket, and — in
 // the block that takes the last ticket — the fixed-order sum and the mode's
 // finish.  A launch of nvb blocks (vb = vb) and a persistent grid
-// that takes the virtual blocks one by one give the same bits.
-template <int MODE>
+// that takes the virtual blocks one by one give the same bits.  MASKGEN:
+// the observed pixels' depth validity is evaluated from od and written to
+// om_out (the pass then needs no mask pass before it).
+template <int MODE, bool MASKGEN = false>
 __device__ __forceinline__ void track_item(const KParams& P, const float* __restrict__ od,
                                            const float* __restrict__ orgb, const uint8_t* __restrict__ om,
                                            const float4* __restrict__ a0, const float4* __restrict__ a1,
                                            DevState* dev, float* __restrict__ partials, int pstride,
                                            unsigned int* __restrict__ counter, DevStats* __restrict__ stats,
-                                           int vb, int nvb) {
+                                           int vb, int nvb, uint8_t* __restrict__ om_out = nullptr) {
     constexpr int N = NV<MODE>::value;
     using L = Layout<MODE>;
     __shared__ float sM[9], sb[3];
@@ -301,9 +312,9 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     const int stride = nvb * kThreads;
     for (int p = vb * kThreads + tid; p < NP; p += 2 * stride) {
         TrackPix q0, q1;
-        track_fetch(P, sM, sb, od, orgb, om, a0, a1, p, W, fW1, fH1, fW2, fH2, q0);
+        track_fetch<MASKGEN>(P, sM, sb, od, orgb, om, om_out, a0, a1, p, W, fW1, fH1, fW2, fH2, q0);
         const bool two = p + stride < NP;
-        if (two) track_fetch(P, sM, sb, od, orgb, om, a0, a1, p + stride, W, fW1, fH1, fW2, fH2, q1);
+        if (two) track_fetch<MASKGEN>(P, sM, sb, od, orgb, om, om_out, a0, a1, p + stride, W, fW1, fH1, fW2, fH2, q1);
         else q1.ok = false;
         track_eval<MODE>(P, kc, sb, q0, acc);
         track_eval<MODE>(P, kc, sb, q1, acc);
