@@ -132,6 +132,7 @@ struct prism_ctx {
     int* fuse_list = nullptr;
     unsigned int* fuse_ctr = nullptr;
     unsigned int* counter = nullptr;
+    DevState* h_state = nullptr;       // pinned host copy of the device state (read_state)
     int max_blocks = 0;
     double* d_imu = nullptr;
     int imu_cap = 0;
@@ -258,6 +259,7 @@ void free_all(prism_handle h) {
         if (h->h_imu[k]) cudaFreeHost(h->h_imu[k]);
         if (h->ev_imu[k]) cudaEventDestroy(h->ev_imu[k]);
     }
+    if (h->h_state) cudaFreeHost(h->h_state);
     if (h->ev_state) cudaEventDestroy(h->ev_state);
     if (h->ev_pred) cudaEventDestroy(h->ev_pred);
 }
@@ -269,12 +271,10 @@ cudaError_t dalloc(prism_handle h, T** p, size_t bytes) {
     return e;
 }
 
-prism_status check_flags(prism_handle h) {
-    int flags = 0;
-    CK(h, cudaMemcpy(&flags, &h->dstate->flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+// Reports (and clears on the device) the flags of a state copy just read.
+prism_status check_flags(prism_handle h, int flags) {
     if (flags) {
-        int zero = 0;
-        CK(h, cudaMemcpy(&h->dstate->flags, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear flags");
+        CK(h, cudaMemsetAsync(&h->dstate->flags, 0, sizeof(int), h->stream), "clear flags");
         std::string m = "device reported:";
         if (flags & FLAG_GN_NOTPD) m += " Gauss-Newton system not positive definite;";
         if (flags & FLAG_LAPLACE_NOTPD) m += " Laplace Hessian not positive definite (state unchanged);";
@@ -285,9 +285,10 @@ prism_status check_flags(prism_handle h) {
 }
 
 prism_status read_state(prism_handle h, prism_state* out) {
+    // one asynchronous copy behind the stream's work, then one wait
+    CK(h, cudaMemcpyAsync(h->h_state, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
     CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
-    DevState s;
-    CK(h, cudaMemcpy(&s, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost), "read state");
+    const DevState& s = *h->h_state;
     std::memset(out, 0, sizeof(*out));
     std::memcpy(out->t, s.t, sizeof(s.t));
     std::memcpy(out->q, s.q, sizeof(s.q));
@@ -295,7 +296,7 @@ prism_status read_state(prism_handle h, prism_state* out) {
     std::memcpy(out->w, s.w, sizeof(s.w));
     std::memcpy(out->cov, s.cov, sizeof(s.cov));
     out->n_localised = s.n_localised;
-    return check_flags(h);
+    return check_flags(h, s.flags);
 }
 
 prism_status write_state(prism_handle h, const prism_state* s) {
@@ -548,6 +549,8 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         dalloc(h, &h->fuse_list, (size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(int)) ||
         dalloc(h, &h->fuse_ctr, 2 * sizeof(unsigned int)))
         return cleanup(PRISM_ENOMEM, "device allocation failed");
+    if (cudaMallocHost(&h->h_state, sizeof(DevState)) != cudaSuccess)
+        return cleanup(PRISM_ENOMEM, "host allocation failed");
     cudaGetLastError();
     {   // the prediction stream (high priority: its one block is scheduled ahead of waiting fuse tiles)
         int least = 0, greatest = 0;
