@@ -312,6 +312,7 @@ def run_ours(args, rank, world, local_rank):
             c_buf.copy_(Ch[i], non_blocking=True)
             F2.step(imus[i], w.dt, d_buf, c_buf, want_state=True)   # state read back to the host
             lat.append((time.perf_counter() - ts) * 1e3)
+        torch.cuda.synchronize()   # the last step's map update and render are part of the run
         e2e_s = time.perf_counter() - t0
         barrier()
         e2e_elapsed, e2e_frames = combine_over_ranks(e2e_s, float(K))

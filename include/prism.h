@@ -178,7 +178,11 @@ prism_status prism_render(prism_handle h, const double* pose7, float* depth, flo
 
 /* One full filter step (R21): predict (skipped on the first step), localise
  * (skipped on the first step), update_map, render of the new anchor.
- * Arguments as for the individual calls; out may be NULL. */
+ * Arguments as for the individual calls; out may be NULL.  With out, the call
+ * returns as soon as the posterior is final: the map update and the anchor
+ * render may still be running on the stream, and they read depth and rgb, so
+ * write those buffers again only in stream order (or after a
+ * synchronisation). */
 prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
                         const float* depth, const float* rgb, prism_state* out);
 

@@ -1,6 +1,7 @@
 // prism_abi.cu — the C ABI of include/prism.h: handle life cycle, argument
 // checks, the order in which each entry enqueues its kernels on the
 // handle's stream, and host-side state, counter and timing I/O.
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -141,6 +142,7 @@ struct prism_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_state = nullptr;   // main stream: the posterior is final
     cudaEvent_t ev_pred = nullptr;    // side stream: the prior is ready
+    cudaEvent_t ev_read = nullptr;    // side stream: the posterior's host copy is done
     static constexpr int kImuRing = 4;
     double* h_imu[kImuRing] = {nullptr, nullptr, nullptr, nullptr};   // pinned IMU staging
     cudaEvent_t ev_imu[kImuRing] = {nullptr, nullptr, nullptr, nullptr};
@@ -262,6 +264,7 @@ void free_all(prism_handle h) {
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->ev_state) cudaEventDestroy(h->ev_state);
     if (h->ev_pred) cudaEventDestroy(h->ev_pred);
+    if (h->ev_read) cudaEventDestroy(h->ev_read);
 }
 
 template <class T>
@@ -284,11 +287,7 @@ prism_status check_flags(prism_handle h, int flags) {
     return PRISM_OK;
 }
 
-prism_status read_state(prism_handle h, prism_state* out) {
-    // one asynchronous copy behind the stream's work, then one wait
-    CK(h, cudaMemcpyAsync(h->h_state, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
-    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
-    const DevState& s = *h->h_state;
+void fill_state(const DevState& s, prism_state* out) {
     std::memset(out, 0, sizeof(*out));
     std::memcpy(out->t, s.t, sizeof(s.t));
     std::memcpy(out->q, s.q, sizeof(s.q));
@@ -296,6 +295,33 @@ prism_status read_state(prism_handle h, prism_state* out) {
     std::memcpy(out->w, s.w, sizeof(s.w));
     std::memcpy(out->cov, s.cov, sizeof(s.cov));
     out->n_localised = s.n_localised;
+}
+
+// prism_step's read-back: the posterior is final at ev_state (after the
+// Laplace pass), so its fields are copied on the side stream behind that
+// event and only that copy is waited for; the map update and the anchor
+// render go on on the main stream (they write none of these fields).
+prism_status read_posterior(prism_handle h, prism_state* out) {
+    DevState* d = h->dstate;
+    DevState* hs = h->h_state;
+    CK(h, cudaStreamWaitEvent(h->side, h->ev_state, 0), "wait for the posterior");
+    // t, q, v, w, cov (contiguous at the start of DevState), then n_localised and flags
+    const size_t head = offsetof(DevState, cov) + sizeof(d->cov);
+    CK(h, cudaMemcpyAsync(hs, d, head, cudaMemcpyDeviceToHost, h->side), "read state");
+    CK(h, cudaMemcpyAsync(&hs->n_localised, &d->n_localised, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->side),
+       "read state");
+    CK(h, cudaEventRecord(h->ev_read, h->side), "read event");
+    CK(h, cudaEventSynchronize(h->ev_read), "wait for the state");
+    fill_state(*hs, out);
+    return check_flags(h, hs->flags);
+}
+
+prism_status read_state(prism_handle h, prism_state* out) {
+    // one asynchronous copy behind the stream's work, then one wait
+    CK(h, cudaMemcpyAsync(h->h_state, h->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream), "read state");
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    const DevState& s = *h->h_state;
+    fill_state(s, out);
     return check_flags(h, s.flags);
 }
 
@@ -557,7 +583,8 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if ((e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&h->ev_pred, cudaEventDisableTiming)) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&h->ev_pred, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_read, cudaEventDisableTiming)) != cudaSuccess)
             return cleanup(PRISM_ECUDA, std::string("streams: ") + cudaGetErrorString(e));
         for (int k = 0; k < prism_ctx::kImuRing; ++k)
             if ((e = cudaEventCreateWithFlags(&h->ev_imu[k], cudaEventDisableTiming)) != cudaSuccess)
@@ -666,7 +693,7 @@ prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
     if ((st = do_render_anchor(h)) != PRISM_OK) return st;
     h->steps += 1;
     if (!out) return PRISM_OK;
-    return read_state(h, out);
+    return read_posterior(h, out);
 }
 
 prism_status prism_get_state(prism_handle h, prism_state* out) {
