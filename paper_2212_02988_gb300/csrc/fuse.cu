@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_fuse_cull(KParams P, const float* __res
 // Persistent over the listed tiles; the last block to finish (ticket in
 // ctr[1]) resets both counters for the next frame.
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_fuse_list(KParams P, MapPlanes M, const float* __restrict__ w2c,
+__global__ void __launch_bounds__(256, 4) k_fuse_list(KParams P, MapPlanes M, const float* __restrict__ w2c,
                                                    const float* __restrict__ depth, const float* __restrict__ rgb,
                                                    const uint8_t* __restrict__ mask, DevStats* __restrict__ stats,
                                                    const int* __restrict__ list, unsigned int* __restrict__ ctr) {

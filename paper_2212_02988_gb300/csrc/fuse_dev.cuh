@@ -15,9 +15,10 @@
 // which is Lambda' = Lambda + Lu, mu' = (Lambda mu + Lu f) / Lambda'.
 // f_occ = -clamp(sdf, -trunc, trunc) (App. D: f_update = [-f_sdf, f_rgb]);
 // colour (one shared variance, reading R11) only where |sdf| <= trunc (R10).
-// A voxel outside the update region is neither read nor written, and a
-// tile whose bounding sphere misses the view frustum exits at once; every
-// other tile refreshes its occupancy bound (kernels.h, MapPlanes::tb).
+// A voxel outside the update region is not written (its occupancy is read
+// for the tile's bound), and a tile whose bounding sphere misses the view
+// frustum exits at once; every other tile refreshes its occupancy bounds
+// (kernels.h, MapPlanes::tb).
 #pragma once
 
 #include "kernels.h"
@@ -97,64 +98,103 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
     }
     const float fW1 = (float)(P.W - 1), fH1 = (float)(P.H - 1);
     unsigned int n_occ = 0, n_col = 0;
+    // The thread's two voxels go through each stage together, so that each
+    // stage's loads are in flight at once: (1) decisions up to the pixel, and
+    // the pixel's mask and depth; (2) the update decision, and the map values
+    // (and observed colour) of the voxels updated; (3) the updates.  The
+    // occupancy of every voxel is read in (1) for the tile's bounds, which
+    // take the value each voxel holds after the update.
+    int x[2], y[2], z[2], pix[2];
+    uint32_t idx[2];
+    float X2[2], dep[2], mu[2];
+    bool in[2], mk[2];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int within = threadIdx.x + 256 * half;
-        const int x = bx * 8 + (within & 7), y = by * 8 + ((within >> 3) & 7), z = bz * 8 + (within >> 6);
-        const uint32_t idx = pad_index(P, x, y, z);
+    for (int h = 0; h < 2; ++h) {
+        const int within = threadIdx.x + 256 * h;
+        x[h] = bx * 8 + (within & 7);
+        y[h] = by * 8 + ((within >> 3) & 7);
+        z[h] = bz * 8 + (within >> 6);
+        idx[h] = pad_index(P, x[h], y[h], z[h]);
         // ---- decisions (FP32 recipe) ----
-        float pc[3] = {__fmaf_rn(__fadd_rn((float)x, 0.5f), P.vs32, P.o32[0]),
-                       __fmaf_rn(__fadd_rn((float)y, 0.5f), P.vs32, P.o32[1]),
-                       __fmaf_rn(__fadd_rn((float)z, 0.5f), P.vs32, P.o32[2])};
+        float pc[3] = {__fmaf_rn(__fadd_rn((float)x[h], 0.5f), P.vs32, P.o32[0]),
+                       __fmaf_rn(__fadd_rn((float)y[h], 0.5f), P.vs32, P.o32[1]),
+                       __fmaf_rn(__fadd_rn((float)z[h], 0.5f), P.vs32, P.o32[2])};
         float X[3];
         affine_rn(sM, sb, pc, X);
-        bool upd = X[2] > 0.0f;
-        float sdf = 0.0f;
-        int pix = 0;
-        if (upd) {
+        X2[h] = X[2];
+        bool ok = X[2] > 0.0f;
+        pix[h] = 0;
+        if (ok) {
             const float iz = __fdiv_rn(1.0f, X[2]);
             const float u = __fmaf_rn(__fmul_rn(P.fx32, X[0]), iz, P.cx32);
             const float v = __fmaf_rn(__fmul_rn(P.fy32, X[1]), iz, P.cy32);
             const float nu = floorf(__fadd_rn(u, 0.5f)), nv = floorf(__fadd_rn(v, 0.5f));
-            upd = nu >= 0.0f && nu <= fW1 && nv >= 0.0f && nv <= fH1;
-            if (upd) {
-                pix = (int)nv * P.W + (int)nu;
-                upd = mask[pix] != 0;
-                if (upd) {
-                    sdf = __fsub_rn(depth[pix], X[2]);
-                    upd = sdf >= -P.trunc32;
-                }
-            }
+            ok = nu >= 0.0f && nu <= fW1 && nv >= 0.0f && nv <= fH1;
+            if (ok) pix[h] = (int)nv * P.W + (int)nu;
         }
-        if (!upd) continue;
-        const bool colour = fabsf(sdf) <= P.trunc32;
+        in[h] = ok;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        mk[h] = false;
+        dep[h] = 0.0f;
+        if (in[h]) {
+            mk[h] = mask[pix[h]] != 0;
+            dep[h] = depth[pix[h]];
+        }
+        mu[h] = map_load_rw<BF16>(M.occ, idx[h]);
+    }
+    bool upd[2], colour[2];
+    float sdf[2], var[2], cvar[2], cr[2], cg[2], cb[2], o0[2], o1[2], o2[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        sdf[h] = mk[h] ? __fsub_rn(dep[h], X2[h]) : 0.0f;
+        upd[h] = mk[h] && sdf[h] >= -P.trunc32;
+        colour[h] = upd[h] && fabsf(sdf[h]) <= P.trunc32;
+        if (upd[h]) var[h] = map_load_rw<BF16>(M.var_occ, idx[h]);
+        if (colour[h]) {
+            cvar[h] = map_load_rw<BF16>(M.var_rgb, idx[h]);
+            cr[h] = map_load_rw<BF16>(M.r, idx[h]);
+            cg[h] = map_load_rw<BF16>(M.g, idx[h]);
+            cb[h] = map_load_rw<BF16>(M.b, idx[h]);
+            const float* o = rgb + 3 * pix[h];
+            o0[h] = o[0];
+            o1[h] = o[1];
+            o2[h] = o[2];
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!upd[h]) continue;
         // ---- Gaussian product (FP32) ----
-        const float f = -fminf(sdf, P.trunc32);
-        const float var = map_load_rw<BF16>(M.var_occ, idx);
-        const float mu = map_load_rw<BF16>(M.occ, idx);
-        const float vl = var * P.upd_prec32;
+        const float f = -fminf(sdf[h], P.trunc32);
+        const float vl = var[h] * P.upd_prec32;
         const float inv = 1.0f / (1.0f + vl);
-        const bool edge = x == 0 || y == 0 || z == 0 || x == P.nx - 1 || y == P.ny - 1 || z == P.nz - 1;
-        const float mu1 = fmaf(vl, f, mu) * inv, var1 = var * inv;
-        map_store<BF16>(M.occ, idx, mu1);
-        map_store<BF16>(M.var_occ, idx, var1);
+        const bool edge = x[h] == 0 || y[h] == 0 || z[h] == 0 || x[h] == P.nx - 1 || y[h] == P.ny - 1 ||
+                          z[h] == P.nz - 1;
+        const float mu1 = fmaf(vl, f, mu[h]) * inv, var1 = var[h] * inv;
+        map_store<BF16>(M.occ, idx[h], mu1);
+        map_store<BF16>(M.var_occ, idx[h], var1);
+        mu[h] = map_round<BF16>(mu1);
         if (edge) {
-            fuse_detail::store_ghosts<BF16>(P, M.occ, x, y, z, map_load_rw<BF16>(M.occ, idx));
-            fuse_detail::store_ghosts<BF16>(P, M.var_occ, x, y, z, map_load_rw<BF16>(M.var_occ, idx));
+            fuse_detail::store_ghosts<BF16>(P, M.occ, x[h], y[h], z[h], mu[h]);
+            fuse_detail::store_ghosts<BF16>(P, M.var_occ, x[h], y[h], z[h], map_round<BF16>(var1));
         }
         ++n_occ;
-        if (colour) {
-            const float cvar = map_load_rw<BF16>(M.var_rgb, idx);
-            const float cl = cvar * P.upd_prec32;
+        if (colour[h]) {
+            const float cl = cvar[h] * P.upd_prec32;
             const float cinv = 1.0f / (1.0f + cl);
-            const float* o = rgb + 3 * pix;
-            map_store<BF16>(M.r, idx, fmaf(cl, o[0], map_load_rw<BF16>(M.r, idx)) * cinv);
-            map_store<BF16>(M.g, idx, fmaf(cl, o[1], map_load_rw<BF16>(M.g, idx)) * cinv);
-            map_store<BF16>(M.b, idx, fmaf(cl, o[2], map_load_rw<BF16>(M.b, idx)) * cinv);
-            map_store<BF16>(M.var_rgb, idx, cvar * cinv);
+            const float r1 = fmaf(cl, o0[h], cr[h]) * cinv, g1 = fmaf(cl, o1[h], cg[h]) * cinv,
+                        b1 = fmaf(cl, o2[h], cb[h]) * cinv, v1 = cvar[h] * cinv;
+            map_store<BF16>(M.r, idx[h], r1);
+            map_store<BF16>(M.g, idx[h], g1);
+            map_store<BF16>(M.b, idx[h], b1);
+            map_store<BF16>(M.var_rgb, idx[h], v1);
             if (edge) {
-                void* planes[4] = {M.r, M.g, M.b, M.var_rgb};
-                for (int q = 0; q < 4; ++q) fuse_detail::store_ghosts<BF16>(P, planes[q], x, y, z, map_load_rw<BF16>(planes[q], idx));
+                fuse_detail::store_ghosts<BF16>(P, M.r, x[h], y[h], z[h], map_round<BF16>(r1));
+                fuse_detail::store_ghosts<BF16>(P, M.g, x[h], y[h], z[h], map_round<BF16>(g1));
+                fuse_detail::store_ghosts<BF16>(P, M.b, x[h], y[h], z[h], map_round<BF16>(b1));
+                fuse_detail::store_ghosts<BF16>(P, M.var_rgb, x[h], y[h], z[h], map_round<BF16>(v1));
             }
             ++n_col;
         }
@@ -162,15 +202,8 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
     // the occupancy bounds of the tile's 4^3 sub-tiles after this update (the
     // render's brick skipping)
     {
-        float m[2], am[2];
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int within = threadIdx.x + 256 * half;
-            m[half] = map_load_rw<BF16>(M.occ, pad_index(P, bx * 8 + (within & 7), by * 8 + ((within >> 3) & 7),
-                                                         bz * 8 + (within >> 6)));
-            am[half] = fabsf(m[half]);
-        }
-        subtile_bounds_store(P, M.tb, bx, by, bz, m, am);
+        const float am[2] = {fabsf(mu[0]), fabsf(mu[1])};
+        subtile_bounds_store(P, M.tb, bx, by, bz, mu, am);
     }
     if (stats) {
         unsigned int a = (unsigned int)warp_sum_u64(n_occ), b = (unsigned int)warp_sum_u64(n_col);

@@ -137,6 +137,12 @@ __device__ __forceinline__ float map_load_rw(const void* plane, uint32_t i) {
         return reinterpret_cast<const float*>(plane)[i];
     }
 }
+// The value map_store<BF16> leaves in a plane for v (what a later load reads).
+template <bool BF16>
+__device__ __forceinline__ float map_round(float v) {
+    if constexpr (BF16) return __bfloat162float(__float2bfloat16_rn(v));
+    else return v;
+}
 template <bool BF16>
 __device__ __forceinline__ void map_store(void* plane, uint32_t i, float v) {
     if constexpr (BF16) {

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256, 2) kb_track(const SlotDesc* __restrict__ 
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(256) kb_fuse(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
+__global__ void __launch_bounds__(256, 4) kb_fuse(const SlotDesc* __restrict__ slots, const BatchDesc* __restrict__ b) {
     pdl_enter();
     __shared__ float sM[9], sb[3];
     const int total = b->fuse_off[b->n];
