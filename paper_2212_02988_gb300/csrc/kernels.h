@@ -66,7 +66,7 @@ cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s, bool pdl = true, uint8_t* mask_out = nullptr);
-int track_grid(const KParams& P, int max_blocks);
+int track_grid(const KParams& P, int mode, int max_blocks);
 // The grid launch_track uses for `mode` (one wave of the device at most).
 int track_launch_grid(const KParams& P, int mode, int max_blocks);
 constexpr int TRACK_NV_MAX = 50;   // FP32 values per block partial

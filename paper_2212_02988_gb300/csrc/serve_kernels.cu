@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) kb_pack(const SlotDesc* __restrict__ slot
 
 // One localisation pass of every localising member; item = one virtual block.
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) kb_track(const SlotDesc* __restrict__ slots, BatchDesc* __restrict__ b,
+__global__ void __launch_bounds__(Block<MODE>::threads, 1) kb_track(const SlotDesc* __restrict__ slots, BatchDesc* __restrict__ b,
                                                 int ctr) {
     pdl_enter();
     const int* off = MODE == TRACK_GN ? b->gn_off : b->lap_off;
@@ -192,8 +192,8 @@ int grid_of(K kern, int threads) {
 cudaError_t batch_grids(bool bf16, BatchGrids* g) {
     g->pix = grid_of(kb_mask, 256);
     g->bricks = grid_of(kb_bricks, 512);
-    g->track_gn = grid_of(kb_track<TRACK_GN>, 256);
-    g->track_lap = grid_of(kb_track<TRACK_LAPLACE>, 256);
+    g->track_gn = grid_of(kb_track<TRACK_GN>, Block<TRACK_GN>::threads);
+    g->track_lap = grid_of(kb_track<TRACK_LAPLACE>, Block<TRACK_LAPLACE>::threads);
     g->fuse = bf16 ? grid_of(kb_fuse<true>, 256) : grid_of(kb_fuse<false>, 256);
     g->render = bf16 ? grid_of(kb_render<true>, 128) : grid_of(kb_render<false>, 128);
     return cudaGetLastError();
@@ -208,8 +208,8 @@ cudaError_t launch_batch_step(const SlotDesc* slots, BatchDesc* batch, const dou
     } while (0)
     PRISM_BK(launch_pdl(kb_predict, kServeMaxSlots, 256, s, slots, batch, imu));
     PRISM_BK(launch_pdl(kb_mask, g.pix, 256, s, slots, batch));
-    for (int it = 0; it < n_gn; ++it) PRISM_BK(launch_pdl(kb_track<TRACK_GN>, g.track_gn, 256, s, slots, batch, it));
-    PRISM_BK(launch_pdl(kb_track<TRACK_LAPLACE>, g.track_lap, 256, s, slots, batch, n_gn));
+    for (int it = 0; it < n_gn; ++it) PRISM_BK(launch_pdl(kb_track<TRACK_GN>, g.track_gn, Block<TRACK_GN>::threads, s, slots, batch, it));
+    PRISM_BK(launch_pdl(kb_track<TRACK_LAPLACE>, g.track_lap, Block<TRACK_LAPLACE>::threads, s, slots, batch, n_gn));
     if (bf16) PRISM_BK(launch_pdl(kb_fuse<true>, g.fuse, 256, s, slots, batch));
     else PRISM_BK(launch_pdl(kb_fuse<false>, g.fuse, 256, s, slots, batch));
     PRISM_BK(launch_pdl(kb_bricks, g.bricks, 512, s, slots, batch));

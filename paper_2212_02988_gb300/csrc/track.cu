@@ -8,7 +8,7 @@ namespace prism {
 // MASKGEN: the pass also evaluates the observation's depth validity and
 // writes it to om_out (the first Gauss-Newton pass of a localisation).
 template <int MODE, bool MASKGEN = false>
-__global__ void __launch_bounds__(kThreads, MODE == TRACK_EXPORT ? 1 : 2)
+__global__ void __launch_bounds__(Block<MODE>::threads, 1)
     k_track(KParams P, const float* __restrict__ od, const float* __restrict__ orgb, const uint8_t* __restrict__ om,
             const float4* __restrict__ a0, const float4* __restrict__ a1, DevState* dev,
             float* __restrict__ partials, int pstride, unsigned int* __restrict__ counter,
@@ -27,21 +27,22 @@ static int wave_blocks() {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_track<MODE>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_track<MODE>, Block<MODE>::threads, 0);
         cached = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
     }
     return cached;
 }
 
-int track_grid(const KParams& P, int max_blocks) {
-    int need = (P.W * P.H + kThreads - 1) / kThreads;
+int track_grid(const KParams& P, int mode, int max_blocks) {
+    const int threads = mode == TRACK_EXPORT ? Block<TRACK_EXPORT>::threads : Block<TRACK_GN>::threads;
+    int need = (P.W * P.H + threads - 1) / threads;
     int cap = max_blocks < 32 * kMaxPerLane ? max_blocks : 32 * kMaxPerLane;
     int g = need < cap ? need : cap;
     return g > 0 ? g : 1;
 }
 
 int track_launch_grid(const KParams& P, int mode, int max_blocks) {
-    const int grid = track_grid(P, max_blocks);
+    const int grid = track_grid(P, mode, max_blocks);
     const int wave = mode == TRACK_GN ? wave_blocks<TRACK_GN>()
                                       : (mode == TRACK_LAPLACE ? wave_blocks<TRACK_LAPLACE>() : wave_blocks<TRACK_EXPORT>());
     return grid < wave ? grid : wave;
@@ -54,29 +55,29 @@ cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
     const int grid = track_launch_grid(P, mode, max_blocks);
     if (mode == TRACK_GN && mask_out) {
         if (!pdl) {
-            k_track<TRACK_GN, true><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+            k_track<TRACK_GN, true><<<grid, Block<TRACK_GN>::threads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                                                               max_blocks, counter, stats, mask_out);
             return cudaGetLastError();
         }
-        return launch_pdl(k_track<TRACK_GN, true>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
+        return launch_pdl(k_track<TRACK_GN, true>, grid, Block<TRACK_GN>::threads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev,
                           partials, max_blocks, counter, stats, mask_out);
     }
     switch (mode) {
         case TRACK_GN:
             if (!pdl) {
-                k_track<TRACK_GN><<<grid, kThreads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+                k_track<TRACK_GN><<<grid, Block<TRACK_GN>::threads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                                                             max_blocks, counter, stats, nullptr);
                 break;
             }
-            launch_pdl(k_track<TRACK_GN>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+            launch_pdl(k_track<TRACK_GN>, grid, Block<TRACK_GN>::threads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                        max_blocks, counter, stats, (uint8_t*)nullptr);
             break;
         case TRACK_LAPLACE:
-            launch_pdl(k_track<TRACK_LAPLACE>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+            launch_pdl(k_track<TRACK_LAPLACE>, grid, Block<TRACK_LAPLACE>::threads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                        max_blocks, counter, stats, (uint8_t*)nullptr);
             break;
         default:
-            launch_pdl(k_track<TRACK_EXPORT>, grid, kThreads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
+            launch_pdl(k_track<TRACK_EXPORT>, grid, Block<TRACK_EXPORT>::threads, s, P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,
                        max_blocks, counter, stats, (uint8_t*)nullptr);
     }
     return cudaGetLastError();

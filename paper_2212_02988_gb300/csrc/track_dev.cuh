@@ -36,8 +36,14 @@ namespace prism {
 
 namespace track_detail {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// Threads a block: one block of 512 an SM for the Gauss-Newton and Laplace
+// passes (half the partials of two blocks of 256 for the last block to add),
+// 256 for the export of the normal equations (50 sums a thread).
+template <int MODE>
+struct Block {
+    static constexpr int threads = MODE == TRACK_EXPORT ? 256 : 512;
+    static constexpr int warps = threads / 32;
+};
 constexpr int kMaxPerLane = 16;   // partials per lane in the last block: grid <= 512
 
 template <int MODE>
@@ -261,7 +267,7 @@ __device__ __forceinline__ void track_eval(const KParams& P, const EvalConst& k,
 using namespace track_detail;
 
 // One block's share of one evaluation: virtual block vb of nvb (pixels
-// vb * 256 + t, stepping by nvb * 256), its partial, the ticket, and — in
+// vb * threads + t, stepping by nvb * threads), its partial, the ticket, and — in
 // the block that takes the last ticket — the fixed-order sum and the mode's
 // finish.  A launch of nvb blocks (vb = vb) and a persistent grid
 // that takes the virtual blocks one by one give the same bits.  MASKGEN:
@@ -275,6 +281,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                                            unsigned int* __restrict__ counter, DevStats* __restrict__ stats,
                                            int vb, int nvb, uint8_t* __restrict__ om_out = nullptr) {
     constexpr int N = NV<MODE>::value;
+    constexpr int kThreads = Block<MODE>::threads, kWarps = Block<MODE>::warps;
     using L = Layout<MODE>;
     __shared__ float sM[9], sb[3];
     __shared__ float swarp[kWarps][N];
