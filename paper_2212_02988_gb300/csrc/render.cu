@@ -28,11 +28,11 @@ __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t
     if (p < P.W * P.H) depth_mask_px(P, depth, mask, p);
 }
 
-__global__ void k_anchor_pack(KParams P, const float* __restrict__ depth, const float* __restrict__ rgb,
-                              float4* __restrict__ a0, float4* __restrict__ a1) {
+__global__ void __launch_bounds__(256) k_anchor_pack(KParams P, const float* __restrict__ depth,
+                                                     const float* __restrict__ rgb, float4* __restrict__ a0,
+                                                     float4* __restrict__ a1) {
     pdl_enter();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < P.W * P.H) anchor_pack_px(P, depth, rgb, a0, a1, p);
+    anchor_pack_tile(P, depth, rgb, a0, a1, blockIdx.x, blockIdx.y);
 }
 
 // ----------------------------------------------------------------- launchers
@@ -77,8 +77,8 @@ cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mas
 
 cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float* rgb, float4* a0, float4* a1,
                                cudaStream_t s) {
-    const int n = P.W * P.H;
-    return launch_pdl(k_anchor_pack, (n + 255) / 256, 256, s, P, depth, rgb, a0, a1);
+    const dim3 grid((P.W + kPackTW - 1) / kPackTW, (P.H + kPackTH - 1) / kPackTH);
+    return launch_pdl(k_anchor_pack, grid, kPackTW * kPackTH, s, P, depth, rgb, a0, a1);
 }
 
 }  // namespace prism

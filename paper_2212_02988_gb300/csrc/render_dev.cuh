@@ -353,23 +353,22 @@ __device__ __forceinline__ void depth_mask_px(const KParams& P, const float* __r
 //   a0 = (n_x, n_y, n_z, z)  with z = 0 where the normal is invalid,
 //   a1 = (r, g, b, 1 if the depth is valid else 0).
 // n = normalize((P(u+1,v) - P(u-1,v)) x (P(u,v+1) - P(u,v-1))), facing the camera.
-// The depth validity of the pixel and of its four neighbours is evaluated
-// here (depth_valid), so no mask pass runs before the packing.
-__device__ __forceinline__ void anchor_pack_px(const KParams& P, const float* __restrict__ depth,
-                                               const float* __restrict__ rgb, float4* __restrict__ a0,
-                                               float4* __restrict__ a1, int p) {
-    const int u = p % P.W, v = p / P.W, W = P.W;
-    const bool mc = depth_valid(P, depth, u, v);
-    bool ok = u >= 1 && u <= P.W - 2 && v >= 1 && v <= P.H - 2 && mc && depth_valid(P, depth, u - 1, v) &&
-              depth_valid(P, depth, u + 1, v) && depth_valid(P, depth, u, v - 1) && depth_valid(P, depth, u, v + 1);
+// anchor_pack_core takes the pixel's depth dc and its neighbours' (dr: u + 1,
+// dl: u - 1, dd: v + 1, du: v - 1), its depth validity mc and ok = it and its
+// four neighbours are valid inside the image border; the two packers below
+// only differ in where those come from.
+__device__ __forceinline__ void anchor_pack_core(const KParams& P, int u, int v, float dc, float dr, float dl,
+                                                 float dd, float du, bool mc, bool ok,
+                                                 const float* __restrict__ rgb, float4* __restrict__ a0,
+                                                 float4* __restrict__ a1, int p) {
     float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
     if (ok) {
         float a[3], b[3], c[3], d[3], pc[3];
-        backproject_rn(P, u + 1, v, depth[p + 1], a);
-        backproject_rn(P, u - 1, v, depth[p - 1], b);
-        backproject_rn(P, u, v + 1, depth[p + W], c);
-        backproject_rn(P, u, v - 1, depth[p - W], d);
-        backproject_rn(P, u, v, depth[p], pc);
+        backproject_rn(P, u + 1, v, dr, a);
+        backproject_rn(P, u - 1, v, dl, b);
+        backproject_rn(P, u, v + 1, dd, c);
+        backproject_rn(P, u, v - 1, du, d);
+        backproject_rn(P, u, v, dc, pc);
         float e1[3], e2[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) { e1[i] = __fsub_rn(a[i], b[i]); e2[i] = __fsub_rn(c[i], d[i]); }
@@ -387,8 +386,79 @@ __device__ __forceinline__ void anchor_pack_px(const KParams& P, const float* __
         }
     }
     if (!ok) n0 = n1 = n2 = 0.0f;
-    a0[p] = make_float4(n0, n1, n2, ok ? depth[p] : 0.0f);
+    a0[p] = make_float4(n0, n1, n2, ok ? dc : 0.0f);
     a1[p] = make_float4(rgb[3 * p], rgb[3 * p + 1], rgb[3 * p + 2], mc ? 1.0f : 0.0f);
+}
+
+// One pixel from global memory (the validity of the pixel and of its four
+// neighbours evaluated here by depth_valid).
+__device__ __forceinline__ void anchor_pack_px(const KParams& P, const float* __restrict__ depth,
+                                               const float* __restrict__ rgb, float4* __restrict__ a0,
+                                               float4* __restrict__ a1, int p) {
+    const int u = p % P.W, v = p / P.W, W = P.W;
+    const bool mc = depth_valid(P, depth, u, v);
+    const bool ok = u >= 1 && u <= P.W - 2 && v >= 1 && v <= P.H - 2 && mc && depth_valid(P, depth, u - 1, v) &&
+                    depth_valid(P, depth, u + 1, v) && depth_valid(P, depth, u, v - 1) &&
+                    depth_valid(P, depth, u, v + 1);
+    const float dc = depth[p];
+    float dr = 0.0f, dl = 0.0f, dd = 0.0f, du = 0.0f;
+    if (ok) {
+        dr = depth[p + 1];
+        dl = depth[p - 1];
+        dd = depth[p + W];
+        du = depth[p - W];
+    }
+    anchor_pack_core(P, u, v, dc, dr, dl, dd, du, mc, ok, rgb, a0, a1, p);
+}
+
+// One 32x8-pixel tile on a block of 256 threads: the depths of the tile and
+// a 2-pixel halo, then the validity of the tile and a 1-pixel halo, go
+// through shared memory (one global read of each depth), with the
+// comparisons of depth_valid.
+constexpr int kPackTW = 32, kPackTH = 8;
+
+__device__ __forceinline__ void anchor_pack_tile(const KParams& P, const float* __restrict__ depth,
+                                                 const float* __restrict__ rgb, float4* __restrict__ a0,
+                                                 float4* __restrict__ a1, int tile_x, int tile_y) {
+    constexpr int DW = kPackTW + 4, DH = kPackTH + 4, VW = kPackTW + 2, VH = kPackTH + 2;
+    __shared__ float sd[DH][DW];
+    __shared__ uint8_t sv[VH][VW];
+    const int W = P.W, H = P.H, x0 = tile_x * kPackTW, y0 = tile_y * kPackTH, t = threadIdx.x;
+    for (int e = t; e < DW * DH; e += blockDim.x) {
+        const int r = e / DW, c = e % DW, u = x0 - 2 + c, v = y0 - 2 + r;
+        sd[r][c] = (u >= 0 && u < W && v >= 0 && v < H) ? depth[v * W + u] : 0.0f;
+    }
+    __syncthreads();
+    for (int e = t; e < VW * VH; e += blockDim.x) {
+        const int r = e / VW, c = e % VW, u = x0 - 1 + c, v = y0 - 1 + r;
+        bool ok = false;
+        if (u >= 0 && u < W && v >= 0 && v < H) {   // depth_valid on the tile
+            const float d = sd[r + 1][c + 1];
+            ok = (d > 0.0f) && isfinite(d);
+            if (ok && u > 0) ok = fabsf(__fsub_rn(d, sd[r + 1][c])) <= P.disc32;
+            if (ok && u < W - 1) ok = fabsf(__fsub_rn(d, sd[r + 1][c + 2])) <= P.disc32;
+            if (ok && v > 0) ok = fabsf(__fsub_rn(d, sd[r][c + 1])) <= P.disc32;
+            if (ok && v < H - 1) ok = fabsf(__fsub_rn(d, sd[r + 2][c + 1])) <= P.disc32;
+        }
+        sv[r][c] = (uint8_t)ok;
+    }
+    __syncthreads();
+    const int tx = t % kPackTW, ty = t / kPackTW, u = x0 + tx, v = y0 + ty;
+    if (ty < kPackTH && u < W && v < H) {
+        const int r = ty + 1, c = tx + 1;   // in sv; in sd: r + 1, c + 1
+        const bool mc = sv[r][c] != 0;
+        const bool ok = u >= 1 && u <= W - 2 && v >= 1 && v <= H - 2 && mc && sv[r][c - 1] && sv[r][c + 1] &&
+                        sv[r - 1][c] && sv[r + 1][c];
+        const float dc = sd[r + 1][c + 1];
+        float dr = 0.0f, dl = 0.0f, dd = 0.0f, du = 0.0f;
+        if (ok) {
+            dr = sd[r + 1][c + 2];
+            dl = sd[r + 1][c];
+            dd = sd[r + 2][c + 1];
+            du = sd[r][c + 1];
+        }
+        anchor_pack_core(P, u, v, dc, dr, dl, dd, du, mc, ok, rgb, a0, a1, v * W + u);
+    }
 }
 
 }  // namespace prism
