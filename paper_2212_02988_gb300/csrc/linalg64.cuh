@@ -13,18 +13,6 @@ __device__ __forceinline__ double fdot3(double a0, double b0, double a1, double 
     return fma(a0, b0, fma(a1, b1, a2 * b2));
 }
 
-__device__ inline void skew3(const double w[3], double K[9]) {
-    K[0] = 0.0; K[1] = -w[2]; K[2] = w[1];
-    K[3] = w[2]; K[4] = 0.0; K[5] = -w[0];
-    K[6] = -w[1]; K[7] = w[0]; K[8] = 0.0;
-}
-
-__device__ inline void mat3mul(const double* A, const double* B, double* C) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            C[3 * i + j] = fdot3(A[3 * i], B[j], A[3 * i + 1], B[3 + j], A[3 * i + 2], B[6 + j]);
-}
-
 __device__ inline void mat3vec(const double* A, const double* x, double* y) {
     for (int i = 0; i < 3; ++i) y[i] = fdot3(A[3 * i], x[0], A[3 * i + 1], x[1], A[3 * i + 2], x[2]);
 }
@@ -50,26 +38,6 @@ __device__ inline void so3_coeffs(double th2, double& a, double& b, double& c) {
     }
 }
 
-// Rodrigues: Exp(w) = I + a K + b K^2
-__device__ inline void so3_exp(const double w[3], double R[9]) {
-    double a, b, c;
-    so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
-    double K[9], K2[9];
-    skew3(w, K);
-    mat3mul(K, K, K2);
-    for (int i = 0; i < 9; ++i) R[i] = fma(a, K[i], fma(b, K2[i], i % 4 == 0 ? 1.0 : 0.0));
-}
-
-// Left Jacobian of SO(3): I + b K + c K^2
-__device__ inline void so3_jl(const double w[3], double J[9]) {
-    double a, b, c;
-    so3_coeffs(fdot3(w[0], w[0], w[1], w[1], w[2], w[2]), a, b, c);
-    double K[9], K2[9];
-    skew3(w, K);
-    mat3mul(K, K, K2);
-    for (int i = 0; i < 9; ++i) J[i] = fma(b, K[i], fma(c, K2[i], i % 4 == 0 ? 1.0 : 0.0));
-}
-
 // Entries (i, j) of K = [w]_x and of K^2 = w w^T - |w|^2 I, by selection
 // (no indexed local array), for the lane-parallel Jacobians below.
 __device__ __forceinline__ double skew_entry(const double w[3], int i, int j) {
@@ -82,6 +50,17 @@ __device__ __forceinline__ double skew2_entry(const double w[3], double th2, int
     const double wi = i == 0 ? w[0] : (i == 1 ? w[1] : w[2]);
     const double wj = j == 0 ? w[0] : (j == 1 ? w[1] : w[2]);
     return i == j ? fma(wi, wj, -th2) : wi * wj;
+}
+
+// Entry (i, j) of Exp(w) = I + a K + b K^2 (exp = true) or of J_l(w) =
+// I + b K + c K^2 (exp = false), K = [w]_x: one branch-free expression, so
+// that the lanes of a warp can evaluate entries of both.
+__device__ __forceinline__ double so3_exp_jl_entry(const double w[3], bool exp, int i, int j) {
+    double a, b, c;
+    const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
+    so3_coeffs(th2, a, b, c);
+    const double s1 = exp ? a : b, s2 = exp ? b : c;
+    return fma(s1, skew_entry(w, i, j), fma(s2, skew2_entry(w, th2, i, j), i == j ? 1.0 : 0.0));
 }
 
 // Entry (i, j) of J_l(w) = I + b K + c K^2, K = [w]_x (the same operations
@@ -143,6 +122,45 @@ __device__ inline void quat_normalise(double* q) {
     for (int i = 0; i < 4; ++i) q[i] *= r;
 }
 
+// normalise(quat_exp(w) (x) q) with w >= 0 (the operations of quat_exp,
+// quat_mul and quat_normalise), computed by the 32 lanes of one warp with
+// quaternion component c = lane & 3 in lane c; returns that component.
+__device__ __forceinline__ double warp_quat_exp_mul(const double w[3], const double* q) {
+    const int c = (threadIdx.x & 31) & 3;
+    const double w0 = w[0], w1 = w[1], w2 = w[2];
+    const double th2 = fdot3(w0, w0, w1, w1, w2, w2);
+    double qe;
+    if (th2 < 0.25) {   // the half-angle series of quat_exp: ch (lane c = 0), sh (c > 0)
+        const double x = 0.25 * th2;
+        const bool c0 = c == 0;
+        const double p = fma(x, fma(x, fma(x, fma(x, fma(x, c0 ? -1.0 / 3628800 : -1.0 / 39916800,
+                                                         c0 ? 1.0 / 40320 : 1.0 / 362880),
+                                                  c0 ? -1.0 / 720 : -1.0 / 5040),
+                                           c0 ? 1.0 / 24 : 1.0 / 120),
+                                    c0 ? -0.5 : -1.0 / 6),
+                             1.0);
+        const double sh = 0.5 * p;
+        qe = c0 ? p : sh * (c == 1 ? w0 : (c == 2 ? w1 : w2));
+    } else {
+        double q4[4];
+        quat_exp(w, q4);
+        qe = c == 0 ? q4[0] : (c == 1 ? q4[1] : (c == 2 ? q4[2] : q4[3]));
+    }
+    // Hamilton product qe (x) q, component c (the operations of quat_mul)
+    const double a0 = __shfl_sync(0xffffffffu, qe, 0), a1 = __shfl_sync(0xffffffffu, qe, 1),
+                 a2 = __shfl_sync(0xffffffffu, qe, 2), a3 = __shfl_sync(0xffffffffu, qe, 3);
+    const int p0 = c, p1 = c ^ 1, p2 = c ^ 2, p3 = c ^ 3;
+    const double t3 = a3 * q[p3];
+    const double qm = fma(a0, q[p0], fma((c == 0 || c == 2) ? -a1 : a1, q[p1],
+                                         fma((c == 0 || c == 3) ? -a2 : a2, q[p2], (c == 0 || c == 1) ? -t3 : t3)));
+    // normalised, w >= 0 (quat_normalise)
+    const double n0 = __shfl_sync(0xffffffffu, qm, 0), n1 = __shfl_sync(0xffffffffu, qm, 1),
+                 n2 = __shfl_sync(0xffffffffu, qm, 2), n3 = __shfl_sync(0xffffffffu, qm, 3);
+    double rn = rsqrt(fma(n0, n0, fdot3(n1, n1, n2, n2, n3, n3)));
+    if (n0 < 0.0) rn = -rn;
+    return (c == 0 ? n0 : (c == 1 ? n1 : (c == 2 ? n2 : n3))) * rn;
+}
+
 __device__ inline void mat3inv(const double* A, double* B) {
     double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
     double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
@@ -180,12 +198,6 @@ __device__ inline void R_to_quat(const double* R, double* q) {
 }
 
 // Rotation of a unit quaternion (value path; not the decision recipe).
-__device__ inline void quat_to_R(const double* q, double* R) {
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
-}
 
 // Block-cooperative inverse of an N x N SPD matrix (A and Ainv in shared
 // or global memory): warp 0 factors it (lane i holding row i) into the

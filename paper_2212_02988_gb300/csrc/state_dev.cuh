@@ -26,7 +26,7 @@ namespace prism {
 // The prediction on one block of 256 threads.
 __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, const double* __restrict__ imu,
                                               int n, double dt) {
-    __shared__ double R[9], B[36], F[144], T1[144], Sig[144], Cv[144], Svp[36], Spv[36], Dm[36], Spp[36], Prec[36];
+    __shared__ double B[36], F[144], T1[144], Sig[144], Cv[144], Svp[36], Spv[36], Dm[36], Spp[36], Prec[36];
     __shared__ double Rw[9], Jl[9], vnew[6], Lch[36], rdg[6];
     __shared__ int ok;
     __shared__ double sums[8];   // mean t, acc (3), gyro (3), then t_end
@@ -68,48 +68,75 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        ok = 1;
+    // The controls and the mean propagation on warp 0, one entry a lane
+    // (GB300's FP64 pipe is paced by warp instructions, not lanes).
+    if (tid < 32) {
+        if (lane == 0) ok = 1;
         double qm[4] = {dev->q[0], dev->q[1], dev->q[2], dev->q[3]};
-        quat_normalise(qm);
-        quat_to_R(qm, R);
+        quat_normalise(qm);   // every lane, the same operations
+        // R(qm) entry e on lane e < 9
+        const double Re = quat_R_entry_rn(qm[0], qm[1], qm[2], qm[3], lane < 9 ? lane : 0);
         const double inv_dt = 1.0 / dt;
-        double u_lin[3] = {0, 0, 0}, u_ang[3] = {0, 0, 0};
+        double u = 0.0;   // lanes 0..2: u_lin, lanes 3..5: u_ang (zero without IMU samples)
         if (n > 0) {
             const double tm = sums[0], tend = sums[7];
             const double acc[3] = {sums[1], sums[2], sums[3]}, gyr[3] = {sums[4], sums[5], sums[6]};
             const double slope_scale = fit[0] > 0.0 ? (tend - tm) / fit[0] : 0.0;
             double gend[3];
             for (int a = 0; a < 3; ++a) gend[a] = fma(fit[1 + a], slope_scale, gyr[a]);
-            double wm[3], half[3], full[3], Rh[9], Rf[9], Rmid[9], Rend[9], am[3], we[3];
-            mat3vec(R, gyr, wm);
-            for (int a = 0; a < 3; ++a) { half[a] = 0.5 * dt * wm[a]; full[a] = dt * wm[a]; }
-            so3_exp(half, Rh);
-            so3_exp(full, Rf);
-            mat3mul(Rh, R, Rmid);
-            mat3mul(Rf, R, Rend);
-            mat3vec(Rmid, acc, am);
-            mat3vec(Rend, gend, we);
-            for (int a = 0; a < 3; ++a) {
-                u_lin[a] = am[a] + (a == 2 ? -P.gravity : 0.0);
-                u_ang[a] = (we[a] - dev->w[a]) * inv_dt;
+            // wm = R gyr (lane a < 3), then to every lane
+            const int ra = lane < 3 ? lane : 0;
+            const double wml = fdot3(__shfl_sync(0xffffffffu, Re, 3 * ra), gyr[0],
+                                     __shfl_sync(0xffffffffu, Re, 3 * ra + 1), gyr[1],
+                                     __shfl_sync(0xffffffffu, Re, 3 * ra + 2), gyr[2]);
+            const double wm[3] = {__shfl_sync(0xffffffffu, wml, 0), __shfl_sync(0xffffffffu, wml, 1),
+                                  __shfl_sync(0xffffffffu, wml, 2)};
+            // Rh = Exp(dt wm / 2) entries on lanes 0..8, Rf = Exp(dt wm) on lanes 9..17
+            const bool hf = lane < 9;
+            const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0), ei = e / 3, ej = e % 3;
+            double vrot[3];
+            for (int a = 0; a < 3; ++a) vrot[a] = hf ? 0.5 * dt * wm[a] : dt * wm[a];
+            const double Ee = so3_exp_jl_entry(vrot, true, ei, ej);
+            // Rmid = Rh R on lanes 0..8, Rend = Rf R on lanes 9..17 (entry (i, j) a fdot3 over k)
+            const int rb = hf ? 3 * ei : 9 + 3 * ei;
+            const double Me = fdot3(__shfl_sync(0xffffffffu, Ee, rb), __shfl_sync(0xffffffffu, Re, ej),
+                                    __shfl_sync(0xffffffffu, Ee, rb + 1), __shfl_sync(0xffffffffu, Re, 3 + ej),
+                                    __shfl_sync(0xffffffffu, Ee, rb + 2), __shfl_sync(0xffffffffu, Re, 6 + ej));
+            // am = Rmid acc on lanes 0..2, we = Rend gend on lanes 3..5
+            const bool lin = lane < 3;
+            const int rr = lane < 3 ? lane : (lane < 6 ? lane - 3 : 0);
+            const int src = (lin ? 0 : 9) + 3 * rr;
+            const double y = fdot3(__shfl_sync(0xffffffffu, Me, src), lin ? acc[0] : gend[0],
+                                   __shfl_sync(0xffffffffu, Me, src + 1), lin ? acc[1] : gend[1],
+                                   __shfl_sync(0xffffffffu, Me, src + 2), lin ? acc[2] : gend[2]);
+            if (lane < 3) u = y + (lane == 2 ? -P.gravity : 0.0);
+            else if (lane < 6) u = (y - dev->w[lane - 3]) * inv_dt;
+        }
+        // the new velocities (lanes 0..5) and position (lanes 0..2)
+        double vn = 0.0;
+        if (lane < 6) {
+            const double vold = lane < 3 ? dev->v[lane] : dev->w[lane - 3];
+            vn = fma(u, dt, vold);
+            vnew[lane] = vn;
+            if (lane < 3) {
+                dev->pv[lane] = vn;
+                dev->pt[lane] = fma(vn, dt, dev->t[lane]);
+            } else {
+                dev->pw[lane - 3] = vn;
             }
         }
-        double wdt[3], qe[4], qn[4];
-        for (int a = 0; a < 3; ++a) {
-            vnew[a] = fma(u_lin[a], dt, dev->v[a]);
-            vnew[3 + a] = fma(u_ang[a], dt, dev->w[a]);
-            dev->pv[a] = vnew[a];
-            dev->pw[a] = vnew[3 + a];
-            dev->pt[a] = fma(vnew[a], dt, dev->t[a]);
-            wdt[a] = vnew[3 + a] * dt;
+        double wdt[3];
+        for (int a = 0; a < 3; ++a) wdt[a] = __shfl_sync(0xffffffffu, vn, 3 + a) * dt;
+        // Rw = Exp(wdt) entries on lanes 0..8, J_l(wdt) on lanes 9..17
+        {
+            const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0);
+            const double v = so3_exp_jl_entry(wdt, lane < 9, e / 3, e % 3);
+            if (lane < 9) Rw[lane] = v;
+            else if (lane < 18) Jl[lane - 9] = v;
         }
-        so3_exp(wdt, Rw);
-        quat_exp(wdt, qe);
-        quat_mul(qe, qm, qn);
-        quat_normalise(qn);
-        for (int a = 0; a < 4; ++a) dev->pq[a] = qn[a];
-        so3_jl(wdt, Jl);
+        // the prior quaternion: normalise(quat_exp(wdt) (x) qm), component lane & 3
+        const double qn = warp_quat_exp_mul(wdt, qm);
+        if (lane < 4) dev->pq[lane] = qn;
     }
     __syncthreads();
     // A, B, F

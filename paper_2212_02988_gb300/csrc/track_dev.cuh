@@ -542,41 +542,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             return;
         }
         if (warp == 0) {   // retraction and the FP32 matrices of the next pass, one quaternion component a lane
-            const double w0 = xn[3], w1 = xn[4], w2 = xn[5];
-            const double th2 = fdot3(w0, w0, w1, w1, w2, w2);
-            const int c = lane & 3;
-            double qe;
-            if (th2 < 0.25) {   // the half-angle series of quat_exp: ch (lane c = 0), sh (c > 0)
-                const double x = 0.25 * th2;
-                const bool c0 = c == 0;
-                const double p = fma(x, fma(x, fma(x, fma(x, fma(x, c0 ? -1.0 / 3628800 : -1.0 / 39916800,
-                                                                 c0 ? 1.0 / 40320 : 1.0 / 362880),
-                                                          c0 ? -1.0 / 720 : -1.0 / 5040),
-                                                   c0 ? 1.0 / 24 : 1.0 / 120),
-                                            c0 ? -0.5 : -1.0 / 6),
-                                     1.0);
-                const double sh = 0.5 * p;
-                qe = c0 ? p : sh * (c == 1 ? w0 : (c == 2 ? w1 : w2));
-            } else {
-                double q4[4];
-                quat_exp(xn + 3, q4);
-                qe = c == 0 ? q4[0] : (c == 1 ? q4[1] : (c == 2 ? q4[2] : q4[3]));
-            }
-            // Hamilton product qe (x) pq, component c (the operations of quat_mul)
-            const double a0 = __shfl_sync(0xffffffffu, qe, 0), a1 = __shfl_sync(0xffffffffu, qe, 1),
-                         a2 = __shfl_sync(0xffffffffu, qe, 2), a3 = __shfl_sync(0xffffffffu, qe, 3);
-            const double* pq = st + 49;
-            const int p0 = c, p1 = c ^ 1, p2 = c ^ 2, p3 = c ^ 3;
-            const double t3 = a3 * pq[p3];
-            const double qm = fma(a0, pq[p0], fma((c == 0 || c == 2) ? -a1 : a1, pq[p1],
-                                                  fma((c == 0 || c == 3) ? -a2 : a2, pq[p2],
-                                                      (c == 0 || c == 1) ? -t3 : t3)));
-            // normalised, w >= 0 (quat_normalise)
-            const double n0 = __shfl_sync(0xffffffffu, qm, 0), n1 = __shfl_sync(0xffffffffu, qm, 1),
-                         n2 = __shfl_sync(0xffffffffu, qm, 2), n3 = __shfl_sync(0xffffffffu, qm, 3);
-            double rn = rsqrt(fma(n0, n0, fdot3(n1, n1, n2, n2, n3, n3)));
-            if (n0 < 0.0) rn = -rn;
-            const double qn = (c == 0 ? n0 : (c == 1 ? n1 : (c == 2 ? n2 : n3))) * rn;
+            const double qn = warp_quat_exp_mul(xn + 3, st + 49);
             double pose[7];
             pose[3] = __shfl_sync(0xffffffffu, qn, 0);
             pose[4] = __shfl_sync(0xffffffffu, qn, 1);

@@ -1,4 +1,5 @@
-"""Brick skipping (prism_config.skip_empty): rays jump over 8^3 bricks whose
+"""Brick skipping (prism_config.skip_empty): rays jump over 4^3 bricks (or
+the largest skippable brick of the 8^3 .. 32^3 levels above them) whose
 occupancy bound shows that no sample in them can be a hit.  The renders
 (depth, colour, mask, hit index) and whole filter steps must be bit-identical
 with and without it, on settled, fused, random and bf16 maps; it must only
@@ -13,10 +14,10 @@ from gpu_helpers import make_pair, t
 pytestmark = pytest.mark.gpu
 
 
-def renders(O, w, maps, poses, storage="f32"):
+def renders(O, w, maps, poses, storage="f32", **over):
     out = {}
     for skip in (0, 1):
-        F, _ = make_pair(w, O, storage=storage, map_arrays=maps, skip_empty=skip)
+        F, _ = make_pair(w, O, storage=storage, map_arrays=maps, skip_empty=skip, **over)
         s0 = F.stats()["render_samples"]
         res = [F.render(p) for p in poses]
         out[skip] = (res, F.stats()["render_samples"] - s0)
@@ -63,6 +64,36 @@ def test_skipping_on_random_field_and_outside_cameras(oracle_mod):
     out = renders(oracle_mod, w, (occ, rgb, var, var), poses)
     for a, b in zip(out[0][0], out[1][0]):
         assert_same(a, b)
+
+
+def random_field(shape, origin, voxel, seed):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    Z, Y, X = np.meshgrid(*(origin + (np.arange(m) + 0.5) * voxel for m in (nz, ny, nx)), indexing="ij")
+    occ = -0.3 * np.ones(shape)
+    for _ in range(6):
+        ctr = rng.uniform(-1.5, 1.5, 3)
+        occ = np.maximum(occ, rng.uniform(0.2, 0.6) - np.sqrt((X - ctr[0]) ** 2 + (Y - ctr[1]) ** 2 +
+                                                              (Z - ctr[2]) ** 2))
+    occ = (occ + rng.normal(0, 0.02, occ.shape)).astype(np.float32)
+    rgb = rng.uniform(0, 1, shape + (3,)).astype(np.float32)
+    return occ, rgb
+
+
+def test_skipping_on_a_non_cubic_grid(oracle_mod):
+    """48 x 40 x 24 voxels: 12 x 10 x 6 bricks of 4^3, then 6 x 5 x 3 of 8^3,
+    where the pyramid stops (an odd count); different brick counts per axis."""
+    w = synth.tiny(n=48, width=71, height=53)
+    nx, ny, nz = 48, 40, 24
+    org = -0.5 * w.extent
+    occ, rgb = random_field((nz, ny, nx), org, w.voxel, seed=21)
+    var = np.ones((nz, ny, nx), np.float32)
+    poses = [np.array([-1.2, 0.3, 0.1, 0.9, 0.1, -0.2, 0.3]), np.array([0.2, -1.9, -0.8, 0.2, 0.6, 0.1, -0.7]),
+             np.array([0.0, 0.0, -1.5, 0.5, -0.5, 0.5, 0.5])]
+    out = renders(oracle_mod, w, (occ, rgb, var, var), poses, nx=nx, ny=ny, nz=nz)
+    for a, b in zip(out[0][0], out[1][0]):
+        assert_same(a, b)
+    assert out[1][1] < out[0][1]
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
