@@ -49,7 +49,10 @@ class Params(C.Structure):
                 ("sigma_pose", C.c_double * 2), ("b_geo", C.c_double), ("b_rgb", C.c_double),
                 ("gate_geo", C.c_double), ("gate_rgb", C.c_double), ("floor_geo", C.c_double),
                 ("floor_rgb", C.c_double), ("ema", C.c_double), ("disc", C.c_double),
-                ("gravity", C.c_double)]
+                ("gravity", C.c_double), ("optimiser", C.c_int32), ("adam_steps", C.c_int32),
+                ("adam_pixels", C.c_int32), ("adam_pad", C.c_int32), ("adam_seed", C.c_uint64),
+                ("adam_lr_t", C.c_double), ("adam_lr_r", C.c_double), ("adam_beta2", C.c_double),
+                ("adam_eps", C.c_double)]
 
 
 class State(C.Structure):
@@ -87,6 +90,11 @@ def lib():
                                       P(LocDiag)]
             L.or_fuse.argtypes = [P(Params), dp, dp, dp, dp, dp, fp, fp]
             L.or_fuse.restype = C.c_int64
+            L.or_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+            L.or_splitmix64.restype = C.c_uint64
+            L.or_sample_pixel.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32]
+            L.or_sample_pixel.restype = C.c_uint32
+            L.or_adam.argtypes = [P(Params), P(Prior), dp, fp, fp, fp, fp, C.c_uint64, dp, dp]
             _lib = L
     return _lib
 
@@ -117,6 +125,12 @@ def params(w, **kw) -> Params:
     p.ema = 0.8
     p.disc = 0.1
     p.gravity = GRAVITY
+    # App. F.2 pose optimiser (used when optimiser = 1)
+    p.optimiser = 0
+    p.adam_steps, p.adam_pixels = 1000, 200
+    p.adam_seed = 0x5EED2212
+    p.adam_lr_t, p.adam_lr_r = 1e-3, 3.6e-4
+    p.adam_beta2, p.adam_eps = 0.999, 1e-8
     for k, v in kw.items():
         if k in ("origin", "sigma_vel", "sigma_pose"):
             for i, x in enumerate(v):
@@ -284,6 +298,30 @@ def localise(p: Params, pr: Prior, prev: State, a_depth, a_rgb, o_depth, o_rgb):
     if rc:
         raise RuntimeError(f"or_localise failed: {rc}")
     return out, {"cost": dg.cost, "n_pixels": dg.n_pixels, "xi": np.array(dg.xi[:])}
+
+
+def splitmix64(seed: int, i: int) -> int:
+    """Output i (0-based) of SplitMix64 started at state `seed`."""
+    return int(lib().or_splitmix64(seed, i))
+
+
+def sample_pixel(seed: int, i: int, n: int) -> int:
+    return int(lib().or_sample_pixel(seed, i, n))
+
+
+def adam(p: Params, pr: Prior, anchor_pose, a_depth, a_rgb, o_depth, o_rgb, counter0: int = 0,
+         trace: bool = False):
+    """The paper's pose optimiser from xi = 0 (App. F.2); returns xi, and the
+    per-step xi (adam_steps x 6) when trace is set."""
+    xi = np.zeros(6)
+    tr = np.zeros((p.adam_steps, 6)) if trace else None
+    anc = _f64(anchor_pose)
+    ad, ar, od, orr = _f32(a_depth), _f32(a_rgb), _f32(o_depth), _f32(o_rgb)
+    rc = lib().or_adam(C.byref(p), C.byref(pr), _p(anc, C.c_double), _p(ad, C.c_float), _p(ar, C.c_float),
+                       _p(od, C.c_float), _p(orr, C.c_float), counter0, _p(xi, C.c_double), _p(tr, C.c_double))
+    if rc:
+        raise RuntimeError(f"or_adam failed ({rc})")
+    return (xi, tr) if trace else xi
 
 
 def fuse(p: Params, m: dict, pose7, depth, rgb):

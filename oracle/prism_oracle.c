@@ -889,6 +889,80 @@ static void tangent_map(const double xi[6], double M[36]) {
     }
 }
 
+/* ============================================== the paper's pose optimiser */
+/* SplitMix64 (Steele, Lea and Flood 2014): the state advances by the golden
+ * gamma 0x9E3779B97F4A7C15 and each output is the state passed through the
+ * variant-13 finaliser.  Output i of the sequence started at `seed`. */
+uint64_t or_splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Uniform pixel of n: floor(n u) with u = (high 32 bits) / 2^32. */
+uint32_t or_sample_pixel(uint64_t seed, uint64_t i, uint32_t n) {
+    return (uint32_t)(((or_splitmix64(seed, i) >> 32) * (uint64_t)n) >> 32);
+}
+
+/* App. F.2 ("Pose optimisation"): Adam with its momentum disabled (beta1 = 0,
+ * so the first moment is the gradient itself), separate step sizes for the
+ * translation and rotation components, adam_steps steps, each evaluating the
+ * objective of App. E.3 on adam_pixels pixels drawn uniformly (with
+ * replacement) from the image; gated and invalid pixels contribute nothing.
+ * The data term's gradient is the L1 subgradient sum sign(r)/b dr/dxi over
+ * the drawn pixels, scaled by (pixels in the image) / adam_pixels so that it
+ * estimates the full-image objective, whose prior term 1/2 xi^T L xi adds
+ * L xi.  Second moment v_s = beta2 v_{s-1} + (1 - beta2) g^2, bias-corrected;
+ * xi -= lr g / (sqrt(v_hat) + eps). */
+int or_adam(const or_params* P, const or_prior* pr, const double anchor_pose[7], const float* a_depth,
+            const float* a_rgb, const float* o_depth, const float* o_rgb, uint64_t counter0,
+            double xi_out[6], double* xi_trace) {
+    const int N = P->width * P->height, S = P->adam_steps, K = P->adam_pixels;
+    double* r = (double*)malloc(sizeof(double) * 4 * N);
+    double* J = (double*)malloc(sizeof(double) * 24 * N);
+    int32_t* assoc = (int32_t*)malloc(sizeof(int32_t) * 2 * N);
+    uint8_t* kept = (uint8_t*)malloc(N);
+    if (!r || !J || !assoc || !kept) { free(r); free(J); free(assoc); free(kept); return -2; }
+    double xi[6] = {0, 0, 0, 0, 0, 0}, v[6] = {0, 0, 0, 0, 0, 0}, pose[7], M[36];
+    double b2t = 1.0;
+    for (int s = 1; s <= S; ++s) {
+        retract(pr, xi, pose);
+        if (or_residuals(P, anchor_pose, a_depth, a_rgb, pose, o_depth, o_rgb, r, J, assoc, kept)) {
+            free(r); free(J); free(assoc); free(kept);
+            return -2;
+        }
+        double gw[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < K; ++k) {
+            const uint32_t p = or_sample_pixel(P->adam_seed, counter0 + (uint64_t)(s - 1) * K + k, (uint32_t)N);
+            if (!kept[p]) continue;
+            for (int res = 0; res < 4; ++res) {
+                const double b = res == 0 ? P->b_geo : P->b_rgb, rr = r[4 * p + res];
+                const double sg = rr > 0.0 ? 1.0 : (rr < 0.0 ? -1.0 : 0.0);
+                for (int i = 0; i < 6; ++i) gw[i] += sg / b * J[24 * p + 6 * res + i];
+            }
+        }
+        tangent_map(xi, M);
+        const double scale = (double)N / (double)K;
+        double g[6];
+        for (int i = 0; i < 6; ++i) {
+            double mg = 0.0, lx = 0.0;
+            for (int k = 0; k < 6; ++k) { mg += M[6 * k + i] * gw[k]; lx += pr->prec_pp[6 * i + k] * xi[k]; }
+            g[i] = scale * mg + lx;
+        }
+        b2t *= P->adam_beta2;
+        for (int i = 0; i < 6; ++i) {
+            v[i] = P->adam_beta2 * v[i] + (1.0 - P->adam_beta2) * g[i] * g[i];
+            const double vhat = v[i] / (1.0 - b2t), lr = i < 3 ? P->adam_lr_t : P->adam_lr_r;
+            xi[i] -= lr * g[i] / (sqrt(vhat) + P->adam_eps);
+        }
+        if (xi_trace) for (int i = 0; i < 6; ++i) xi_trace[6 * (s - 1) + i] = xi[i];
+    }
+    for (int i = 0; i < 6; ++i) xi_out[i] = xi[i];
+    free(r); free(J); free(assoc); free(kept);
+    return 0;
+}
+
 int or_localise(const or_params* P, const or_prior* pr, const or_state* prev,
                 const float* a_depth, const float* a_rgb, const float* o_depth, const float* o_rgb,
                 or_state* out, or_loc_diag* diag) {
@@ -896,7 +970,11 @@ int or_localise(const or_params* P, const or_prior* pr, const or_state* prev,
     for (int a = 0; a < 3; ++a) anchor[a] = prev->t[a];
     for (int a = 0; a < 4; ++a) anchor[3 + a] = prev->q[a];
     double H[36], g[6], Ht[36], st[2], M[36], Mt[36], T[36], Hx[36], gx[6], step[6];
-    for (int it = 0; it < P->n_gn; ++it) {
+    if (P->optimiser == 1) {   /* the paper's Adam; draws numbered from the frame's count */
+        const uint64_t c0 = (uint64_t)prev->n_localised * (uint64_t)P->adam_steps * (uint64_t)P->adam_pixels;
+        if (or_adam(P, pr, anchor, a_depth, a_rgb, o_depth, o_rgb, c0, xi, NULL)) return -2;
+    }
+    for (int it = 0; P->optimiser != 1 && it < P->n_gn; ++it) {
         retract(pr, xi, pose);
         if (or_normal_equations(P, anchor, a_depth, a_rgb, pose, o_depth, o_rgb, H, g, Ht, st)) return -2;
         /* normal equations in xi: (M^T H M + L) step = -(M^T g + L xi) */

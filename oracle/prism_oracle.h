@@ -41,6 +41,16 @@ typedef struct {
     double ema;                  /* Laplace covariance EMA coefficient (App. F.2: 0.8) */
     double disc;                 /* depth-discontinuity threshold, m (App. F.3) */
     double gravity;              /* m/s^2, world -z */
+    /* pose optimiser: 0 Gauss-Newton on the IRLS form (n_gn iterations), 1 the
+     * paper's Adam (App. F.2: momentum off, adam_steps steps of adam_pixels
+     * uniformly sampled pixels, step sizes lr_t / lr_r; beta2 and eps unstated,
+     * Adam's defaults) */
+    int32_t optimiser;
+    int32_t adam_steps;
+    int32_t adam_pixels;
+    int32_t adam_pad;
+    uint64_t adam_seed;
+    double adam_lr_t, adam_lr_r, adam_beta2, adam_eps;
 } or_params;
 
 /* Filter state s = (pose, velocity): pose (t, q), q = (w, x, y, z) maps
@@ -98,6 +108,17 @@ int or_localise(const or_params* P, const or_prior* pr, const or_state* prev,
                 or_state* out, or_loc_diag* diag);
 int64_t or_fuse(const or_params* P, double* occ, double* rgb, double* var_occ, double* var_rgb,
                 const double pose[7], const float* depth, const float* rgb_obs);
+/* Output i (0-based) of SplitMix64 started at state `seed`, and the pixel
+ * index it draws from n pixels (the high 32 bits times n, shifted down). */
+uint64_t or_splitmix64(uint64_t seed, uint64_t i);
+uint32_t or_sample_pixel(uint64_t seed, uint64_t i, uint32_t n);
+/* The paper's pose optimiser on the objective of App. E.3 from xi = 0: Adam
+ * steps s = 1 .. adam_steps on tangent coordinates xi at the prior mean;
+ * pixels of step s are draws counter0 + (s - 1) adam_pixels + k.  xi_out: the
+ * result; xi_trace (adam_steps x 6, may be NULL): xi after every step. */
+int or_adam(const or_params* P, const or_prior* pr, const double anchor_pose[7], const float* a_depth,
+            const float* a_rgb, const float* o_depth, const float* o_rgb, uint64_t counter0,
+            double xi_out[6], double* xi_trace);
 #ifdef __cplusplus
 }
 #endif
