@@ -283,6 +283,28 @@ def run_ours(args, rank, world, local_rank):
                "note": "prism_render_backward (pose + per-voxel gradients, FP32 atomics), not part of the step"}
     F.close()
 
+    # The paper's pose optimiser (App. F.2: Adam, momentum off, 1000 steps of
+    # 200 pixels) on the same frames, for its localisation time beside the
+    # Gauss-Newton passes it is the alternative to; not part of the step.
+    adam = None
+    n_adam = min(K, 8)
+    if n_adam > 0:
+        Fa = Filter(config(w.n, w.extent, w.width, w.height, storage=storage, optimiser=1), s1, device=local_rank)
+        Fa.map_load(*maps)
+        Fa.step(None, w.dt, D[0], C[0])
+        Fa.step(imus[1], w.dt, D[1], C[1])
+        Fa.set_timing(True)
+        Fa.timing_reset()
+        for i in range(2, 2 + n_adam):
+            Fa.step(imus[i], w.dt, D[i], C[i])
+        torch.cuda.synchronize()
+        ta = Fa.timing()
+        ca = Fa.cfg
+        adam = {"ms_per_localise": ta["localise_ms"] / max(ta["localise_n"], 1), "frames": n_adam,
+                "steps": ca.adam_steps, "pixels_per_step": ca.adam_pixels,
+                "note": "Adam with momentum off (App. F.2) and the Laplace pass, one block; not part of the step"}
+        Fa.close()
+
     d_st = {k: st1[k] - st0[k] for k in st1}
     rays_per = d_st["render_rays"] / max(K, 1)      # one anchor render per timed step
     samp_per = d_st["render_samples"] / max(K, 1)
@@ -377,6 +399,7 @@ def run_ours(args, rank, world, local_rank):
                               "ms_per_step": loc_ms},
         "e2e": e2e,
         "render_adjoint": adj,
+        "pose_optimiser_adam": adam,
         "gpu_launches": int(d_st["kernel_launches"]),
         "clocks": clocks,
     }

@@ -65,6 +65,12 @@ typedef enum {
 
 enum { PRISM_STORAGE_F32 = 0, PRISM_STORAGE_BF16 = 1 };
 
+/* Pose optimiser of the localisation: Gauss-Newton on the IRLS form of the
+ * objective (n_gn passes, the default), or the paper's Adam (App. F.2, "Pose
+ * optimisation": momentum off, adam_steps steps of adam_pixels pixels drawn
+ * uniformly, step sizes adam_lr_t / adam_lr_r). */
+enum { PRISM_OPT_GAUSS_NEWTON = 0, PRISM_OPT_ADAM = 1 };
+
 /* Filter configuration.  prism_config_default() fills the paper's values
  * (App. F.2, Tbl. transscales) for a cubic grid and an image size. */
 typedef struct {
@@ -93,6 +99,13 @@ typedef struct {
     double ema;                  /* Laplace covariance EMA coefficient (0.8) */
     double disc;                 /* depth discontinuity threshold, metres (0.1) */
     double gravity;              /* m/s^2 along world -z (9.81) */
+    int32_t optimiser;           /* PRISM_OPT_GAUSS_NEWTON (default) or PRISM_OPT_ADAM */
+    int32_t adam_steps;          /* Adam steps per frame (App. F.2: 1000) */
+    int32_t adam_pixels;         /* pixels drawn per step, 1..256 (App. F.2: 200) */
+    int32_t adam_reserved;       /* 0 */
+    uint64_t adam_seed;          /* seed of the SplitMix64 pixel draws (draws numbered across frames) */
+    double adam_lr_t, adam_lr_r; /* step sizes, translation / rotation (App. F.2: 1e-3, 3.6e-4) */
+    double adam_beta2, adam_eps; /* second-moment decay and epsilon (unstated: Adam's 0.999, 1e-8) */
 } prism_config;
 
 /* Filter state (host copy).  cov is 12x12 row-major over the error state

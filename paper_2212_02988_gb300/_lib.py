@@ -30,7 +30,10 @@ class Config(C.Structure):
                 ("sigma_vel", C.c_double * 2), ("sigma_pose", C.c_double * 2),
                 ("b_geo", C.c_double), ("b_rgb", C.c_double), ("gate_geo", C.c_double),
                 ("gate_rgb", C.c_double), ("floor_geo", C.c_double), ("floor_rgb", C.c_double),
-                ("ema", C.c_double), ("disc", C.c_double), ("gravity", C.c_double)]
+                ("ema", C.c_double), ("disc", C.c_double), ("gravity", C.c_double),
+                ("optimiser", C.c_int32), ("adam_steps", C.c_int32), ("adam_pixels", C.c_int32),
+                ("adam_reserved", C.c_int32), ("adam_seed", C.c_uint64), ("adam_lr_t", C.c_double),
+                ("adam_lr_r", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double)]
 
 
 class State(C.Structure):

@@ -58,7 +58,7 @@ cudaError_t launch_anchor_pack(const KParams& P, const float* depth, const float
                                cudaStream_t s);
 
 // track.cu — normal-equation passes of the localisation.
-enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2 };
+enum TrackMode : int { TRACK_EXPORT = 0, TRACK_GN = 1, TRACK_LAPLACE = 2, TRACK_ADAM = 3 };
 // Evaluate the objective with the relative transform dev->rel (GN, Laplace)
 // or dev->aux (export) against the packed anchor; the last block reduces
 // the per-block partials in a fixed order and runs the mode's FP64 finish.
@@ -70,6 +70,19 @@ int track_grid(const KParams& P, int mode, int max_blocks);
 // The grid launch_track uses for `mode` (one wave of the device at most).
 int track_launch_grid(const KParams& P, int mode, int max_blocks);
 constexpr int TRACK_NV_MAX = 50;   // FP32 values per block partial
+
+// adam.cu — the paper's pose optimiser (App. F.2): Adam with momentum off on
+// tangent coordinates xi at the prior mean, `steps` steps of `pixels` pixels
+// (<= 256) drawn uniformly with SplitMix64 from `seed` (draws numbered from
+// n_localised x steps x pixels); leaves dev->xi, dev->cur_pose and dev->rel
+// for the Laplace pass.  One block.
+struct AdamArgs {
+    int steps, pixels;
+    unsigned long long seed;
+    double lr_t, lr_r, beta2, eps;
+};
+cudaError_t launch_adam(const KParams& P, const float* o_depth, const float* o_rgb, const uint8_t* o_mask,
+                        const float4* a0, const float4* a1, DevState* dev, const AdamArgs& A, cudaStream_t s);
 
 // state.cu — FP64 prediction and GN start; the FP32 matrices of a pose.
 // pdl = false: a plain launch (for a kernel that follows an event wait, whose

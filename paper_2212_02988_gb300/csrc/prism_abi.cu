@@ -33,6 +33,15 @@ bool valid_config(const prism_config* c, std::string& why) {
     if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
         return bad("Laplace scales and IRLS floors must be > 0");
     if (!(c->ema >= 0 && c->ema <= 1)) return bad("ema must be in [0, 1]");
+    if (c->optimiser != PRISM_OPT_GAUSS_NEWTON && c->optimiser != PRISM_OPT_ADAM)
+        return bad("optimiser must be 0 (Gauss-Newton) or 1 (Adam)");
+    if (c->optimiser == PRISM_OPT_ADAM) {
+        if (c->adam_steps < 1 || c->adam_pixels < 1 || c->adam_pixels > 256)
+            return bad("adam_steps must be >= 1 and adam_pixels in [1, 256]");
+        if (!(c->adam_lr_t > 0) || !(c->adam_lr_r > 0) || !(c->adam_eps > 0) || !(c->adam_beta2 >= 0) ||
+            !(c->adam_beta2 < 1))
+            return bad("Adam step sizes and eps must be > 0 and beta2 in [0, 1)");
+    }
     for (double x : {c->origin[0], c->origin[1], c->origin[2], c->cx, c->cy, c->tau, c->max_depth})
         if (!std::isfinite(x)) return bad("non-finite configuration value");
     return true;
@@ -376,6 +385,25 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb, b
     PoseArg pa{};
     if (after_side) CK(h, cudaStreamWaitEvent(h->stream, h->ev_pred, 0), "wait for the prior");
     if (!prepped) LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream, !after_side), "pose matrices");
+    if (h->cfg.optimiser == PRISM_OPT_ADAM) {   // the paper's optimiser, then the Laplace pass
+        LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+        AdamArgs A;
+        A.steps = h->cfg.adam_steps;
+        A.pixels = h->cfg.adam_pixels;
+        A.seed = (unsigned long long)h->cfg.adam_seed;
+        A.lr_t = h->cfg.adam_lr_t;
+        A.lr_r = h->cfg.adam_lr_r;
+        A.beta2 = h->cfg.adam_beta2;
+        A.eps = h->cfg.adam_eps;
+        LAUNCH(h, launch_adam(h->kp, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, A, h->stream), "Adam");
+        LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+                               h->counter, h->max_blocks, h->dstats, h->stream),
+               "Laplace pass");
+        CK(h, cudaEventRecord(h->ev_state, h->stream), "state event");
+        h->has_prior = false;
+        h->anchor_at_mean = false;
+        return PRISM_OK;
+    }
     // the first pass also evaluates the observation's depth validity into o_mask
     // (read by the later passes and by the fuse)
     for (int it = 0; it < h->cfg.n_gn; ++it)
@@ -519,6 +547,14 @@ void prism_config_default(prism_config* c, int32_t n, double extent, int32_t wid
     c->ema = 0.8;
     c->disc = 0.1;
     c->gravity = 9.81;
+    c->optimiser = PRISM_OPT_GAUSS_NEWTON;
+    c->adam_steps = 1000;
+    c->adam_pixels = 200;
+    c->adam_seed = 0x5EED2212ull;
+    c->adam_lr_t = 1e-3;
+    c->adam_lr_r = 3.6e-4;
+    c->adam_beta2 = 0.999;
+    c->adam_eps = 1e-8;
 }
 
 prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, void* stream, prism_handle* out) {

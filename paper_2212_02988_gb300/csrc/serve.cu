@@ -610,6 +610,8 @@ prism_status prism_serve_open(prism_server_handle S, const prism_config* cfg, co
     if (!stream_id) return sfail(S, PRISM_EINVAL, "stream_id is NULL");
     std::string why;
     if (!valid_config(cfg, why)) return sfail(S, PRISM_EINVAL, "invalid config: " + why);
+    if (cfg->optimiser != PRISM_OPT_GAUSS_NEWTON)
+        return sfail(S, PRISM_EINVAL, "the server localises with Gauss-Newton (optimiser 0)");
     if (s1) {
         double p[7];
         std::memcpy(p, s1->t, 3 * sizeof(double));

@@ -48,15 +48,15 @@ constexpr int kMaxPerLane = 16;   // partials per lane in the last block: grid <
 
 template <int MODE>
 struct NV {
-    static constexpr int value = MODE == TRACK_GN ? 29 : (MODE == TRACK_LAPLACE ? 23 : 50);
+    static constexpr int value = MODE == TRACK_GN ? 29 : (MODE == TRACK_LAPLACE ? 23 : (MODE == TRACK_ADAM ? 8 : 50));
 };
 
 // offsets into the per-thread accumulator
 template <int MODE>
 struct Layout {
-    static constexpr bool H = MODE != TRACK_LAPLACE;
+    static constexpr bool H = MODE == TRACK_GN || MODE == TRACK_EXPORT;
     static constexpr bool G = MODE != TRACK_LAPLACE;
-    static constexpr bool HT = MODE != TRACK_GN;
+    static constexpr bool HT = MODE == TRACK_LAPLACE || MODE == TRACK_EXPORT;
     static constexpr int oH = 0;
     static constexpr int oG = H ? 21 : 0;
     static constexpr int oHT = oG + (G ? 6 : 0);
@@ -66,7 +66,8 @@ struct Layout {
 
 // One residual r with Jacobian J: H += w J J^T, g += w r J, Ht += J J^T / b^2,
 // with sw = sqrt(w) (the IRLS weight) and ib = 1 / b (the Laplace scale)
-// folded into J first, so that every matrix entry is one FMA.
+// folded into J first, so that every matrix entry is one FMA; for the
+// paper's Adam (TRACK_ADAM) g += sign(r) J / b, the L1 subgradient.
 template <int MODE>
 __device__ __forceinline__ void accumulate(float* acc, const float J[6], float r, float sw, float ib, float cost) {
     using L = Layout<MODE>;
@@ -84,7 +85,11 @@ __device__ __forceinline__ void accumulate(float* acc, const float J[6], float r
             if (L::H) acc[L::oH + e] = fmaf(Js[i], Js[j], acc[L::oH + e]);
             if (L::HT) acc[L::oHT + e] = fmaf(Jt[i], Jt[j], acc[L::oHT + e]);
         }
-    if (L::G) {
+    if constexpr (MODE == TRACK_ADAM) {   // the L1 subgradient sign(r) / b J
+        const float sg = r > 0.0f ? ib : (r < 0.0f ? -ib : 0.0f);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[L::oG + i] = fmaf(sg, J[i], acc[L::oG + i]);
+    } else if (L::G) {
         const float swr = sw * r;
 #pragma unroll
         for (int i = 0; i < 6; ++i) acc[L::oG + i] = fmaf(swr, Js[i], acc[L::oG + i]);

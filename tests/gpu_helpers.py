@@ -33,7 +33,8 @@ def make_pair(w, O, storage="f32", map_arrays=None, s1_pose=None, vel=None, **ov
     F = Filter(cfg, s, device=0)
     if map_arrays is not None:
         F.map_load(*(t(np.asarray(a, dtype=np.float32)) for a in map_arrays))
-    p = O.params(w, **{k: v for k, v in over.items() if k in ("n_gn", "max_depth")})
+    p = O.params(w, **{k: v for k, v in over.items()
+                       if k in ("n_gn", "max_depth", "optimiser") or k.startswith("adam_")})
     return F, p
 
 

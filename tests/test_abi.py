@@ -68,6 +68,9 @@ def test_config_default_is_the_paper(lib):
         gold["ema"]["value"])
     assert c.fx == 560.0 and c.cx == 319.5 and c.cy == 239.5
     assert c.skip_empty == 1
+    # the paper's Adam (App. F.2), selected by optimiser = 1
+    assert c.optimiser == 0 and c.adam_steps == 1000 and c.adam_pixels == 200
+    assert c.adam_lr_t == 1e-3 and c.adam_lr_r == 3.6e-4 and c.adam_beta2 == 0.999 and c.adam_eps == 1e-8
 
 
 def test_invalid_config_rejected_without_gpu_work(lib):
@@ -81,6 +84,12 @@ def test_invalid_config_rejected_without_gpu_work(lib):
     c.nx, c.skip_empty = 64, 2
     assert L.prism_create_map(C.byref(c), None, None, C.byref(h)) == lib.EINVAL
     assert b"skip_empty" in L.prism_last_error(None)
+    c.skip_empty, c.optimiser = 1, 2
+    assert L.prism_create_map(C.byref(c), None, None, C.byref(h)) == lib.EINVAL
+    assert b"optimiser" in L.prism_last_error(None)
+    c.optimiser, c.adam_pixels = 1, 300                # more pixels a step than the kernel's block
+    assert L.prism_create_map(C.byref(c), None, None, C.byref(h)) == lib.EINVAL
+    assert b"adam_pixels" in L.prism_last_error(None)
     assert L.prism_destroy(None) == lib.EINVAL
     assert L.prism_status_string(lib.ENOTPD) == b"matrix not positive definite"
 
