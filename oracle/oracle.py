@@ -7,7 +7,9 @@ filter step of the paper (Sec. 3.3, App. F):
 
     frame 1:  fuse at the given state s_1, render the anchor at s_1;
     frame t:  predict (App. E.1/E.2) -> localise (App. E.3, Sec. 4.1) ->
-              fuse at the new mean (App. D) -> render the new anchor (App. B).
+              fuse at the new mean (App. D) -> render the new anchor (App. B);
+    rollout:  predict repeatedly from the belief with no observation, and
+              render the map mean at each predicted pose mean (App. I).
 """
 from __future__ import annotations
 
@@ -322,6 +324,25 @@ def adam(p: Params, pr: Prior, anchor_pose, a_depth, a_rgb, o_depth, o_rgb, coun
     if rc:
         raise RuntimeError(f"or_adam failed ({rc})")
     return (xi, tr) if trace else xi
+
+
+def rollout(p: Params, s: State, windows, dts, occ=None, rgb=None):
+    """Predictive rollout from the filter belief (App. I, "Prediction and
+    Control"; Fig. 1): each frame applies the transition of `predict`
+    (App. E.1/E.2) with no observation, so its prior -- mean and the full
+    12x12 covariance over pose and velocity -- is the next frame's state.
+    With a map (occ, rgb) each frame also renders the map mean at the
+    predicted pose mean (App. B).  windows: one IMU array (n x 7) or None per
+    frame; dts: the frame intervals.  Returns the per-frame states (as
+    state_arrays dicts) and the per-frame renders (empty without a map)."""
+    states, images = [], []
+    for imu, dt in zip(windows, dts):
+        pr = prior_arrays(predict(p, s, imu, dt))
+        s = make_state(pr["pose"], pr["vel"], pr["cov"], s.n_localised)
+        states.append(state_arrays(s))
+        if occ is not None:
+            images.append(render(p, occ, rgb, pr["pose"]))
+    return states, images
 
 
 def fuse(p: Params, m: dict, pose7, depth, rgb):
