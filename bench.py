@@ -281,6 +281,60 @@ def run_ours(args, rank, world, local_rank):
         adj_ms = a0.elapsed_time(a1) / n_adj
         adj = {"ms_per_call": adj_ms, "calls": n_adj, "mrays_per_s": w.width * w.height / (adj_ms * 1e-3) / 1e6,
                "note": "prism_render_backward (pose + per-voxel gradients, FP32 atomics), not part of the step"}
+
+    # Predictive rollouts (App. I) from the final belief: 32 candidate control
+    # sequences of 10 frames (the recorded IMU windows with a constant offset
+    # on the specific force and the angular rate per candidate), the states
+    # read back and every predicted frame rendered, in one call; not part of
+    # the step.
+    roll = None
+    n_roll = min(K, 5)
+    if n_roll > 0:
+        n_seq, k_roll = 32, 10
+        rs = np.random.default_rng(11)
+        base = [imus[1 + W + j % K] for j in range(k_roll)]
+        wins = []
+        for _ in range(n_seq):
+            da, dg = rs.normal(0, 0.5, 3), rs.normal(0, 0.2, 3)
+            cand = []
+            for x in base:
+                y = x.copy()
+                y[:, 1:4] += da
+                y[:, 4:7] += dg
+                cand.append(y)
+            wins.append(cand)
+        bufs = F.rollout(wins, w.dt)   # allocates the image buffers (untimed)
+        bufs = {"depth": bufs["depth"], "rgb": bufs["rgb"]}
+        F.rollout(wins, w.dt, out=bufs)
+        torch.cuda.synchronize()
+        a = F.stats()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_r = time.perf_counter()
+        r0.record()
+        for _ in range(n_roll):
+            F.rollout(wins, w.dt, out=bufs)   # states read back: each call synchronises
+        r1.record()
+        torch.cuda.synchronize()
+        roll_wall = (time.perf_counter() - t_r) / n_roll
+        roll_dev = r0.elapsed_time(r1) / n_roll
+        bst = F.stats()
+        fr = n_seq * k_roll
+        roll_samples = (bst["render_samples"] - a["render_samples"]) / n_roll
+        roll_hits = (bst["render_hits"] - a["render_hits"]) / n_roll
+        s0, s1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(n_roll):
+            F.rollout(wins, w.dt, images=False)
+        s1e.record()
+        torch.cuda.synchronize()
+        roll = {"sequences": n_seq, "frames_per_sequence": k_roll, "calls": n_roll,
+                "ms_per_call": roll_wall * 1e3, "device_ms_per_call": roll_dev,
+                "states_only_ms_per_call": s0.elapsed_time(s1e) / n_roll,
+                "predicted_frames_per_s": fr / roll_wall,
+                "render_mrays_per_s": fr * w.width * w.height / roll_wall / 1e6,
+                "samples_per_frame": roll_samples / fr, "hits_per_frame": roll_hits / fr,
+                "note": "prism_rollout: states (one block per sequence) + all 320 images in one render "
+                        "launch, wall time per call with the states read back; not part of the step"}
     F.close()
 
     # The paper's pose optimiser (App. F.2: Adam, momentum off, 1000 steps of
@@ -400,6 +454,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "render_adjoint": adj,
         "pose_optimiser_adam": adam,
+        "rollout": roll,
         "gpu_launches": int(d_st["kernel_launches"]),
         "clocks": clocks,
     }

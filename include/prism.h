@@ -277,6 +277,34 @@ prism_status prism_render_backward(prism_handle h, const double* pose7, const fl
                                    const float* grad_rgb, float* grad_occ, float* grad_rgb_map,
                                    double* grad_pose6, double* grad_pose7);
 
+/* Predictive rollouts from the filter belief (App. I, "Prediction and
+ * Control"; Fig. 1).  From the current posterior q(s_t) and the map mean,
+ * each of n_seq candidate control sequences of k frames propagates the state
+ * belief with the transition of prism_predict (App. E.1/E.2) and no
+ * observation: a frame's prior (mean, velocities and the full 12x12
+ * covariance) becomes the next frame's state.  Each frame also renders the
+ * map mean (App. B) at its predicted pose mean, normalised as prism_render
+ * normalises a pose, all frames in one launch.  The filter's state, prior,
+ * anchor and map are left as they were.  Frame f = s k + i is frame i of
+ * sequence s.
+ * imu: HOST, the IMU rows of frames 0, 1, ... one after another (7 doubles
+ *      a row, as in prism_predict), NULL when every count is 0.
+ * counts: HOST, n_seq k row counts (>= 0; 0 = no controls, constant velocity).
+ * dt: HOST, n_seq k frame intervals (finite, > 0).
+ * states: HOST, n_seq k records, or NULL; when given, the stream is
+ *      synchronised and frame f's predicted state written to states[f].
+ * depth (n_seq k H W floats), rgb (n_seq k H W 3 floats), hitk (n_seq k H W
+ *      int32, the hit sample index as prism_render reports it): DEVICE
+ *      pointers, frame-major, each may be NULL; with all three NULL nothing
+ *      is rendered.  The render adds to the work counters but not to the
+ *      detail counters.
+ * The inputs are copied before the call returns.  Returns PRISM_EINVAL for
+ * n_seq < 1, k < 1, n_seq k > 65535 or a bad count, interval or IMU value;
+ * PRISM_ENOTPD when a predicted pose covariance was not positive definite
+ * (reported only with states; the records are still written). */
+prism_status prism_rollout(prism_handle h, int32_t n_seq, int32_t k, const double* imu, const int32_t* counts,
+                           const double* dt, prism_state* states, float* depth, float* rgb, int32_t* hitk);
+
 /* Work counters and per-phase timing.  Detail counters (off by default)
  * make the render also count the distinct trilinear corners each ray
  * reads, at a few instructions per sample. */

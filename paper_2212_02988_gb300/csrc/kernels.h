@@ -119,6 +119,27 @@ cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, f
 cudaError_t launch_tile_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s);
 cudaError_t launch_brick_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s);
 
+// rollout.cu — predictive rollouts (App. I): per candidate sequence one block
+// chains k predictions (App. E.1/E.2) from the posterior of `src` on its own
+// scratch state, each prior becoming the next state.  Frame f = seq k + i
+// reads IMU rows row0[f] .. row0[f] + counts[f] - 1 and interval dts[f], and
+// writes its state to out[f] and the FP32 camera-to-world matrices of its
+// normalised pose mean to mats[12 f ..].  RollOut has prism_state's layout.
+struct RollOut {
+    double t[3], q[4], v[3], w[3];
+    double cov[144];
+    int32_t n_localised;
+    int32_t flags;   // FLAG_PRIOR_NOTPD when the frame's pose prior was not PD
+};
+cudaError_t launch_rollout_states(const KParams& P, const DevState* src, DevState* scratch, int n_seq, int k,
+                                  const double* imu, const long long* row0, const int* counts, const double* dts,
+                                  RollOut* out, float* mats, cudaStream_t s);
+// render.cu — the render of `frames` poses in one launch (grid z = frame):
+// frame f reads mats[12 f ..] and writes depth / rgb / hitk at f H W
+// (f H W 3 for rgb); each output may be NULL.  frames <= 65535.
+cudaError_t launch_render_frames(const KParams& P, const float* mats, int frames, const MapPlanes& M, float* depth,
+                                 float* rgb, int32_t* hitk, DevStats* stats, cudaStream_t s);
+
 // render_bwd.cu — adjoint of the render at the pose whose matrices are in
 // `mats` (DevState::aux); adds the pose gradient to dev->grad_pose.
 cudaError_t launch_render_bwd(const KParams& P, const float* mats, const MapPlanes& M, const float* grad_depth,

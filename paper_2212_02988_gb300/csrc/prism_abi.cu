@@ -157,6 +157,14 @@ struct prism_ctx {
     cudaEvent_t ev_imu[kImuRing] = {nullptr, nullptr, nullptr, nullptr};
     int h_imu_cap = 0;
     int imu_slot = 0;
+    // prism_rollout's buffers: device scratch states, records, matrices and
+    // inputs in one block; their pinned host staging, reused once ev_roll
+    // (recorded after the upload) has passed
+    void* roll_dev = nullptr;
+    size_t roll_cap = 0;
+    char* h_roll = nullptr;
+    size_t h_roll_cap = 0;
+    cudaEvent_t ev_roll = nullptr;
     bool has_anchor = false;
     bool anchor_at_mean = false;   // the anchor was rendered at the current state mean
     bool has_prior = false;
@@ -270,6 +278,9 @@ void free_all(prism_handle h) {
         if (h->h_imu[k]) cudaFreeHost(h->h_imu[k]);
         if (h->ev_imu[k]) cudaEventDestroy(h->ev_imu[k]);
     }
+    if (h->roll_dev) cudaFree(h->roll_dev);
+    if (h->h_roll) cudaFreeHost(h->h_roll);
+    if (h->ev_roll) cudaEventDestroy(h->ev_roll);
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->ev_state) cudaEventDestroy(h->ev_state);
     if (h->ev_pred) cudaEventDestroy(h->ev_pred);
@@ -797,6 +808,90 @@ prism_status prism_render_backward(prism_handle h, const double* pose7, const fl
         grad_pose7[5] = 2.0 * (w * gth[1] - cy) / n;
         grad_pose7[6] = 2.0 * (w * gth[2] - cz) / n;
     }
+    return PRISM_OK;
+}
+
+prism_status prism_rollout(prism_handle h, int32_t n_seq, int32_t k, const double* imu, const int32_t* counts,
+                           const double* dt, prism_state* states, float* depth, float* rgb, int32_t* hitk) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (n_seq < 1 || k < 1) return fail(h, PRISM_EINVAL, "n_seq and k must be >= 1");
+    if ((int64_t)n_seq * k > 65535) return fail(h, PRISM_EINVAL, "n_seq * k must be <= 65535");
+    if (!counts || !dt) return fail(h, PRISM_EINVAL, "counts or dt is NULL");
+    const int frames = n_seq * k;
+    int64_t rows = 0;
+    for (int f = 0; f < frames; ++f) {
+        if (counts[f] < 0) return fail(h, PRISM_EINVAL, "counts must be >= 0");
+        if (counts[f] > 0 && !imu) return fail(h, PRISM_EINVAL, "imu is NULL with rows to read");
+        std::string why;
+        if (!imu_ok(imu ? imu + 7 * rows : nullptr, counts[f], dt[f], why)) return fail(h, PRISM_EINVAL, why);
+        rows += counts[f];
+    }
+    DeviceGuard g(h->device);
+    // one block: scratch states | records | matrices | row offsets | counts | dts | IMU rows
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_rec = up((size_t)n_seq * sizeof(DevState));
+    const size_t o_mat = o_rec + up((size_t)frames * sizeof(RollOut));
+    const size_t o_row = o_mat + up((size_t)frames * 12 * sizeof(float));
+    const size_t o_cnt = o_row + up((size_t)frames * sizeof(long long));
+    const size_t o_dt = o_cnt + up((size_t)frames * sizeof(int));
+    const size_t o_imu = o_dt + up((size_t)frames * sizeof(double));
+    const size_t total = o_imu + up((size_t)(rows > 0 ? rows : 1) * 7 * sizeof(double));
+    const size_t staged = total - o_row;   // the inputs, uploaded in one copy
+    if (!h->ev_roll) CK(h, cudaEventCreateWithFlags(&h->ev_roll, cudaEventDisableTiming), "rollout event");
+    if (total > h->roll_cap) {
+        CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+        if (h->roll_dev) {
+            cudaFree(h->roll_dev);
+            h->bytes -= (int64_t)h->roll_cap;
+            h->roll_dev = nullptr;
+            h->roll_cap = 0;
+        }
+        CK(h, dalloc(h, &h->roll_dev, total), "rollout buffers");
+        h->roll_cap = total;
+    }
+    CK(h, cudaEventSynchronize(h->ev_roll), "rollout staging reuse");
+    if (staged > h->h_roll_cap) {
+        if (h->h_roll) cudaFreeHost(h->h_roll);
+        h->h_roll = nullptr;
+        h->h_roll_cap = 0;
+        CK(h, cudaMallocHost((void**)&h->h_roll, staged), "rollout staging");
+        h->h_roll_cap = staged;
+    }
+    char* hb = h->h_roll;
+    long long* h_row = (long long*)hb;
+    int* h_cnt = (int*)(hb + (o_cnt - o_row));
+    double* h_dt = (double*)(hb + (o_dt - o_row));
+    long long r = 0;
+    for (int f = 0; f < frames; ++f) {
+        h_row[f] = r;
+        h_cnt[f] = counts[f];
+        h_dt[f] = dt[f];
+        r += counts[f];
+    }
+    if (rows > 0) std::memcpy(hb + (o_imu - o_row), imu, (size_t)rows * 7 * sizeof(double));
+    char* db = (char*)h->roll_dev;
+    CK(h, cudaMemcpyAsync(db + o_row, hb, staged, cudaMemcpyHostToDevice, h->stream), "rollout upload");
+    CK(h, cudaEventRecord(h->ev_roll, h->stream), "rollout event");
+    RollOut* d_rec = (RollOut*)(db + o_rec);
+    float* d_mats = (float*)(db + o_mat);
+    LAUNCH(h, launch_rollout_states(h->kp, h->dstate, (DevState*)db, n_seq, k, (const double*)(db + o_imu),
+                                    (const long long*)(db + o_row), (const int*)(db + o_cnt),
+                                    (const double*)(db + o_dt), d_rec, d_mats, h->stream),
+           "rollout states");
+    if (depth || rgb || hitk)
+        LAUNCH(h, launch_render_frames(h->kp, d_mats, frames, h->map, depth, rgb, hitk, h->dstats, h->stream),
+               "rollout render");
+    if (!states) return PRISM_OK;
+    static_assert(sizeof(RollOut) == sizeof(prism_state), "rollout record layout");
+    CK(h, cudaMemcpyAsync(states, d_rec, (size_t)frames * sizeof(RollOut), cudaMemcpyDeviceToHost, h->stream),
+       "read rollout states");
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    bool notpd = false;
+    for (int f = 0; f < frames; ++f) {
+        notpd |= states[f].reserved != 0;
+        states[f].reserved = 0;
+    }
+    if (notpd) return fail(h, PRISM_ENOTPD, "device reported: a predicted pose covariance not positive definite");
     return PRISM_OK;
 }
 

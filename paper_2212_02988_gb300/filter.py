@@ -171,6 +171,47 @@ class Filter:
                                       C.byref(out) if out is not None else None), self.h)
         return out
 
+    def rollout(self, windows, dt, images: bool = True, hitk: bool = False, want_states: bool = True,
+                out: dict | None = None) -> dict:
+        """prism_rollout: predictive rollouts of candidate control sequences.
+        windows: n_seq sequences of k IMU windows ((n, 7) arrays or None);
+        dt: a scalar or an (n_seq, k) array of frame intervals.  Returns the
+        predicted states ((n_seq, k) nested lists of State, or None) and,
+        with images, depth (n_seq, k, H, W), rgb (n_seq, k, H, W, 3) and
+        hitk (n_seq, k, H, W) when asked.  `out` may hold preallocated image
+        tensors of those shapes."""
+        n_seq, k = len(windows), len(windows[0])
+        if n_seq == 0 or k == 0 or any(len(w) != k for w in windows):
+            raise ValueError("windows must be n_seq >= 1 sequences of the same k >= 1 windows")
+        rows, counts = [], np.zeros(n_seq * k, dtype=np.int32)
+        for s_i, seq in enumerate(windows):
+            for i, w in enumerate(seq):
+                if w is None or len(w) == 0:
+                    continue
+                w = np.ascontiguousarray(w, dtype=np.float64)
+                if w.ndim != 2 or w.shape[1] != 7:
+                    raise ValueError("each IMU window must be (n, 7)")
+                rows.append(w)
+                counts[s_i * k + i] = len(w)
+        imu = np.ascontiguousarray(np.concatenate(rows)) if rows else None
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n_seq, k)).ravel())
+        dev = torch.device("cuda", self.device)
+        out = dict(out or {})
+        shp = (n_seq, k, self.H, self.W)
+        if images:
+            out.setdefault("depth", torch.empty(shp, device=dev))
+            out.setdefault("rgb", torch.empty(shp + (3,), device=dev))
+            if hitk:
+                out.setdefault("hitk", torch.empty(shp, dtype=torch.int32, device=dev))
+        recs = (State * (n_seq * k))() if want_states else None
+        self._check(self.L.prism_rollout(self.h, n_seq, k, _hptr(imu), counts.ctypes.data_as(C.POINTER(C.c_int32)),
+                                         _hptr(dts), recs,
+                                         _dptr(out.get("depth"), shp, name="depth"),
+                                         _dptr(out.get("rgb"), shp + (3,), name="rgb"),
+                                         _dptr(out.get("hitk"), shp, torch.int32, "hitk")), self.h)
+        out["states"] = None if recs is None else [[recs[s_i * k + i] for i in range(k)] for s_i in range(n_seq)]
+        return out
+
     def get_state(self) -> State:
         s = State()
         self._check(self.L.prism_get_state(self.h, C.byref(s)), self.h)

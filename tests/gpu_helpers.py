@@ -59,3 +59,23 @@ def world_frame_scale(H, anchor_pose7):
     Hc = T.T @ H @ T
     sigma = np.abs(T) @ np.sqrt(np.clip(np.diag(Hc), 0.0, None))
     return np.outer(sigma, sigma)
+
+
+# Render bar: hit indices bit-exact, depth and colour within 1e-5 relative.
+RTOL = 1e-5
+
+
+def check_render(out, ref, atol_rgb=1e-6):
+    """GPU render outputs (tensors; mask optional) against an oracle render."""
+    hk = out["hitk"].cpu().numpy().reshape(ref["hitk"].shape)
+    assert np.array_equal(hk, ref["hitk"]), f"{np.sum(hk != ref['hitk'])} hit indices differ"
+    if out.get("mask") is not None:
+        mask = out["mask"].cpu().numpy().reshape(ref["mask"].shape)
+        assert np.array_equal(mask, ref["mask"])
+    d = out["depth"].cpu().numpy().reshape(ref["depth"].shape)
+    m = ref["mask"] > 0
+    assert np.all(d[~m] == 0)
+    err = np.abs(d[m] - ref["depth"][m])
+    assert np.all(err <= RTOL * ref["depth"][m]), err.max()
+    c = out["rgb"].cpu().numpy().reshape(ref["rgb"].shape)
+    np.testing.assert_allclose(c[m], ref["rgb"][m], rtol=RTOL, atol=atol_rgb)

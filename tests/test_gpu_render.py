@@ -8,25 +8,10 @@ import pytest
 import torch
 
 import synth
-from gpu_helpers import bf16_round, make_pair, t
+from gpu_helpers import RTOL, bf16_round, check_render, make_pair, t
 
 pytestmark = pytest.mark.gpu
 
-RTOL = 1e-5
-
-
-def check_render(out, ref, atol_rgb=1e-6):
-    hk = out["hitk"].cpu().numpy().reshape(ref["hitk"].shape)
-    assert np.array_equal(hk, ref["hitk"]), f"{np.sum(hk != ref['hitk'])} hit indices differ"
-    mask = out["mask"].cpu().numpy().reshape(ref["mask"].shape)
-    assert np.array_equal(mask, ref["mask"])
-    d = out["depth"].cpu().numpy().reshape(ref["depth"].shape)
-    m = ref["mask"] > 0
-    assert np.all(d[~m] == 0)
-    err = np.abs(d[m] - ref["depth"][m])
-    assert np.all(err <= RTOL * ref["depth"][m]), err.max()
-    c = out["rgb"].cpu().numpy().reshape(ref["rgb"].shape)
-    np.testing.assert_allclose(c[m], ref["rgb"][m], rtol=RTOL, atol=atol_rgb)
 
 
 @pytest.mark.parametrize("name,frames", [("room64_80x60", (0, 7, 23)), ("room128_320x240", (0, 51))])
