@@ -380,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
     loc_ms = tm["localise_ms"] / max(tm["localise_n"], 1)
 
     # ---- end to end through the same public call ----
-    e2e = None
+    e2e = calib = None
     if not args.no_e2e:
         Dh = D.cpu().pin_memory()
         Ch = C.cpu().pin_memory()
@@ -392,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
             F2.step(imus[i], w.dt, D[i], C[i])
         torch.cuda.synchronize()
         barrier()
-        lat = []
+        lat, e2e_states = [], []
         gc.collect()
         gc.disable()
         t0 = time.perf_counter()
@@ -401,7 +401,7 @@ def run_ours(args, rank, world, local_rank):
             ts = time.perf_counter()
             d_buf.copy_(Dh[i], non_blocking=True)
             c_buf.copy_(Ch[i], non_blocking=True)
-            F2.step(imus[i], w.dt, d_buf, c_buf, want_state=True)   # state read back to the host
+            e2e_states.append(F2.step(imus[i], w.dt, d_buf, c_buf, want_state=True))   # state read back
             lat.append((time.perf_counter() - ts) * 1e3)
         torch.cuda.synchronize()   # the last step's map update and render are part of the run
         e2e_s = time.perf_counter() - t0
@@ -416,6 +416,20 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(d_buf.numel() * 4 + c_buf.numel() * 4 + imu_bytes),
                "d2h_bytes_per_step": ctypes.sizeof(State),
                "p50_step_ms": statistics.median(lat), "p99_step_ms": float(np.percentile(lat, 99))}
+        # State-uncertainty calibration (App. G) of the states read back in
+        # that run, against the trajectory's true poses
+        from paper_2212_02988_gb300 import calibration, state_arrays
+        sa = [state_arrays(x) for x in e2e_states]
+        cr = calibration.calibrate(np.array([a["pose"] for a in sa]), np.array([a["cov"] for a in sa]),
+                                   np.array([seq.pose7(1 + W + j) for j in range(K)]))
+        p95 = calibration.chi2_cdf(cr["nssr"] * cr["scale"], 6) <= 0.95
+        calib = {"frames": K, "rms_translation_m": cr["rms_translation"],
+                 "rms_rotation_deg": cr["rms_rotation_deg"], "ml_scale": cr["scale"],
+                 "frac_within_chi2_95_unscaled": float(np.mean(p95)),
+                 "curve_observed_at": {f"{q:.2f}": float(o) for q, o in zip(cr["levels"], cr["observed"])
+                                       if round(q * 20) % 4 == 2},
+                 "note": "pose residuals against the true poses whitened by the filter's pose covariance; "
+                         "ml_scale < 1: the covariances are pessimistic (App. G)"}
 
     res = {
         "metric": METRIC, "value": frames / elapsed, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -455,6 +469,7 @@ def run_ours(args, rank, world, local_rank):
         "render_adjoint": adj,
         "pose_optimiser_adam": adam,
         "rollout": roll,
+        "calibration": calib,
         "gpu_launches": int(d_st["kernel_launches"]),
         "clocks": clocks,
     }
