@@ -134,7 +134,7 @@ struct RollOut {
 cudaError_t launch_rollout_states(const KParams& P, const DevState* src, DevState* scratch, int n_seq, int k,
                                   const double* imu, const long long* row0, const int* counts, const double* dts,
                                   RollOut* out, float* mats, cudaStream_t s);
-// render.cu — the render of `frames` poses in one launch (grid z = frame):
+// The render of `frames` poses in one launch (grid z = frame):
 // frame f reads mats[12 f ..] and writes depth / rgb / hitk at f H W
 // (f H W 3 for rgb); each output may be NULL.  frames <= 65535.
 cudaError_t launch_render_frames(const KParams& P, const float* mats, int frames, const MapPlanes& M, float* depth,

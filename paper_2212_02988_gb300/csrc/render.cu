@@ -22,25 +22,6 @@ __global__ void __launch_bounds__(128, 10) k_render(KParams P, const float* __re
     render_tile<BF16, DETAIL, PX>(P, sR, sc, M, depth, rgb, mask, hitk, stats, blockIdx.x, blockIdx.y);
 }
 
-// The render of many poses in one launch: grid z indexes the frame.
-template <bool BF16, int PX>
-__global__ void __launch_bounds__(128, 10) k_render_frames(KParams P, const float* __restrict__ mats, MapPlanes M,
-                                                       float* __restrict__ depth, float* __restrict__ rgb,
-                                                       int32_t* __restrict__ hitk, DevStats* __restrict__ stats) {
-    pdl_enter();
-    __shared__ float sR[9], sc[3];
-    const size_t f = blockIdx.z, npix = (size_t)P.W * P.H;
-    if (threadIdx.x < 12) {
-        const float v = mats[12 * f + threadIdx.x];
-        if (threadIdx.x < 9) sR[threadIdx.x] = v;
-        else sc[threadIdx.x - 9] = v;
-    }
-    __syncthreads();
-    render_tile<BF16, false, PX>(P, sR, sc, M, depth ? depth + f * npix : nullptr,
-                                 rgb ? rgb + 3 * f * npix : nullptr, nullptr, hitk ? hitk + f * npix : nullptr,
-                                 stats, blockIdx.x, blockIdx.y);
-}
-
 __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t* __restrict__ mask) {
     pdl_enter();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,25 +67,6 @@ cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& 
         else render_px<false, false>(P, grid, mats, M, depth, rgb, mask, hitk, stats, anchor_src, anchor_dst, s);
     }
     return cudaGetLastError();
-}
-
-template <bool BF16>
-static cudaError_t render_frames_px(const KParams& P, dim3 grid, const float* mats, const MapPlanes& M, float* depth,
-                                   float* rgb, int32_t* hitk, DevStats* stats, cudaStream_t s) {
-    switch (render_px_specialisation(P)) {
-        case 66: return launch_pdl(k_render_frames<BF16, 66>, grid, 128, s, P, mats, M, depth, rgb, hitk, stats);
-        case 130: return launch_pdl(k_render_frames<BF16, 130>, grid, 128, s, P, mats, M, depth, rgb, hitk, stats);
-        case 258: return launch_pdl(k_render_frames<BF16, 258>, grid, 128, s, P, mats, M, depth, rgb, hitk, stats);
-        default: return launch_pdl(k_render_frames<BF16, 0>, grid, 128, s, P, mats, M, depth, rgb, hitk, stats);
-    }
-}
-
-cudaError_t launch_render_frames(const KParams& P, const float* mats, int frames, const MapPlanes& M, float* depth,
-                                 float* rgb, int32_t* hitk, DevStats* stats, cudaStream_t s) {
-    if (frames < 1 || frames > 65535) return cudaErrorInvalidValue;
-    const dim3 grid((P.W + 15) / 16, (P.H + 7) / 8, frames);
-    return P.bf16 ? render_frames_px<true>(P, grid, mats, M, depth, rgb, hitk, stats, s)
-                  : render_frames_px<false>(P, grid, mats, M, depth, rgb, hitk, stats, s);
 }
 
 cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s) {
