@@ -428,8 +428,8 @@ def run_ours(args, rank, world, local_rank):
                  "frac_within_chi2_95_unscaled": float(np.mean(p95)),
                  "curve_observed_at": {f"{q:.2f}": float(o) for q, o in zip(cr["levels"], cr["observed"])
                                        if round(q * 20) % 4 == 2},
-                 "note": "pose residuals against the true poses whitened by the filter's pose covariance; "
-                         "ml_scale < 1: the covariances are pessimistic (App. G)"}
+                 "note": "pose residuals against the true poses whitened by the filter's pose covariance "
+                         "(App. G); ml_scale > 1: the covariances are smaller than the errors, < 1: pessimistic"}
 
     res = {
         "metric": METRIC, "value": frames / elapsed, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
