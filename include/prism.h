@@ -199,6 +199,23 @@ prism_status prism_render(prism_handle h, const double* pose7, float* depth, flo
 prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
                         const float* depth, const float* rgb, prism_state* out);
 
+/* prism_step with the frame in HOST memory: depth_host (H x W floats) and
+ * rgb_host (H x W x 3 floats) are copied into device buffers the handle
+ * owns (two, used in turn).  After the first step the copies run on a copy
+ * stream of the handle beside the prediction, so that the upload of frame t
+ * overlaps frame t-1's map update and anchor render; the buffer a step
+ * writes was last read two steps before, which the posterior of the step
+ * before has already waited for.  Pinned host memory that the device maps
+ * (cudaMallocHost / cudaHostAlloc under unified addressing) is read by a
+ * copy kernel; other host memory goes through cudaMemcpyAsync, which
+ * stages pageable memory before the call returns.  With out given the copies are
+ * complete when the call returns; with out NULL they may still be in flight,
+ * so keep the host frames unchanged until the next call on the handle
+ * returns (which waits for them).  Otherwise as prism_step.  The first call
+ * allocates the two buffers (PRISM_ENOMEM if it cannot). */
+prism_status prism_step_host(prism_handle h, const double* imu, int32_t n, double dt,
+                             const float* depth_host, const float* rgb_host, prism_state* out);
+
 /* Copy the state to HOST memory (synchronises the stream; reports a pending
  * device-side PRISM_ENOTPD). */
 prism_status prism_get_state(prism_handle h, prism_state* out);

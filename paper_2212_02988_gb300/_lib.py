@@ -105,6 +105,7 @@ def load() -> C.CDLL:
         "prism_update_map": (st, [H, fp, fp]),
         "prism_render": (st, [H, dp, fp, fp, vp, vp]),
         "prism_step": (st, [H, dp, C.c_int32, C.c_double, fp, fp, P(State)]),
+        "prism_step_host": (st, [H, dp, C.c_int32, C.c_double, fp, fp, P(State)]),
         "prism_get_state": (st, [H, P(State)]),
         "prism_set_state": (st, [H, P(State)]),
         "prism_map_load": (st, [H, fp, fp, fp, fp]),

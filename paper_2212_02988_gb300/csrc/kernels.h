@@ -114,6 +114,10 @@ cudaError_t launch_map_load(const KParams& P, const MapPlanes& M, const float* o
                             const float* var_occ, const float* var_rgb, cudaStream_t s);
 cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, float* rgb, float* var_occ,
                              float* var_rgb, cudaStream_t s);
+// A frame in mapped pinned host memory (s0, s1: its device views) copied to
+// d0, d1 (n0, n1 floats) by the SMs' loads; a plain launch of `blocks`.
+cudaError_t launch_frame_upload(const float* s0, float* d0, size_t n0, const float* s1, float* d1, size_t n1,
+                                int blocks, cudaStream_t s);
 // The tile bounds M.tb of the whole map (after a fill or a load), and the
 // brick bounds M.bb derived from them (after any change of M.tb).
 cudaError_t launch_tile_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s);

@@ -113,6 +113,50 @@ cudaError_t launch_map_store(const KParams& P, const MapPlanes& M, float* occ, f
     return cudaGetLastError();
 }
 
+// A frame in pinned host memory that the device maps (s0, s1: device views of
+// it) copied by the SMs' own loads: n0 floats s0 -> d0, n1 floats s1 -> d1.
+// Each thread has four 16-byte loads in flight per round (the host memory's
+// latency is the bound); single floats where an address is not 16-byte
+// aligned, and for the tail.
+__global__ void __launch_bounds__(256) k_frame_upload(const float* __restrict__ s0, float* __restrict__ d0,
+                                                      size_t n0, const float* __restrict__ s1,
+                                                      float* __restrict__ d1, size_t n1) {
+    pdl_enter();
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    const float* src[2] = {s0, s1};
+    float* dst[2] = {d0, d1};
+    const size_t cnt[2] = {n0, n1};
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float* s = src[a];
+        float* d = dst[a];
+        const size_t n = cnt[a];
+        size_t done = 0;
+        if (((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(d)) & 15) == 0) {
+            const size_t nv = n / 4;
+            const float4* s4 = reinterpret_cast<const float4*>(s);
+            float4* d4 = reinterpret_cast<float4*>(d);
+            size_t i = tid;
+            for (; i + 3 * stride < nv; i += 4 * stride) {
+                const float4 x0 = s4[i], x1 = s4[i + stride], x2 = s4[i + 2 * stride], x3 = s4[i + 3 * stride];
+                d4[i] = x0;
+                d4[i + stride] = x1;
+                d4[i + 2 * stride] = x2;
+                d4[i + 3 * stride] = x3;
+            }
+            for (; i < nv; i += stride) d4[i] = s4[i];
+            done = nv * 4;
+        }
+        for (size_t i = done + tid; i < n; i += stride) d[i] = s[i];
+    }
+}
+
+cudaError_t launch_frame_upload(const float* s0, float* d0, size_t n0, const float* s1, float* d1, size_t n1,
+                                int blocks, cudaStream_t s) {
+    k_frame_upload<<<blocks, 256, 0, s>>>(s0, d0, n0, s1, d1, n1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tile_bounds(const KParams& P, const MapPlanes& M, cudaStream_t s) {
     const unsigned int tiles = (unsigned int)(P.nbx * P.nby * P.nbz);
     if (P.bf16) launch_pdl(k_tile_bounds<true>, tiles, 256, s, P, M);

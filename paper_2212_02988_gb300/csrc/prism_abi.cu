@@ -165,6 +165,13 @@ struct prism_ctx {
     char* h_roll = nullptr;
     size_t h_roll_cap = 0;
     cudaEvent_t ev_roll = nullptr;
+    // prism_step_host's device copies of the host frames, used in turn, and
+    // the event after the last call's copies
+    float* in_depth[2] = {nullptr, nullptr};
+    float* in_rgb[2] = {nullptr, nullptr};
+    int in_slot = 0;
+    cudaStream_t copy = nullptr;      // their uploads, beside the prediction
+    cudaEvent_t ev_in = nullptr;
     bool has_anchor = false;
     bool anchor_at_mean = false;   // the anchor was rendered at the current state mean
     bool has_prior = false;
@@ -278,6 +285,15 @@ void free_all(prism_handle h) {
         if (h->h_imu[k]) cudaFreeHost(h->h_imu[k]);
         if (h->ev_imu[k]) cudaEventDestroy(h->ev_imu[k]);
     }
+    for (int b = 0; b < 2; ++b) {
+        if (h->in_depth[b]) cudaFree(h->in_depth[b]);
+        if (h->in_rgb[b]) cudaFree(h->in_rgb[b]);
+    }
+    if (h->copy) {
+        cudaStreamSynchronize(h->copy);
+        cudaStreamDestroy(h->copy);
+    }
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->roll_dev) cudaFree(h->roll_dev);
     if (h->h_roll) cudaFreeHost(h->h_roll);
     if (h->ev_roll) cudaEventDestroy(h->ev_roll);
@@ -389,12 +405,14 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
 
 // after_side: the prior was predicted on the side stream (prism_step) and the
 // passes wait for it; prepped: that prediction also left the Gauss-Newton
-// start matrices (the anchor is the one rendered at the state mean).
+// start matrices (the anchor is the one rendered at the state mean);
+// wait_in: the frame is being uploaded on the copy stream (prism_step_host).
 prism_status do_localise(prism_handle h, const float* depth, const float* rgb, bool after_side = false,
-                         bool prepped = false) {
+                         bool prepped = false, bool wait_in = false) {
     PhaseTimer t(h, PH_LOCALISE);
     PoseArg pa{};
     if (after_side) CK(h, cudaStreamWaitEvent(h->stream, h->ev_pred, 0), "wait for the prior");
+    if (wait_in) CK(h, cudaStreamWaitEvent(h->stream, h->ev_in, 0), "wait for the frame");
     if (!prepped) LAUNCH(h, launch_prep(h->dstate, PREP_REL, pa, h->stream, !after_side), "pose matrices");
     if (h->cfg.optimiser == PRISM_OPT_ADAM) {   // the paper's optimiser, then the Laplace pass
         LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
@@ -523,6 +541,10 @@ bool imu_ok(const double* imu, int32_t n, double dt, std::string& why) {
         if (!std::isfinite(imu[i])) { why = "non-finite IMU value"; return false; }
     return true;
 }
+
+// The filter step after its argument checks (prism_step, prism_step_host).
+prism_status step_checked(prism_handle h, const double* imu, int32_t n, double dt, const float* depth,
+                          const float* rgb, prism_state* out, bool wait_in = false);
 
 }  // namespace
 
@@ -725,15 +747,72 @@ prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     if (!depth || !rgb) return fail(h, PRISM_EINVAL, "depth or rgb is NULL");
     DeviceGuard g(h->device);
-    prism_status st;
-    bool mask_ready = false;
     if (h->steps > 0) {
         std::string why;
         if (!imu_ok(imu, n, dt, why)) return fail(h, PRISM_EINVAL, why);
         if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
+    }
+    return step_checked(h, imu, n, dt, depth, rgb, out);
+}
+
+prism_status prism_step_host(prism_handle h, const double* imu, int32_t n, double dt, const float* depth_host,
+                             const float* rgb_host, prism_state* out) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!depth_host || !rgb_host) return fail(h, PRISM_EINVAL, "depth or rgb is NULL");
+    DeviceGuard g(h->device);
+    if (h->steps > 0) {
+        std::string why;
+        if (!imu_ok(imu, n, dt, why)) return fail(h, PRISM_EINVAL, why);
+        if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
+    }
+    const size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    if (!h->ev_in) {
+        for (int b = 0; b < 2; ++b)
+            if (dalloc(h, &h->in_depth[b], npix * 4) != cudaSuccess || dalloc(h, &h->in_rgb[b], npix * 12) != cudaSuccess)
+                return fail(h, PRISM_ENOMEM, "host-frame buffers");
+        CK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "host-frame event");
+        CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "host-frame stream");
+    }
+    CK(h, cudaEventSynchronize(h->ev_in), "previous host-frame copies");
+    const int b = h->in_slot;
+    h->in_slot ^= 1;
+    // after the first step: on the copy stream beside the prediction, behind
+    // the previous posterior (which follows the map update that last read
+    // this buffer); the localisation waits for them before its first pass
+    const bool later = h->steps > 0;
+    cudaStream_t cs = later ? h->copy : h->stream;
+    if (later) CK(h, cudaStreamWaitEvent(h->copy, h->ev_state, 0), "wait for the posterior");
+    // pinned host memory the device maps: the SMs load it (faster over the
+    // host link than the copy engines); anything else: the copy engines
+    cudaPointerAttributes ad{}, ac{};
+    const bool mapped = cudaPointerGetAttributes(&ad, depth_host) == cudaSuccess &&
+                        cudaPointerGetAttributes(&ac, rgb_host) == cudaSuccess && ad.type == cudaMemoryTypeHost &&
+                        ac.type == cudaMemoryTypeHost && ad.devicePointer && ac.devicePointer;
+    cudaGetLastError();
+    if (mapped) {
+        LAUNCH(h, launch_frame_upload((const float*)ad.devicePointer, h->in_depth[b], npix,
+                                      (const float*)ac.devicePointer, h->in_rgb[b], 3 * npix, h->max_blocks / 4, cs),
+               "frame upload");
+    } else {
+        CK(h, cudaMemcpyAsync(h->in_depth[b], depth_host, npix * 4, cudaMemcpyHostToDevice, cs), "depth upload");
+        CK(h, cudaMemcpyAsync(h->in_rgb[b], rgb_host, npix * 12, cudaMemcpyHostToDevice, cs), "rgb upload");
+    }
+    CK(h, cudaEventRecord(h->ev_in, cs), "host-frame event");
+    return step_checked(h, imu, n, dt, h->in_depth[b], h->in_rgb[b], out, later);
+}
+
+}  // extern "C"
+
+namespace {
+
+prism_status step_checked(prism_handle h, const double* imu, int32_t n, double dt, const float* depth,
+                          const float* rgb, prism_state* out, bool wait_in) {
+    prism_status st;
+    bool mask_ready = false;
+    if (h->steps > 0) {
         const bool prep = h->anchor_at_mean;
         if ((st = do_predict_side(h, imu, n, dt, prep)) != PRISM_OK) return st;
-        if ((st = do_localise(h, depth, rgb, true, prep)) != PRISM_OK) return st;
+        if ((st = do_localise(h, depth, rgb, true, prep, wait_in)) != PRISM_OK) return st;
         mask_ready = true;
     }
     if ((st = do_fuse(h, depth, rgb, mask_ready)) != PRISM_OK) return st;
@@ -742,6 +821,10 @@ prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
     if (!out) return PRISM_OK;
     return read_posterior(h, out);
 }
+
+}  // namespace
+
+extern "C" {
 
 prism_status prism_get_state(prism_handle h, prism_state* out) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");

@@ -68,6 +68,19 @@ def _dptr(t: torch.Tensor | None, shape=None, dtype=torch.float32, name="tensor"
     return C.c_void_p(t.data_ptr())
 
 
+def _host_img(a, shape, name):
+    """Pointer to a host float32 image: a contiguous numpy array or CPU tensor
+    (pinned memory makes the library's copy asynchronous)."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name} must be a contiguous float32 CPU tensor of shape {tuple(shape)}")
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous or \
+            tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} must be a contiguous float32 array of shape {tuple(shape)}")
+    return C.c_void_p(a.ctypes.data)
+
+
 def _hptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -210,6 +223,17 @@ class Filter:
                                          _dptr(out.get("rgb"), shp + (3,), name="rgb"),
                                          _dptr(out.get("hitk"), shp, torch.int32, "hitk")), self.h)
         out["states"] = None if recs is None else [[recs[s_i * k + i] for i in range(k)] for s_i in range(n_seq)]
+        return out
+
+    def step_host(self, imu, dt, depth, rgb, want_state: bool = False):
+        """prism_step_host: the step with the frame in host memory (numpy or
+        CPU tensors; pinned tensors make the upload asynchronous)."""
+        imu = np.zeros((0, 7)) if imu is None else np.ascontiguousarray(imu, dtype=np.float64)
+        d = _host_img(depth, (self.H, self.W), "depth")
+        c = _host_img(rgb, (self.H, self.W, 3), "rgb")
+        out = State() if want_state else None
+        self._check(self.L.prism_step_host(self.h, _hptr(imu) if len(imu) else None, len(imu), dt, d, c,
+                                           C.byref(out) if out is not None else None), self.h)
         return out
 
     def get_state(self) -> State:

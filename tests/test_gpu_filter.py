@@ -39,3 +39,41 @@ def test_filter_steps_match_oracle(oracle_mod, name, n, start):
     st = F.stats()
     assert st["render_rays"] == n * w.width * w.height
     F.close()
+
+
+def test_step_host_matches_step(oracle_mod):
+    """prism_step_host (frames in host memory, uploaded on the prediction
+    stream) gives bit for bit what prism_step gives on device frames, with
+    pinned tensors, pageable arrays and steps that return no state mixed."""
+    import torch
+    from paper_2212_02988_gb300 import state_arrays
+    w = synth.ROOM128
+    n = 10
+    s = synth.Sequence(w, n_frames=n)
+    m = s.settled_map()
+    A, _ = make_pair(w, oracle_mod, map_arrays=m, s1_pose=s.pose7(0), vel=s.velocity(0))
+    B, _ = make_pair(w, oracle_mod, map_arrays=m, s1_pose=s.pose7(0), vel=s.velocity(0))
+    for i in range(n):
+        f = s.frame(i)
+        imu = s.imu_window(i) if i else None
+        want = i % 3 != 1
+        a = A.step(imu, w.dt, t(f["depth"]), t(f["rgb"]), want_state=want)
+        if i % 2:
+            hd, hc = (torch.from_numpy(np.ascontiguousarray(f[k], dtype=np.float32)).pin_memory()
+                      for k in ("depth", "rgb"))
+        else:
+            hd, hc = (np.ascontiguousarray(f[k], dtype=np.float32) for k in ("depth", "rgb"))
+        b = B.step_host(imu, w.dt, hd, hc, want_state=want)
+        if want:
+            sa, sb = state_arrays(a), state_arrays(b)
+            for key in ("pose", "vel", "cov"):
+                assert np.array_equal(sa[key], sb[key]), (i, key)
+        if not want:
+            torch.cuda.synchronize()   # the host frames must outlive their upload
+    ra, rb = A.render(), B.render()
+    assert torch.equal(ra["hitk"], rb["hitk"]) and torch.equal(ra["depth"], rb["depth"])
+    sa, sb = state_arrays(A.get_state()), state_arrays(B.get_state())
+    for key in ("pose", "vel", "cov"):
+        assert np.array_equal(sa[key], sb[key])
+    A.close()
+    B.close()
