@@ -766,12 +766,15 @@ prism_status prism_step_host(prism_handle h, const double* imu, int32_t n, doubl
         if (!h->has_anchor) return fail(h, PRISM_ESTATE, "no anchor");
     }
     const size_t npix = (size_t)h->cfg.width * h->cfg.height;
-    if (!h->ev_in) {
+    if (!h->ev_in || !h->copy) {   // first call (or one after a failed set-up): what is missing
         for (int b = 0; b < 2; ++b)
-            if (dalloc(h, &h->in_depth[b], npix * 4) != cudaSuccess || dalloc(h, &h->in_rgb[b], npix * 12) != cudaSuccess)
+            if ((!h->in_depth[b] && dalloc(h, &h->in_depth[b], npix * 4) != cudaSuccess) ||
+                (!h->in_rgb[b] && dalloc(h, &h->in_rgb[b], npix * 12) != cudaSuccess)) {
+                cudaGetLastError();
                 return fail(h, PRISM_ENOMEM, "host-frame buffers");
-        CK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "host-frame event");
-        CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "host-frame stream");
+            }
+        if (!h->ev_in) CK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "host-frame event");
+        if (!h->copy) CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "host-frame stream");
     }
     CK(h, cudaEventSynchronize(h->ev_in), "previous host-frame copies");
     const int b = h->in_slot;
