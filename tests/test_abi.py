@@ -163,3 +163,19 @@ def test_serve_create_rejects_bad_config_without_gpu_work(lib):
     c.max_slots, c.n_gn = 8, 63
     assert L.prism_serve_create(C.byref(c), C.byref(h)) == lib.EINVAL
     assert L.prism_serve_destroy(None) == lib.EINVAL
+
+
+def test_entry_points_reject_a_null_handle_without_gpu_work(lib):
+    """Every handle-taking entry answers PRISM_EINVAL for a NULL handle
+    before touching the device (the check runs on a machine without a GPU)."""
+    L = lib.load()
+    f = C.c_float(0.0)
+    st = lib.State()
+    assert L.prism_step(None, None, 0, 0.1, C.byref(f), C.byref(f), None) == lib.EINVAL
+    assert L.prism_step_host(None, None, 0, 0.1, C.byref(f), C.byref(f), C.byref(st)) == lib.EINVAL
+    cnt = (C.c_int32 * 1)(0)
+    dts = (C.c_double * 1)(0.1)
+    assert L.prism_rollout(None, 1, 1, None, cnt, dts, None, None, None, None) == lib.EINVAL
+    assert L.prism_predict(None, None, 0, 0.1) == lib.EINVAL
+    assert L.prism_get_state(None, C.byref(st)) == lib.EINVAL
+    assert b"NULL" in L.prism_last_error(None)
