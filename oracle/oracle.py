@@ -345,6 +345,43 @@ def rollout(p: Params, s: State, windows, dts, occ=None, rgb=None):
     return states, images
 
 
+def map_loss_grad(p: Params, occ, rgb, poses, depths, rgbs, sd: float, sc: float):
+    """The rendering loss of gradient-descent mapping (the alternative to the
+    closed-form update, Sec. 4.4, Fig. sdfvsvi) and its gradient in the map
+    means: sum over frames and over pixels where the render (App. B) hits and
+    the observed depth is valid of (d - D)^2 / (2 sd^2) + |c - C|^2 / (2 sc^2),
+    the gradient carried to the voxels by the render adjoint; plus the
+    Gaussian prior of App. B, sum (mu - mu0)^2 / (2 prior_var).  Returns
+    (loss, g_occ, g_rgb)."""
+    occ, rgb = _f64(occ), _f64(rgb)
+    g_occ, g_rgb = np.zeros_like(occ), np.zeros_like(rgb)
+    loss = 0.0
+    for pose, D, Cobs in zip(poses, depths, rgbs):
+        r = render(p, occ, rgb, pose)
+        D = np.asarray(D, dtype=np.float64)
+        v = (r["mask"] > 0) & np.isfinite(D) & (D > 0)
+        dd = np.where(v, r["depth"] - D, 0.0)
+        dc = np.where(v[..., None], r["rgb"] - np.asarray(Cobs, dtype=np.float64), 0.0)
+        loss += float(np.sum(dd * dd) / (2 * sd * sd) + np.sum(dc * dc) / (2 * sc * sc))
+        b = render_backward(p, occ, rgb, pose, dd / (sd * sd), dc / (sc * sc))
+        g_occ += b["occ"]
+        g_rgb += b["rgb"]
+    v0 = p.prior_var   # prior means: occupancy init_occ, colour 0 (App. F.2)
+    loss += float(np.sum((occ - p.init_occ) ** 2) + np.sum(rgb ** 2)) / (2 * v0)
+    g_occ += (occ - p.init_occ) / v0
+    g_rgb += rgb / v0
+    return loss, g_occ, g_rgb
+
+
+def map_descent(p: Params, occ, rgb, poses, depths, rgbs, sd: float, sc: float, lr_occ: float,
+                lr_rgb: float):
+    """One step of gradient descent on map_loss_grad's loss:
+    mu <- mu - lr g, lr_occ for occupancy and lr_rgb for colour.  Returns
+    (occ', rgb', loss before the step)."""
+    loss, g_occ, g_rgb = map_loss_grad(p, occ, rgb, poses, depths, rgbs, sd, sc)
+    return _f64(occ) - lr_occ * g_occ, _f64(rgb) - lr_rgb * g_rgb, loss
+
+
 def fuse(p: Params, m: dict, pose7, depth, rgb):
     """In-place FP64 map update; m holds occ, rgb, var_occ, var_rgb (float64)."""
     for k in ("occ", "rgb", "var_occ", "var_rgb"):
