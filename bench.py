@@ -337,6 +337,9 @@ def run_ours(args, rank, world, local_rank):
                         "launch, wall time per call with the states read back; not part of the step"}
     F.close()
 
+    # Closed-form against gradient-descent mapping (Sec. 4.4); not part of the step.
+    mapping = mapping_comparison(dev) if K > 0 else None
+
     # The paper's pose optimiser (App. F.2: Adam, momentum off, 1000 steps of
     # 200 pixels) on the same frames, for its localisation time beside the
     # Gauss-Newton passes it is the alternative to; not part of the step.
@@ -470,11 +473,105 @@ def run_ours(args, rank, world, local_rank):
         "render_adjoint": adj,
         "pose_optimiser_adam": adam,
         "rollout": roll,
+        "mapping_comparison": mapping,
         "calibration": calib,
         "gpu_launches": int(d_st["kernel_launches"]),
         "clocks": clocks,
     }
     return res
+
+
+# ------------------------------------------------- mapping: closed form vs descent
+def mapping_comparison(dev, n_start: int = 8, n_frames: int = 8, budget_its: int = 240):
+    """Closed-form map updates against gradient-descent mapping (Sec. 4.4,
+    Fig. sdfvsvi) on the 128^3 / 320x240 room: both start from the map that
+    closed-form updates of frames 0..n_start-1 leave (at the true poses) and
+    take in frames n_start..n_start+n_frames-1; the error is the mean
+    absolute difference between the map's render at those poses and the
+    noise-free depth.  Device time (CUDA events around the calls)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2212_02988_gb300 import Filter, config, make_state
+    from synth.gpu_frames import raycast_frames
+
+    w = synth.ROOM128
+    seq = synth.Sequence(w, n_frames=n_start + n_frames + 1, seed=w.seed + 7)
+    idx = list(range(n_start + n_frames))
+    D, Cc = raycast_frames(seq, idx, dev)
+    Dc, _ = raycast_frames(seq, idx, dev, noise=False)
+    cfg = config(w.n, w.extent, w.width, w.height)
+    F = Filter(cfg, make_state(seq.pose7(0)), device=dev.index)
+    for i in range(n_start):
+        F.set_state(make_state(seq.pose7(i)))
+        F.update_map(D[i], Cc[i])
+    start = F.map_store()
+    test = list(range(n_start, n_start + n_frames))
+    poses = np.stack([seq.pose7(i) for i in test])
+    tD, tC = D[n_start:].contiguous(), Cc[n_start:].contiguous()
+
+    def depth_error():
+        errs = []
+        for j, i in enumerate(test):
+            r = F.render(poses[j])
+            m = (r["mask"] > 0) & (Dc[i] > 0)
+            errs.append(torch.abs(r["depth"][m] - Dc[i][m]).mean().item())
+        return float(np.mean(errs))
+
+    def reset():
+        F.map_load(start["occ"], start["rgb"], start["var_occ"], start["var_rgb"])
+        torch.cuda.synchronize()
+
+    e0 = depth_error()
+    # closed form: one map update a frame (the fuse, App. D)
+    cf_ms = 0.0
+    for j, i in enumerate(test):
+        F.set_state(make_state(poses[j]))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        F.update_map(tD[j], tC[j])
+        b.record()
+        torch.cuda.synchronize()
+        cf_ms += a.elapsed_time(b)
+    e_cf = depth_error()
+    # descent: plain steps over all the frames; the step size is the best of
+    # a short sweep (20 steps each), then a longer run
+    sd, sc = 0.02, 0.1
+    best = None
+    for lr in (5e-9, 1e-8, 2e-8, 5e-8, 1e-7):
+        reset()
+        for _ in range(20):
+            loss = F.map_descent(poses, tD, tC, sd, sc, lr, 5 * lr, want_loss=False)
+        loss = F.map_descent(poses, tD, tC, sd, sc, 0.0, 0.0)
+        if np.isfinite(loss) and (best is None or loss < best[1]):
+            best = (lr, loss)
+    lr = best[0]
+    reset()
+    curve, ms, matched = [(0.0, e0)], 0.0, None
+    marks = {1, 2, 4, 8, 16, 32, 64, 128, 240}
+    for it in range(1, budget_its + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        F.map_descent(poses, tD, tC, sd, sc, lr, 5 * lr, want_loss=False)
+        b.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+        if it in marks:
+            e = depth_error()
+            curve.append((ms, e))
+            if matched is None and e <= e_cf:
+                matched = ms
+    F.close()
+    return {"workload": w.name, "start_frames": n_start, "frames": n_frames,
+            "start_depth_error_m": e0,
+            "closed_form": {"ms": cf_ms, "depth_error_m": e_cf},
+            "descent": {"lr_occ": lr, "lr_rgb": 5 * lr, "sd": sd, "sc": sc,
+                        "curve_ms_error_m": curve, "ms_to_match_closed_form": matched,
+                        "ms_per_step": ms / budget_its},
+            "note": "gradient-descent mapping through the render adjoint (prism_map_descent) against the "
+                    "closed-form update (prism_update_map) on the same frames and start map; depth error of "
+                    "the map's renders against noise-free depth at the frames' poses"}
 
 
 # ---------------------------------------------------------------- serving

@@ -322,6 +322,27 @@ prism_status prism_render_backward(prism_handle h, const double* pose7, const fl
 prism_status prism_rollout(prism_handle h, int32_t n_seq, int32_t k, const double* imu, const int32_t* counts,
                            const double* dt, prism_state* states, float* depth, float* rgb, int32_t* hitk);
 
+/* One step of gradient-descent mapping, the alternative to the closed-form
+ * map update that the paper compares against (Sec. 4.4, Fig. sdfvsvi), over
+ * n frames with known poses.  For each frame the map mean is rendered at its
+ * pose (App. B); where the render hits and the observed depth is valid
+ * (finite, > 0) the loss gains (d - D)^2 / (2 sd^2) + |c - C|^2 / (2 sc^2),
+ * and the render adjoint carries its gradient to the occupancy and colour
+ * means, summed over the frames.  With the App. B prior (mean init_occ /
+ * init_rgb, variance prior_var) every mean then takes the step
+ * mu <- mu - lr (g + (mu - mu0) / prior_var), lr_occ for occupancy and
+ * lr_rgb for colour; variances are not changed.  The frames are those of
+ * the map before the step (all frames first, then one update).
+ * poses: HOST, n x 7 (t, q); depth (n x H x W floats) and rgb (n x H x W x 3
+ * floats): DEVICE.  sd, sc > 0; lr_occ, lr_rgb >= 0.  loss: HOST, 1 double,
+ * the loss before the step (data and prior terms), or NULL; when given the
+ * stream is synchronised.  The first call allocates the gradient and render
+ * buffers (PRISM_ENOMEM if it cannot).  PRISM_EINVAL for n < 1, a pose that
+ * is not finite or has a zero quaternion, or a bad scale or step size. */
+prism_status prism_map_descent(prism_handle h, int32_t n, const double* poses, const float* depth,
+                               const float* rgb, double sd, double sc, double lr_occ, double lr_rgb,
+                               double* loss);
+
 /* Work counters and per-phase timing.  Detail counters (off by default)
  * make the render also count the distinct trilinear corners each ray
  * reads, at a few instructions per sample. */

@@ -122,6 +122,8 @@ def load() -> C.CDLL:
         "prism_status_string": (C.c_char_p, [C.c_int32]),
         "prism_render_backward": (st, [H, dp, fp, fp, fp, fp, dp, dp]),
         "prism_rollout": (st, [H, C.c_int32, C.c_int32, dp, P(C.c_int32), dp, P(State), fp, fp, fp]),
+        "prism_map_descent": (st, [H, C.c_int32, dp, fp, fp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   dp]),
         "prism_normal_equations_noalloc": (st, [P(Config), dp, fp, fp, dp, fp, fp, vp, dp]),
         "prism_noalloc_last_error": (C.c_char_p, []),
         "prism_serve_config_default": (None, [P(ServeConfig)]),

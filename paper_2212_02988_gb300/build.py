@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libprism.so")
 SOURCES = ["render.cu", "track.cu", "state.cu", "fuse.cu", "mapio.cu", "prism_abi.cu", "noalloc.cu",
-           "render_bwd.cu", "serve_kernels.cu", "serve.cu", "adam.cu", "rollout.cu"]
+           "render_bwd.cu", "serve_kernels.cu", "serve.cu", "adam.cu", "rollout.cu", "mapping.cu"]
 HEADERS = ["prism_dev.cuh", "linalg64.cuh", "kernels.h", "render_dev.cuh", "track_dev.cuh", "fuse_dev.cuh",
            "state_dev.cuh", "serve.h", "host_util.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

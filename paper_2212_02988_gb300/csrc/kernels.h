@@ -144,6 +144,21 @@ cudaError_t launch_rollout_states(const KParams& P, const DevState* src, DevStat
 cudaError_t launch_render_frames(const KParams& P, const float* mats, int frames, const MapPlanes& M, float* depth,
                                  float* rgb, int32_t* hitk, DevStats* stats, cudaStream_t s);
 
+// mapping.cu — gradient-descent mapping (the alternative to the closed-form
+// update).  launch_map_loss: over one rendered frame (depth, rgb, hit mask of
+// the render), where the render hit and obs_d is valid, the loss gradients
+// (d - D) / sd^2 and (c - C) / sc^2 replace depth and rgb (0 elsewhere) and
+// the loss terms are added to *loss.  launch_map_step: mu <- mu - lr (g +
+// (mu - mu0) / prior_var) on every padded element of the occupancy (g_occ, N
+// floats) and colour (g_rgb, 3N floats, linear layout) planes, the prior
+// term of the loss added to *loss; the tile and brick bounds are left to the
+// caller.
+cudaError_t launch_map_loss(const KParams& P, float* depth, float* rgb, const uint8_t* mask, const float* obs_d,
+                            const float* obs_c, double sd, double sc, double* loss, cudaStream_t s);
+cudaError_t launch_map_step(const KParams& P, const MapPlanes& M, const float* g_occ, const float* g_rgb,
+                            double lr_occ, double lr_rgb, double mu0_occ, double mu0_rgb, double prior_var,
+                            double* loss, cudaStream_t s);
+
 // render_bwd.cu — adjoint of the render at the pose whose matrices are in
 // `mats` (DevState::aux); adds the pose gradient to dev->grad_pose.
 cudaError_t launch_render_bwd(const KParams& P, const float* mats, const MapPlanes& M, const float* grad_depth,

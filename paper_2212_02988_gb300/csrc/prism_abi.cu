@@ -165,6 +165,9 @@ struct prism_ctx {
     char* h_roll = nullptr;
     size_t h_roll_cap = 0;
     cudaEvent_t ev_roll = nullptr;
+    // prism_map_descent's buffers: gradients (N + 3N floats), one rendered
+    // frame (depth, colour, hit mask) and the loss, in one block
+    void* md_dev = nullptr;
     // prism_step_host's device copies of the host frames, used in turn, and
     // the event after the last call's copies
     float* in_depth[2] = {nullptr, nullptr};
@@ -294,6 +297,7 @@ void free_all(prism_handle h) {
         cudaStreamDestroy(h->copy);
     }
     if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->md_dev) cudaFree(h->md_dev);
     if (h->roll_dev) cudaFree(h->roll_dev);
     if (h->h_roll) cudaFreeHost(h->h_roll);
     if (h->ev_roll) cudaEventDestroy(h->ev_roll);
@@ -978,6 +982,60 @@ prism_status prism_rollout(prism_handle h, int32_t n_seq, int32_t k, const doubl
         states[f].reserved = 0;
     }
     if (notpd) return fail(h, PRISM_ENOTPD, "device reported: a predicted pose covariance not positive definite");
+    return PRISM_OK;
+}
+
+prism_status prism_map_descent(prism_handle h, int32_t n, const double* poses, const float* depth,
+                               const float* rgb, double sd, double sc, double lr_occ, double lr_rgb,
+                               double* loss) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (n < 1 || !poses || !depth || !rgb) return fail(h, PRISM_EINVAL, "n < 1 or a NULL array");
+    if (!(sd > 0) || !(sc > 0) || !std::isfinite(sd) || !std::isfinite(sc))
+        return fail(h, PRISM_EINVAL, "sd and sc must be finite and > 0");
+    if (!(lr_occ >= 0) || !(lr_rgb >= 0) || !std::isfinite(lr_occ) || !std::isfinite(lr_rgb))
+        return fail(h, PRISM_EINVAL, "step sizes must be finite and >= 0");
+    for (int j = 0; j < n; ++j)
+        if (!finite_pose(poses + 7 * j)) return fail(h, PRISM_EINVAL, "pose is not finite or has a zero quaternion");
+    DeviceGuard g(h->device);
+    const size_t npix = (size_t)h->cfg.width * h->cfg.height;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_grgb = up(h->nvox * sizeof(float));
+    const size_t o_rd = o_grgb + up(3 * h->nvox * sizeof(float));
+    const size_t o_rc = o_rd + up(npix * sizeof(float));
+    const size_t o_rm = o_rc + up(3 * npix * sizeof(float));
+    const size_t o_loss = o_rm + up(npix);
+    const size_t total = o_loss + 256;
+    if (!h->md_dev) CK(h, dalloc(h, &h->md_dev, total), "descent buffers");
+    char* b = (char*)h->md_dev;
+    float* g_occ = (float*)b;
+    float* g_rgb = (float*)(b + o_grgb);
+    float* r_d = (float*)(b + o_rd);
+    float* r_c = (float*)(b + o_rc);
+    uint8_t* r_m = (uint8_t*)(b + o_rm);
+    double* d_loss = (double*)(b + o_loss);
+    CK(h, cudaMemsetAsync(g_occ, 0, o_rd, h->stream), "clear gradients");
+    CK(h, cudaMemsetAsync(d_loss, 0, sizeof(double), h->stream), "clear loss");
+    for (int j = 0; j < n; ++j) {
+        PoseArg pa{};
+        normalise_pose(poses + 7 * j, pa.p);
+        LAUNCH(h, launch_prep(h->dstate, PREP_AUX_C2W, pa, h->stream), "pose matrices");
+        LAUNCH(h, launch_render(h->kp, h->dstate->aux, h->map, r_d, r_c, r_m, nullptr, h->dstats, nullptr, nullptr,
+                                h->detail, h->stream),
+               "render");
+        LAUNCH(h, launch_map_loss(h->kp, r_d, r_c, r_m, depth + npix * j, rgb + 3 * npix * j, sd, sc, d_loss,
+                                  h->stream),
+               "loss gradients");
+        LAUNCH(h, launch_render_bwd(h->kp, h->dstate->aux, h->map, r_d, r_c, g_occ, g_rgb, h->dstate, h->stream),
+               "render adjoint");
+    }
+    LAUNCH(h, launch_map_step(h->kp, h->map, g_occ, g_rgb, lr_occ, lr_rgb, h->cfg.init_occ, h->cfg.init_rgb,
+                              h->cfg.prior_var, d_loss, h->stream),
+           "descent step");
+    LAUNCH(h, launch_tile_bounds(h->kp, h->map, h->stream), "tile bounds");
+    ++h->launches;   // and the brick bounds derived from them
+    if (!loss) return PRISM_OK;
+    CK(h, cudaMemcpyAsync(loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read loss");
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
     return PRISM_OK;
 }
 

@@ -236,6 +236,20 @@ class Filter:
                                            C.byref(out) if out is not None else None), self.h)
         return out
 
+    def map_descent(self, poses, depth, rgb, sd: float, sc: float, lr_occ: float, lr_rgb: float,
+                    want_loss: bool = True):
+        """prism_map_descent: one gradient-descent step on the map means over
+        n frames with known poses (n x 7), depth (n, H, W) and rgb (n, H, W, 3)
+        CUDA tensors.  Returns the loss before the step (or None)."""
+        poses = np.ascontiguousarray(poses, dtype=np.float64).reshape(-1, 7)
+        n = len(poses)
+        d = _dptr(depth, (n, self.H, self.W), name="depth")
+        c = _dptr(rgb, (n, self.H, self.W, 3), name="rgb")
+        out = np.zeros(1) if want_loss else None
+        self._check(self.L.prism_map_descent(self.h, n, _hptr(poses), d, c, sd, sc, lr_occ, lr_rgb,
+                                             _hptr(out)), self.h)
+        return float(out[0]) if want_loss else None
+
     def get_state(self) -> State:
         s = State()
         self._check(self.L.prism_get_state(self.h, C.byref(s)), self.h)
