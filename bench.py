@@ -371,7 +371,7 @@ def run_ours(args, rank, world, local_rank):
     G = samp_per * 8 * b + hits_per * 2 * 8 * 3 * b              # logical gathered voxel bytes
     warm = {k: st_w1[k] - st_w0[k] for k in st_w1}
     u_ratio = warm["render_unique_corners"] / max(warm["render_samples"] * 8, 1)
-    U = samp_per * 8 * b * u_ratio + hits_per * 8 * 3 * b         # per-ray unique bytes (estimate, see DESIGN)
+    U = samp_per * 8 * b * u_ratio + hits_per * 8 * 3 * b         # per-ray unique bytes (estimate from the counted fraction)
     peak, peak_kind = measured_peaks()
     achieved_G = G / (render_ms * 1e-3) / 1e9
     achieved = U / (render_ms * 1e-3) / 1e9

@@ -256,7 +256,8 @@ prism_status prism_normal_equations(prism_handle h, const double* pose7, const f
  * (the rendered anchor) and depth / rgb (the observation) are DEVICE pointers
  * in the image layout, `stream` a cudaStream_t (NULL = legacy default), out
  * a HOST array of 80 doubles laid out as for prism_normal_equations.  Only
- * cfg's image size, intrinsics, gates, scales, floors and disc are used.
+ * cfg's image size, intrinsics, gates, scales, floors and disc are used and
+ * checked.
  *
  * All scratch (packed anchor, the observation's validity mask, per-block
  * partial sums, ticket counter, device state) lives in one static device
@@ -264,8 +265,11 @@ prism_status prism_normal_equations(prism_handle h, const double* pose7, const f
  * until the process exits; the call allocates and frees nothing.  Images
  * larger than PRISM_NOALLOC_MAX_PIXELS are rejected with PRISM_EINVAL.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it: make that
- * first call before any stream capture.  Calls share the array and it keeps
+ * (cudaGetSymbolAddress, with that device current) and caches it for the
+ * life of the process: make that first call before any stream capture, and
+ * do not call the entry point on a device after a cudaDeviceReset of it
+ * (the cached address belonged to the destroyed context).  The device is
+ * the caller's current device; all four image pointers must be on it.  Calls share the array and it keeps
  * the last call's contents: two calls whose work overlaps on the GPU (other
  * streams, other host threads) race and give wrong results; serialise them.
  * The call synchronises `stream` before returning.  Errors: as elsewhere,

@@ -11,6 +11,10 @@ namespace prism {
 
 // Checks a configuration; on failure `why` says what is wrong.
 bool valid_config(const prism_config* c, std::string& why);
+// Checks only the fields the localisation objective reads (image size,
+// intrinsics, gates, Laplace scales, IRLS floors, discontinuity threshold);
+// valid_config includes these checks.
+bool valid_track_config(const prism_config* c, std::string& why);
 // The kernels' parameter block of a configuration (FP32 copies are single
 // roundings of the FP64 values).
 void fill_kparams(const prism_config* c, KParams& k);

@@ -14,12 +14,15 @@
 // Host code may not hand the array's name to a kernel: on the host it only
 // stands in for the symbol.  The device address is obtained once per device,
 // with that device current, by cudaGetSymbolAddress on the first call made on
-// that device, and cached.
+// that device, and cached for the life of the process.  A device reset
+// (cudaDeviceReset) destroys the context that address belongs to; the entry
+// point must not be called on that device after one.
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
 
+#include "host_util.h"
 #include "kernels.h"
 #include "prism.h"
 #include "prism_dev.cuh"
@@ -71,31 +74,6 @@ prism_status scratch_address(int dev, unsigned char** out) {
     return PRISM_OK;
 }
 
-void fill_params(const prism_config* c, KParams& k) {
-    std::memset(&k, 0, sizeof(k));
-    k.nx = c->nx; k.ny = c->ny; k.nz = c->nz;
-    k.W = c->width; k.H = c->height;
-    k.fx32 = (float)c->fx; k.fy32 = (float)c->fy; k.cx32 = (float)c->cx; k.cy32 = (float)c->cy;
-    k.ifx32 = (float)(1.0 / c->fx); k.ify32 = (float)(1.0 / c->fy);
-    k.disc32 = (float)c->disc;
-    k.gate_geo32 = (float)c->gate_geo; k.gate_rgb32 = (float)c->gate_rgb;
-    k.b_geo32 = (float)c->b_geo; k.b_rgb32 = (float)c->b_rgb;
-    k.floor_geo32 = (float)c->floor_geo; k.floor_rgb32 = (float)c->floor_rgb;
-    k.fx = c->fx; k.fy = c->fy; k.cx = c->cx; k.cy = c->cy;
-}
-
-void normalise_pose(const double* in, double* out) {
-    const double n = std::sqrt(((in[3] * in[3] + in[4] * in[4]) + in[5] * in[5]) + in[6] * in[6]);
-    for (int a = 0; a < 3; ++a) out[a] = in[a];
-    for (int a = 0; a < 4; ++a) out[3 + a] = in[3 + a] / n;
-}
-
-bool finite_pose(const double* p) {
-    for (int i = 0; i < 7; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6] > 1e-20;
-}
-
 #define NA_CK(call, what)                                                                   \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \
@@ -112,14 +90,12 @@ prism_status prism_normal_equations_noalloc(const prism_config* cfg, const doubl
                                             void* stream, double* out) {
     if (!cfg || !anchor_pose7 || !anchor_depth || !anchor_rgb || !pose7 || !depth || !rgb || !out)
         return fail(PRISM_EINVAL, "NULL argument");
-    if (cfg->width < 3 || cfg->height < 3) return fail(PRISM_EINVAL, "image smaller than 3 x 3");
+    std::string why;
+    if (!valid_track_config(cfg, why)) return fail(PRISM_EINVAL, "invalid config: " + why);
     if ((double)cfg->width * cfg->height > (double)kPix)
         return fail(PRISM_EINVAL, "image has " + std::to_string((long long)cfg->width * cfg->height) +
                                       " pixels; the allocation-free entry point supports at most " +
                                       std::to_string((long long)kPix));
-    if (!(cfg->fx > 0) || !(cfg->fy > 0) || !(cfg->b_geo > 0) || !(cfg->b_rgb > 0) || !(cfg->floor_geo > 0) ||
-        !(cfg->floor_rgb > 0))
-        return fail(PRISM_EINVAL, "fx, fy, Laplace scales and IRLS floors must be > 0");
     if (!finite_pose(anchor_pose7) || !finite_pose(pose7)) return fail(PRISM_EINVAL, "pose is not finite");
     int dev = 0;
     NA_CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -128,7 +104,7 @@ prism_status prism_normal_equations_noalloc(const prism_config* cfg, const doubl
     if (st != PRISM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     KParams P;
-    fill_params(cfg, P);
+    fill_kparams(cfg, P);
     DevState* ds = (DevState*)(base + kOffState);
     unsigned int* counter = (unsigned int*)(base + kOffCounter);
     float* partials = (float*)(base + kOffPartials);

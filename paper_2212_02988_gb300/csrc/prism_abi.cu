@@ -18,20 +18,33 @@ using namespace prism;
 
 namespace prism {
 
+bool valid_track_config(const prism_config* c, std::string& why) {
+    auto bad = [&](const char* m) { why = m; return false; };
+    if (!c) return bad("config is NULL");
+    if (c->width < 3 || c->height < 3 || (double)c->width * c->height > 1.0e8) return bad("image size out of range");
+    if (!(c->fx > 0) || !(c->fy > 0)) return bad("fx, fy must be > 0");
+    if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
+        return bad("Laplace scales and IRLS floors must be > 0");
+    // gates and the discontinuity threshold may be +inf (no gate)
+    if (!(c->gate_geo >= 0) || !(c->gate_rgb >= 0) || !(c->disc >= 0))
+        return bad("gates and the discontinuity threshold must be >= 0");
+    for (double x : {c->cx, c->cy, c->fx, c->fy, c->b_geo, c->b_rgb, c->floor_geo, c->floor_rgb})
+        if (!std::isfinite(x)) return bad("non-finite configuration value");
+    return true;
+}
+
 bool valid_config(const prism_config* c, std::string& why) {
     auto bad = [&](const char* m) { why = m; return false; };
     if (!c) return bad("config is NULL");
+    if (!valid_track_config(c, why)) return false;
     if (c->nx <= 0 || c->ny <= 0 || c->nz <= 0 || (c->nx % 8) || (c->ny % 8) || (c->nz % 8))
         return bad("nx, ny, nz must be positive multiples of 8");
     if ((double)(c->nx + 2) * (c->ny + 2) * (c->nz + 2) > 2147483648.0) return bad("grid larger than 2^31 voxels");
     if (c->storage != PRISM_STORAGE_F32 && c->storage != PRISM_STORAGE_BF16) return bad("storage must be 0 or 1");
-    if (c->width < 3 || c->height < 3 || (double)c->width * c->height > 1.0e8) return bad("image size out of range");
     if (c->n_gn < 1 || c->n_gn > 1000) return bad("n_gn must be in [1, 1000]");
     if (c->skip_empty != 0 && c->skip_empty != 1) return bad("skip_empty must be 0 or 1");
-    if (!(c->voxel > 0) || !(c->eps > 0) || !(c->fx > 0) || !(c->fy > 0)) return bad("voxel, eps, fx, fy must be > 0");
+    if (!(c->voxel > 0) || !(c->eps > 0)) return bad("voxel and eps must be > 0");
     if (!(c->prior_var > 0) || !(c->update_var > 0) || !(c->trunc > 0)) return bad("variances and trunc must be > 0");
-    if (!(c->b_geo > 0) || !(c->b_rgb > 0) || !(c->floor_geo > 0) || !(c->floor_rgb > 0))
-        return bad("Laplace scales and IRLS floors must be > 0");
     if (!(c->ema >= 0 && c->ema <= 1)) return bad("ema must be in [0, 1]");
     if (c->optimiser != PRISM_OPT_GAUSS_NEWTON && c->optimiser != PRISM_OPT_ADAM)
         return bad("optimiser must be 0 (Gauss-Newton) or 1 (Adam)");
@@ -42,7 +55,7 @@ bool valid_config(const prism_config* c, std::string& why) {
             !(c->adam_beta2 < 1))
             return bad("Adam step sizes and eps must be > 0 and beta2 in [0, 1)");
     }
-    for (double x : {c->origin[0], c->origin[1], c->origin[2], c->cx, c->cy, c->tau, c->max_depth})
+    for (double x : {c->origin[0], c->origin[1], c->origin[2], c->tau, c->max_depth})
         if (!std::isfinite(x)) return bad("non-finite configuration value");
     return true;
 }

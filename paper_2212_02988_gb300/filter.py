@@ -85,21 +85,45 @@ def _hptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _common_cuda_device(named) -> torch.device:
+    """The one CUDA device that every (name, tensor) pair lives on; raises
+    ValueError before any device work when they differ or are not CUDA."""
+    devs = {}
+    for name, x in named:
+        if not isinstance(x, torch.Tensor):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        devs.setdefault(x.device, name)
+    if len(devs) != 1:
+        raise ValueError("image tensors must share one device, got " +
+                         ", ".join(f"{n} on {d}" for d, n in devs.items()))
+    (d,) = devs
+    if d.type != "cuda":
+        raise ValueError(f"image tensors must be CUDA tensors, got {d}")
+    return d
+
+
 def normal_equations_noalloc(cfg: Config, anchor_pose7, anchor_depth, anchor_rgb, pose7, depth, rgb,
                              stream: torch.cuda.Stream | None = None) -> dict:
     """prism_normal_equations_noalloc: the normal equations of one pose with
     no device allocation (scratch in the library's static device array; see
-    include/prism.h).  Device arrays are CUDA tensors on the current device."""
+    include/prism.h).  The four images must be CUDA tensors on one device;
+    the call runs on that device, on `stream` (which must belong to it) or
+    on that device's current stream."""
+    d = _common_cuda_device((("anchor_depth", anchor_depth), ("anchor_rgb", anchor_rgb),
+                             ("depth", depth), ("rgb", rgb)))
+    if stream is not None and stream.device != d:
+        raise ValueError(f"stream is on {stream.device}, the images on {d}")
     L = _lib.load()
     H, W = cfg.height, cfg.width
     ap = np.ascontiguousarray(anchor_pose7, dtype=np.float64)
     p = np.ascontiguousarray(pose7, dtype=np.float64)
     out = np.zeros(80)
-    s = stream if stream is not None else torch.cuda.current_stream()
-    st = L.prism_normal_equations_noalloc(C.byref(cfg), _hptr(ap), _dptr(anchor_depth, (H, W), name="anchor_depth"),
-                                          _dptr(anchor_rgb, (H, W, 3), name="anchor_rgb"), _hptr(p),
-                                          _dptr(depth, (H, W), name="depth"), _dptr(rgb, (H, W, 3), name="rgb"),
-                                          C.c_void_p(s.cuda_stream), _hptr(out))
+    with torch.cuda.device(d):
+        s = stream if stream is not None else torch.cuda.current_stream(d)
+        st = L.prism_normal_equations_noalloc(
+            C.byref(cfg), _hptr(ap), _dptr(anchor_depth, (H, W), name="anchor_depth"),
+            _dptr(anchor_rgb, (H, W, 3), name="anchor_rgb"), _hptr(p), _dptr(depth, (H, W), name="depth"),
+            _dptr(rgb, (H, W, 3), name="rgb"), C.c_void_p(s.cuda_stream), _hptr(out))
     if st != _lib.OK:
         raise PrismError(st, L.prism_noalloc_last_error().decode())
     return {"H": out[:36].reshape(6, 6), "g": out[36:42], "Ht": out[42:78].reshape(6, 6),

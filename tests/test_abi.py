@@ -179,3 +179,42 @@ def test_entry_points_reject_a_null_handle_without_gpu_work(lib):
     assert L.prism_predict(None, None, 0, 0.1) == lib.EINVAL
     assert L.prism_get_state(None, C.byref(st)) == lib.EINVAL
     assert b"NULL" in L.prism_last_error(None)
+
+
+def test_noalloc_rejects_bad_arguments_without_gpu_work(lib):
+    """The allocation-free entry checks its configuration, its size limit and
+    its poses before any CUDA call (so this runs without a GPU): a frame just
+    over the stated maximum, a NaN discontinuity threshold, a zero quaternion."""
+    L = lib.load()
+    c = lib.Config()
+    L.prism_config_default(C.byref(c), 64, 4.0, 641, 480)
+    pose = (C.c_double * 7)(0, 0, 0, 1, 0, 0, 0)
+    img = (C.c_float * 4)()
+    out = (C.c_double * 80)()
+    args = lambda cfg, p: (C.byref(cfg), pose, img, img, p, img, img, None, out)
+    assert L.prism_normal_equations_noalloc(*args(c, pose)) == lib.EINVAL
+    assert b"at most 307200" in L.prism_noalloc_last_error()
+    L.prism_config_default(C.byref(c), 64, 4.0, 640, 480)
+    c.disc = float("nan")
+    assert L.prism_normal_equations_noalloc(*args(c, pose)) == lib.EINVAL
+    assert b"discontinuity" in L.prism_noalloc_last_error()
+    c.disc = 0.1
+    zero = (C.c_double * 7)(0, 0, 0, 0, 0, 0, 0)
+    assert L.prism_normal_equations_noalloc(*args(c, zero)) == lib.EINVAL
+    assert b"not finite" in L.prism_noalloc_last_error()
+
+
+def test_noalloc_binding_checks_devices_before_any_call():
+    """The binding refuses image tensors on different devices, or not on a
+    CUDA device, before it reaches the library (CPU and meta tensors stand in
+    for two devices here)."""
+    import torch
+    from paper_2212_02988_gb300.filter import _common_cuda_device
+    a = torch.zeros(2, 2)
+    m = torch.empty(2, 2, device="meta")
+    with pytest.raises(ValueError, match="share one device"):
+        _common_cuda_device((("anchor_depth", a), ("anchor_rgb", a), ("depth", m), ("rgb", a)))
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        _common_cuda_device((("anchor_depth", a), ("depth", a)))
+    with pytest.raises(ValueError, match="must be a CUDA tensor"):
+        _common_cuda_device((("anchor_depth", a), ("depth", None)))

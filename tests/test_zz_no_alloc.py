@@ -26,9 +26,11 @@ def _close(got, ref):
     assert np.all(np.abs(got["g"] - ref["g"]) <= 2e-4 * gscale)
 
 
-def test_noalloc_matches_handle_path(oracle_mod):
+@pytest.mark.parametrize("w", [synth.ROOM128, synth.ROOM256], ids=lambda w: w.name)
+def test_noalloc_matches_handle_path(oracle_mod, w):
+    """320x240, and 640x480: the stated maximum, which fills the scratch
+    array's anchor and mask regions exactly."""
     from paper_2212_02988_gb300 import PrismError, config, normal_equations_noalloc
-    w = synth.ROOM128
     s = synth.Sequence(w)
     F, _ = make_pair(w, oracle_mod)
     A = s.pose7(8)
@@ -49,10 +51,10 @@ def test_noalloc_matches_handle_path(oracle_mod):
     assert torch.cuda.mem_get_info()[0] == free_before
     _close(got0, refs[0])
     _close(got1, refs[1])
-    # images beyond the stated maximum are rejected before any GPU work
-    big = config(w.n, w.extent, 1280, 960)
-    bd = torch.ones((960, 1280), device=ad.device)
-    bc = torch.zeros((960, 1280, 3), device=ad.device)
+    # one pixel column beyond the stated maximum is rejected before any GPU work
+    big = config(w.n, w.extent, 641, 480)
+    bd = torch.ones((480, 641), device=ad.device)
+    bc = torch.zeros((480, 641, 3), device=ad.device)
     with pytest.raises(PrismError) as e:
         normal_equations_noalloc(big, A, bd, bc, poses[0], bd, bc)
     assert e.value.status == -1 and "at most" in str(e.value)
