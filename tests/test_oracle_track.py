@@ -202,3 +202,170 @@ def test_prior_only_returns_prior(oracle_mod, tiny_pair):
     np.testing.assert_allclose(oa["pose"], pa["pose"], atol=1e-14)
     np.testing.assert_allclose(oa["vel"], pa["vel"], atol=1e-14)
     np.testing.assert_allclose(oa["cov"], pa["cov"], rtol=1e-9, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Laplace assembly (Sec. 4.1, App. E.3), EMA (App. F.2) and recombination
+# (Sec. 3.3.2), each rebuilt here from its definition: the Jacobians come from
+# the oracle's residuals (pinned above by finite differences), the SO(3) left
+# Jacobian from finite differences of SciPy's rotations, and everything else
+# is numpy linear algebra written from the paper's formulas.
+
+def left_jacobian_fd(phi, h=1e-6):
+    """J_l(phi) defined by Exp(phi + d) = Exp(J_l d) Exp(phi) to first order,
+    by central differences of SciPy's exponential and logarithm."""
+    R0inv = Rotation.from_rotvec(phi).inv()
+    J = np.zeros((3, 3))
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        J[:, i] = ((Rotation.from_rotvec(phi + e) * R0inv).as_rotvec()
+                   - (Rotation.from_rotvec(phi - e) * R0inv).as_rotvec()) / (2 * h)
+    return J
+
+
+def joint_prior(O, pose7, vel6, seed):
+    """A prior in the form the prediction hands to the localisation (App. E.2):
+    a random SPD 12x12 joint over (pose, velocity) split into the pose
+    marginal and the velocity conditional v | p = vbar + D xi, with
+    D = C_vp C_pp^-1 and Sigma_vel = C_vv - D C_pv."""
+    rng = np.random.default_rng(seed)
+    sd = np.array([0.01, 0.01, 0.01, 0.006, 0.006, 0.006, 0.2, 0.2, 0.2, 0.3, 0.3, 0.3])
+    A = rng.normal(size=(12, 12))
+    corr = A @ A.T + 12 * np.eye(12)
+    corr /= np.sqrt(np.outer(np.diag(corr), np.diag(corr)))
+    C = corr * np.outer(sd, sd)
+    Cpp, Cvp, Cvv = C[:6, :6], C[6:, :6], C[6:, 6:]
+    D = Cvp @ np.linalg.inv(Cpp)
+    Svel = Cvv - D @ Cvp.T
+    pr = O.Prior()
+    for a in range(3):
+        pr.t[a] = pose7[a]
+        pr.v[a], pr.w[a] = vel6[a], vel6[3 + a]
+    for a in range(4):
+        pr.q[a] = pose7[3 + a]
+    for i in range(144):
+        pr.cov[i] = C.flat[i]
+    L = np.linalg.inv(Cpp)
+    for i in range(36):
+        pr.cov_pp[i], pr.prec_pp[i] = Cpp.flat[i], L.flat[i]
+        pr.D[i], pr.cov_vel[i] = D.flat[i], Svel.flat[i]
+    return pr, {"L": L, "D": D, "Svel": Svel, "vbar": np.asarray(vel6, float)}
+
+
+@pytest.fixture(scope="module")
+def laplace_case(oracle_mod, tiny_pair):
+    """One localisation of the tiny textured pair from a prior 6 mm / 0.5 deg
+    off the observed pose, so the optimum xi* is far from 0."""
+    O = oracle_mod
+    w, s, A, B, a_d, a_rgb, o_d, o_rgb = tiny_pair
+    p = O.params(w)
+    mu = perturb(B, np.array([0.004, -0.003, 0.003, 0.005, -0.006, 0.004]))
+    vel = np.array([0.4, -0.2, 0.1, 0.3, -0.1, 0.2])
+    pr, parts = joint_prior(O, mu, vel, seed=5)
+    return O, p, pr, parts, A, a_d, a_rgb, o_d, o_rgb
+
+
+def laplace_by_hand(O, p, parts, A, a_d, a_rgb, o_d, o_rgb, pose, xi, factor=2.0, use_Minv=True):
+    res = O.residuals(p, A, a_d, a_rgb, pose, o_d, o_rgb)
+    kept = res["kept"] > 0
+    b = np.array([p.b_geo, p.b_rgb, p.b_rgb, p.b_rgb])
+    Js = res["J"][kept] / b[None, :, None]
+    Ht = np.einsum("nki,nkj->ij", Js, Js)
+    Mi = np.eye(6)
+    if use_Minv:
+        Mi[3:, 3:] = np.linalg.inv(left_jacobian_fd(xi[3:]))
+    return np.linalg.inv(factor * Ht + Mi.T @ parts["L"] @ Mi), Mi, kept.sum()
+
+
+def test_localise_returns_the_retraction_of_xi(laplace_case):
+    """The returned pose is the prior mean moved by the reported optimum
+    xi*: t = t_mu + xi_t, R = Exp(xi_theta) R_mu (reading R15's coordinates).
+    Catches a retraction on the wrong side (R_mu Exp(xi_theta))."""
+    O, p, pr, parts, A, a_d, a_rgb, o_d, o_rgb = laplace_case
+    prev = O.make_state(A)
+    out, diag = O.localise(p, pr, prev, a_d, a_rgb, o_d, o_rgb)
+    est, mu, xi = O.state_arrays(out)["pose"], O.prior_arrays(pr)["pose"], diag["xi"]
+    np.testing.assert_allclose(est[:3], mu[:3] + xi[:3], rtol=0, atol=1e-14)
+    want = Rotation.from_rotvec(xi[3:]).as_matrix() @ R_of(mu)
+    np.testing.assert_allclose(R_of(est), want, rtol=0, atol=1e-12)
+    wrong = R_of(mu) @ Rotation.from_rotvec(xi[3:]).as_matrix()
+    assert np.abs(wrong - want).max() > 1e-6
+    assert np.linalg.norm(xi[3:]) > 3e-3 and diag["n_pixels"] > 500
+
+
+def test_laplace_covariance_first_frame(laplace_case):
+    """First localisation (no EMA): the pose covariance is
+    (2 sum J^T J / b^2 + M^-T L M^-1)^-1 at the optimum, M = diag(I, J_l(xi*)).
+    Catches: the factor 1 instead of 2 in front of the data term; the prior
+    Hessian left in xi coordinates (no M^-1); the prior dropped."""
+    O, p, pr, parts, A, a_d, a_rgb, o_d, o_rgb = laplace_case
+    prev = O.make_state(A)
+    out, diag = O.localise(p, pr, prev, a_d, a_rgb, o_d, o_rgb)
+    pose = O.state_arrays(out)["pose"]
+    got = O.state_arrays(out)["cov"][:6, :6]
+    want, _, n = laplace_by_hand(O, p, parts, A, a_d, a_rgb, o_d, o_rgb, pose, diag["xi"])
+    assert n == diag["n_pixels"]
+    rel = lambda X: np.abs(X - want).max() / np.abs(want).max()
+    tol = 1e-10
+    assert rel(got) < tol
+    Ht2 = np.linalg.inv(want) - np.linalg.inv(laplace_by_hand(
+        O, p, parts, A, a_d, a_rgb, o_d, o_rgb, pose, diag["xi"], factor=0.0)[0])
+    slips = {
+        "factor 1": laplace_by_hand(O, p, parts, A, a_d, a_rgb, o_d, o_rgb, pose, diag["xi"], factor=1.0)[0],
+        "no M^-1": laplace_by_hand(O, p, parts, A, a_d, a_rgb, o_d, o_rgb, pose, diag["xi"], use_Minv=False)[0],
+        "no prior": np.linalg.inv(Ht2),
+    }
+    for name, X in slips.items():
+        assert rel(X) > 100 * tol, name
+
+
+def test_laplace_ema_on_later_frames(laplace_case):
+    """A later localisation (n_localised > 0) returns 0.8 Sigma_prev +
+    0.2 Sigma_Laplace (App. F.2, EMA coefficient 0.8).  The previous
+    covariance is made 50x the Laplace one, so swapped weights (0.2 / 0.8),
+    a missing EMA, or an EMA on the precision instead of the covariance all
+    miss by far more than rounding."""
+    O, p, pr, parts, A, a_d, a_rgb, o_d, o_rgb = laplace_case
+    first, diag0 = O.localise(p, pr, O.make_state(A), a_d, a_rgb, o_d, o_rgb)
+    lap = O.state_arrays(first)["cov"][:6, :6]
+    prev_cov = np.eye(12) * 1e-4
+    prev_cov[:6, :6] = 50 * lap + np.diag([1e-6] * 3 + [1e-7] * 3)
+    prev = O.make_state(A, cov=prev_cov, n_localised=3)
+    out, diag = O.localise(p, pr, prev, a_d, a_rgb, o_d, o_rgb)
+    np.testing.assert_array_equal(diag["xi"], diag0["xi"])   # the EMA does not move the optimum
+    got = O.state_arrays(out)["cov"][:6, :6]
+    want = 0.8 * prev_cov[:6, :6] + 0.2 * lap
+    rel = lambda X: np.abs(X - want).max() / np.abs(want).max()
+    assert rel(got) < 1e-12
+    assert O.state_arrays(out)["n_localised"] == 4
+    for X in (0.2 * prev_cov[:6, :6] + 0.8 * lap, lap,
+              np.linalg.inv(0.8 * np.linalg.inv(prev_cov[:6, :6]) + 0.2 * np.linalg.inv(lap))):
+        assert rel(X) > 1e-3
+
+
+def test_recombination_of_velocity(laplace_case):
+    """Sec. 3.3.2: with v | p = vbar + D xi(p) and xi = xi* + M^-1 delta at
+    the optimum, the velocity mean is vbar + D xi*, cov(v, p) = D M^-1 Sigma_p
+    and cov(v) = D M^-1 Sigma_p M^-T D^T + Sigma_vel, Sigma_p the returned
+    pose covariance.  Catches D used without M^-1, Sigma_vel dropped, and the
+    cross block transposed."""
+    O, p, pr, parts, A, a_d, a_rgb, o_d, o_rgb = laplace_case
+    out, diag = O.localise(p, pr, O.make_state(A), a_d, a_rgb, o_d, o_rgb)
+    sa = O.state_arrays(out)
+    xi, S = diag["xi"], sa["cov"]
+    Sp = S[:6, :6]
+    Mi = np.eye(6)
+    Mi[3:, 3:] = np.linalg.inv(left_jacobian_fd(xi[3:]))
+    D, Svel = parts["D"], parts["Svel"]
+    np.testing.assert_allclose(sa["vel"], parts["vbar"] + D @ xi, rtol=0, atol=1e-13)
+    cross = D @ Mi @ Sp
+    vv = cross @ Mi.T @ D.T + Svel
+    rel = lambda X, Y: np.abs(X - Y).max() / np.abs(Y).max()
+    tol = 1e-10
+    assert rel(S[6:, :6], cross) < tol and rel(S[:6, 6:], cross.T) < tol
+    assert rel(S[6:, 6:], vv) < tol
+    assert rel(D @ Sp, cross) > 100 * tol                  # M^-1 matters at this xi*
+    assert rel(D @ Sp @ D.T + Svel, vv) > 100 * tol
+    assert rel(cross @ Mi.T @ D.T, vv) > 100 * tol         # Sigma_vel matters
+    assert rel(cross.T, cross) > 100 * tol                 # the block is not symmetric
