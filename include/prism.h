@@ -170,7 +170,13 @@ prism_status prism_predict(prism_handle h, const double* imu, int32_t n, double 
  * prism_predict since the last localisation and an anchor (PRISM_ESTATE).
  * depth: DEVICE pointer, H x W floats; rgb: DEVICE pointer, H x W x 3 floats.
  * out: HOST pointer or NULL; when given, the stream is synchronised and the
- * new state written (this also reports PRISM_ENOTPD found on the device). */
+ * new state written (this also reports PRISM_ENOTPD found on the device).
+ * Divergence guard: when the prior's pose covariance, a Gauss-Newton system
+ * or the Laplace Hessian is not positive definite (or not finite), the
+ * localisation is rejected: the state stays exactly as it was, a following
+ * map update of the same prism_step fuses nothing, and the state read
+ * reports PRISM_ENOTPD.  Each prediction clears the device flags, so a
+ * report covers the latest step only. */
 prism_status prism_localise(prism_handle h, const float* depth, const float* rgb, prism_state* out);
 
 /* Fuse a frame into the map at the current state mean (App. D, Eq.
@@ -190,7 +196,9 @@ prism_status prism_render(prism_handle h, const double* pose7, float* depth, flo
                           uint8_t* mask, int32_t* hitk);
 
 /* One full filter step (R21): predict (skipped on the first step), localise
- * (skipped on the first step), update_map, render of the new anchor.
+ * (skipped on the first step), update_map, render of the new anchor.  A
+ * rejected localisation (see prism_localise) leaves state and map unchanged
+ * and returns PRISM_ENOTPD when out is given.
  * Arguments as for the individual calls; out may be NULL.  With out, the call
  * returns as soon as the posterior is final: the map update and the anchor
  * render may still be running on the stream, and they read depth and rgb, so
@@ -216,8 +224,8 @@ prism_status prism_step(prism_handle h, const double* imu, int32_t n, double dt,
 prism_status prism_step_host(prism_handle h, const double* imu, int32_t n, double dt,
                              const float* depth_host, const float* rgb_host, prism_state* out);
 
-/* Copy the state to HOST memory (synchronises the stream; reports a pending
- * device-side PRISM_ENOTPD). */
+/* Copy the state to HOST memory (synchronises the stream; reports
+ * PRISM_ENOTPD while the latest step's flags are raised). */
 prism_status prism_get_state(prism_handle h, prism_state* out);
 
 /* Replace the state (HOST pointer); the pending prior is discarded. */

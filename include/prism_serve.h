@@ -37,8 +37,9 @@
  *   Calls return a prism_status (prism.h); prism_serve_last_error describes
  *   the last failure.  A CUDA failure in a server thread puts the server in
  *   a failed state: later calls return PRISM_ECUDA.  A step the device flags
- *   (a matrix that is not positive definite) is reported in its result's
- *   status as PRISM_ENOTPD; the stream continues.
+ *   (a matrix that is not positive definite) is rejected as prism_step
+ *   rejects it (the stream's state and map stay unchanged) and reported in
+ *   its result's status as PRISM_ENOTPD; the stream continues.
  */
 #ifndef PRISM_SERVE_H
 #define PRISM_SERVE_H

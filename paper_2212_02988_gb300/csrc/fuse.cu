@@ -20,8 +20,10 @@ __global__ void __launch_bounds__(256) k_fuse(KParams P, MapPlanes M, const floa
 
 // The tiles in the frustum, appended to `list` (ctr[0] counts them; the
 // order is irrelevant: every tile's update is independent of the others).
+// rejected (nullable): a nonzero value lists no tile (the localisation of
+// this step was rejected, so its frame is not fused).
 __global__ void __launch_bounds__(256) k_fuse_cull(KParams P, const float* __restrict__ w2c, int* __restrict__ list,
-                                                   unsigned int* __restrict__ ctr) {
+                                                   unsigned int* __restrict__ ctr, const int* __restrict__ rejected) {
     pdl_enter();
     __shared__ float sM[9], sb[3];
     load_w2c(w2c, sM, sb);
@@ -29,7 +31,7 @@ __global__ void __launch_bounds__(256) k_fuse_cull(KParams P, const float* __res
     const int n = P.nbx * P.nby * P.nbz;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     bool keep = false;
-    if (t < n) keep = !tile_outside_frustum(P, sM, sb, t % P.nbx, (t / P.nbx) % P.nby, t / (P.nbx * P.nby));
+    if (t < n && !(rejected && *rejected)) keep = !tile_outside_frustum(P, sM, sb, t % P.nbx, (t / P.nbx) % P.nby, t / (P.nbx * P.nby));
     const unsigned int ballot = __ballot_sync(0xffffffffu, keep);
     const int lane = threadIdx.x & 31;
     unsigned int base = 0;
@@ -81,9 +83,9 @@ static int fuse_grid() {
 
 cudaError_t launch_fuse_listed(const KParams& P, const MapPlanes& M, const float* w2c, const float* depth,
                                const float* rgb, const uint8_t* mask, DevStats* stats, int* list, unsigned int* ctr,
-                               cudaStream_t s) {
+                               const int* rejected, cudaStream_t s) {
     const int n = P.nbx * P.nby * P.nbz;
-    cudaError_t e = launch_pdl(k_fuse_cull, (n + 255) / 256, 256, s, P, w2c, list, ctr);
+    cudaError_t e = launch_pdl(k_fuse_cull, (n + 255) / 256, 256, s, P, w2c, list, ctr, rejected);
     if (e != cudaSuccess) return e;
     if (P.bf16) return launch_pdl(k_fuse_list<true>, fuse_grid<true>(), 256, s, P, M, w2c, depth, rgb, mask, stats,
                                   (const int*)list, ctr);

@@ -101,10 +101,11 @@ cudaError_t launch_fuse(const KParams& P, const MapPlanes& M, const float* w2c, 
                         const float* rgb, const uint8_t* mask, DevStats* stats, cudaStream_t s);
 // The same update in two launches: the frustum test of every tile appends
 // the tiles in view to `list` (ntiles ints), then a persistent grid updates
-// only those; ctr (2 uints, zero between calls) counts them.
+// only those; ctr (2 uints, zero between calls) counts them.  rejected
+// (device int, nullable; DevState::rejected): nonzero lists no tile.
 cudaError_t launch_fuse_listed(const KParams& P, const MapPlanes& M, const float* w2c, const float* depth,
                                const float* rgb, const uint8_t* mask, DevStats* stats, int* list, unsigned int* ctr,
-                               cudaStream_t s);
+                               const int* rejected, cudaStream_t s);
 
 // mapio.cu — fill with the prior, and conversion between the caller's dense
 // layout and the padded (ghost-bordered) device layout.

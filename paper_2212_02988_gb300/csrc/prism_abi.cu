@@ -327,14 +327,15 @@ cudaError_t dalloc(prism_handle h, T** p, size_t bytes) {
     return e;
 }
 
-// Reports (and clears on the device) the flags of a state copy just read.
+// Reports the flags of a state copy just read (each prediction clears them
+// on the device, so they are those of the latest step until the next one).
 prism_status check_flags(prism_handle h, int flags) {
     if (flags) {
-        CK(h, cudaMemsetAsync(&h->dstate->flags, 0, sizeof(int), h->stream), "clear flags");
         std::string m = "device reported:";
         if (flags & FLAG_GN_NOTPD) m += " Gauss-Newton system not positive definite;";
-        if (flags & FLAG_LAPLACE_NOTPD) m += " Laplace Hessian not positive definite (state unchanged);";
+        if (flags & FLAG_LAPLACE_NOTPD) m += " Laplace Hessian not positive definite;";
         if (flags & FLAG_PRIOR_NOTPD) m += " prior pose covariance not positive definite;";
+        m += " the step was rejected (state and map unchanged)";
         return fail(h, PRISM_ENOTPD, m);
     }
     return PRISM_OK;
@@ -469,8 +470,9 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb, b
 prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool mask_ready) {
     PhaseTimer t(h, PH_FUSE);
     if (!mask_ready) LAUNCH(h, launch_depth_mask(h->kp, depth, h->o_mask, h->stream), "observation mask");
+    // after a localisation in the same step (mask_ready), a rejected step fuses nothing
     LAUNCH(h, launch_fuse_listed(h->kp, h->map, h->dstate->w2c, depth, rgb, h->o_mask, h->dstats, h->fuse_list,
-                                 h->fuse_ctr, h->stream),
+                                 h->fuse_ctr, mask_ready ? &h->dstate->rejected : nullptr, h->stream),
            "fuse");
     ++h->launches;   // (two kernels: the frustum list and the update)
     if (h->kp.skip) LAUNCH(h, launch_brick_bounds(h->kp, h->map, h->stream), "brick bounds");

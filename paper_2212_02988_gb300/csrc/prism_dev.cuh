@@ -97,7 +97,10 @@ struct DevState {
     float aux[12];             // a pose given by the host (render or one objective evaluation)
     int n_localised;
     int flags;                 // bit 0: GN system not PD; bit 1: Laplace system not PD; bit 2: prior not PD
-    int pad[2];
+                               // (cleared by each prediction, set by the kernels of that step)
+    int rejected;              // the last localisation raised a flag: the posterior was left as it was and
+                               // the step's map update lists no tile (0 after creation or a state write)
+    int pad1;
 };
 
 enum : int { FLAG_GN_NOTPD = 1, FLAG_LAPLACE_NOTPD = 2, FLAG_PRIOR_NOTPD = 4 };

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(256, 4) kb_fuse(const SlotDesc* __restrict__ s
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int i = find_member(b->fuse_off, b->n, item);
         const SlotDesc& S = slots[b->m[i].slot];
+        if (S.dev->rejected) continue;   // the member's localisation was rejected: its frame is not fused
         load_w2c(S.dev->w2c, sM, sb);
         __syncthreads();
         fuse_tile<BF16>(S.P, S.M, sM, sb, S.depth, S.rgb, S.o_mask, S.stats, (uint32_t)(item - b->fuse_off[i]));

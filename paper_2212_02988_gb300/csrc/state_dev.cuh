@@ -32,6 +32,7 @@ __device__ __forceinline__ void predict_block(const KParams& P, DevState* dev, c
     __shared__ double sums[8];   // mean t, acc (3), gyro (3), then t_end
     __shared__ double fit[4];    // sum dt^2, sum dt * dgyro (3)
     const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) dev->flags = 0;   // a new step: only its own kernels raise flags
     // the previous covariance, staged once (the products below read it in
     // dependent chains)
     for (int e = tid; e < 144; e += blockDim.x) Cv[e] = dev->cov[e];

@@ -295,7 +295,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     __shared__ double sx[8][36];
     __shared__ int s_last, s_ok;
     __shared__ double st[kStage];
-    __shared__ int s_nloc;
+    __shared__ int s_nloc, s_flags;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // Every block starts copying the state the last block's finish will need
     // (written by earlier kernels), so that it is in shared memory when the
@@ -304,6 +304,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         const double* src = stage_src<MODE>(dev, tid);
         if (src) cp_async(&st[tid], src, 8);
         else if (MODE == TRACK_LAPLACE && tid == 170) cp_async(&s_nloc, &dev->n_localised, 4);
+        else if (MODE == TRACK_LAPLACE && tid == 171) cp_async(&s_flags, &dev->flags, 4);
     }
     if (tid < 12) {
         const float* mats = MODE == TRACK_EXPORT ? dev->aux : dev->rel;
@@ -575,7 +576,19 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         return;
     }
 
-    // MODE == TRACK_LAPLACE: Sigma = (2 Ht + Mi^T L Mi)^-1, Mi = diag(I, J_l(xi_theta)^-1)
+    // MODE == TRACK_LAPLACE.  Divergence guard: a flag raised by this step's
+    // prediction (prior not positive definite) or by a Gauss-Newton pass
+    // rejects the step; the posterior stays as it was and the map update
+    // that follows lists no tile.
+    if (s_flags != 0) {
+        if (tid == 0) {
+            dev->rejected = 1;
+            dev->ne_out[78] = S[L::oCost];
+            dev->ne_out[79] = S[L::oCount];
+        }
+        return;
+    }
+    // Sigma = (2 Ht + Mi^T L Mi)^-1, Mi = diag(I, J_l(xi_theta)^-1)
     double* Mi = sx[0];
     double* T1 = sx[1];
     double* Hl = sx[2];
@@ -611,6 +624,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (!spd_inverse_block<6>(Hl, Sl, Lf, rdg, &s_ok)) {
         if (tid == 0) {
             dev->flags |= FLAG_LAPLACE_NOTPD;
+            dev->rejected = 1;
             dev->ne_out[78] = S[L::oCost];
             dev->ne_out[79] = S[L::oCount];
         }
@@ -668,6 +682,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         if (lane < 4) dev->q[lane] = pose[3 + lane];
         if (lane == 0) {
             dev->n_localised += 1;
+            dev->rejected = 0;
             dev->ne_out[78] = S[L::oCost];
             dev->ne_out[79] = S[L::oCount];
         }
