@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "prism_oracle.h"))):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -97,6 +97,8 @@ def lib():
             L.or_sample_pixel.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32]
             L.or_sample_pixel.restype = C.c_uint32
             L.or_adam.argtypes = [P(Params), P(Prior), dp, fp, fp, fp, fp, C.c_uint64, dp, dp]
+            L.or_set_threads.argtypes = [C.c_int32]
+            L.or_get_threads.restype = C.c_int32
             _lib = L
     return _lib
 
@@ -155,6 +157,16 @@ def _f64(a):
 
 
 # ------------------------------------------------------------------ wrappers
+def set_threads(n: int) -> None:
+    """Worker threads of the oracle's loops (n <= 0: every online processor,
+    the default).  Results are bit-identical for any thread count."""
+    lib().or_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().or_get_threads())
+
+
 def render(p: Params, occ, rgb, pose7, pix=None):
     """Render at pose7 = (t, q).  Returns dict of depth, rgb, mask, hitk,
     n_samples; per pixel of `pix` (flat indices) if given, else (H, W)."""

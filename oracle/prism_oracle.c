@@ -3,7 +3,7 @@
  * TEST INFRASTRUCTURE ONLY: the tests, the package's smoke check and the
  * benchmark's CPU-baseline leg load this library; the product path never
  * does.  It shares no code with the CUDA library.  Build with
- *     gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so prism_oracle.c -lm
+ *     gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -pthread -o liboracle.so prism_oracle.c -lm
  * (-ffp-contract=off: every a*b+c below is two rounded operations unless it
  * is written as fma/fmaf).
  *
@@ -32,12 +32,87 @@
  *
  * Integer decisions use the FP32 recipe written out at each site (the device
  * kernels follow the same recipe); all values are FP64.
+ *
+ * The loops over rays (or_render), pixels (or_residuals, or_normal_equations)
+ * and voxels (or_fuse) run on POSIX threads; each result is bit-identical for
+ * any thread count (see parallel_for).  Build with -pthread.
  */
+#define _POSIX_C_SOURCE 200809L
 #include "prism_oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------ threads */
+/* Work that is independent per item (a ray, a pixel, a row of voxels) is
+ * split into ranges that worker threads take in turn.  Every item writes
+ * only its own outputs; integer counts are added per worker (exact in any
+ * order);
+ * floating-point sums over items are formed per fixed chunk of items and the
+ * chunk sums added in chunk order, neither depending on the thread count.
+ * So every result is bit-identical for any number of threads. */
+static int g_threads = 0;   /* 0: every online processor */
+
+void or_set_threads(int32_t n) { g_threads = n > 0 ? n : 0; }
+
+int32_t or_get_threads(void) {
+    if (g_threads > 0) return g_threads;
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n > 0 ? (int32_t)n : 1;
+}
+
+typedef void (*range_fn)(void* ctx, long begin, long end, int job);
+typedef struct {
+    range_fn fn;
+    void* ctx;
+    long n, grain;
+    long* next;   /* shared: the first item not yet taken */
+    int job;
+} range_job;
+
+/* A worker takes ranges of `grain` items in turn until none is left. */
+static void* run_ranges(void* arg) {
+    range_job* j = (range_job*)arg;
+    for (;;) {
+        long b = __atomic_fetch_add(j->next, j->grain, __ATOMIC_RELAXED);
+        if (b >= j->n) break;
+        j->fn(j->ctx, b, b + j->grain < j->n ? b + j->grain : j->n, j->job);
+    }
+    return NULL;
+}
+
+#define OR_MAX_THREADS 256
+
+/* fn(ctx, begin, end, job) over [0, n) in ranges of `grain` items, taken by
+ * at most or_get_threads() workers; returns the number of workers (job ids
+ * 0 .. workers - 1; a worker may receive several ranges). */
+static int parallel_for(long n, long grain, range_fn fn, void* ctx) {
+    if (grain < 1) grain = 1;
+    long ranges = (n + grain - 1) / grain;
+    int T = or_get_threads();
+    if (T > OR_MAX_THREADS) T = OR_MAX_THREADS;
+    if ((long)T > ranges) T = ranges > 0 ? (int)ranges : 1;
+    long next = 0;
+    range_job jobs[OR_MAX_THREADS];
+    pthread_t th[OR_MAX_THREADS];
+    int started[OR_MAX_THREADS];
+    for (int t = 0; t < T; ++t) {
+        jobs[t].fn = fn;
+        jobs[t].ctx = ctx;
+        jobs[t].n = n;
+        jobs[t].grain = grain;
+        jobs[t].next = &next;
+        jobs[t].job = t;
+        started[t] = t > 0 && pthread_create(&th[t], NULL, run_ranges, &jobs[t]) == 0;
+    }
+    run_ranges(&jobs[0]);   /* the caller works too; a worker that failed to start leaves its share to the others */
+    for (int t = 1; t < T; ++t)
+        if (started[t]) pthread_join(th[t], NULL);
+    return T;
+}
 
 /* ------------------------------------------------------------ small linear algebra */
 static void mat3_mul(const double A[9], const double B[9], double C[9]) {
@@ -294,42 +369,48 @@ static double trilinear64(const or_params* P, const double* m, int stride, int c
     return s;
 }
 
-int or_render(const or_params* P, const double* occ, const double* rgb, const double pose_in[7],
-              const int32_t* pix, int32_t npix, double* depth, double* rgb_out, uint8_t* mask,
-              int32_t* hitk, int64_t* n_samples) {
-    double R[9], pose[7];
-    normalise_pose(pose_in, pose);
-    quat_to_R(pose + 3, R);
-    /* FP32 ray set-up (decision recipe) */
+typedef struct {
+    const or_params* P;
+    const double *occ, *rgb;
+    const int32_t* pix;
+    double* depth;
+    double* rgb_out;
+    uint8_t* mask;
+    int32_t* hitk;
+    double pose[7];
     float R32[9], c32[3], o32[3];
-    for (int i = 0; i < 9; ++i) R32[i] = (float)R[i];
-    for (int a = 0; a < 3; ++a) { c32[a] = (float)pose[a]; o32[a] = (float)P->origin[a]; }
+    long kmax;
+    int64_t nsamp[OR_MAX_THREADS];
+} render_ctx;
+
+/* Rays n in [begin, end). */
+static void render_rays(void* arg, long begin, long end, int job) {
+    render_ctx* X = (render_ctx*)arg;
+    const or_params* P = X->P;
     float inv_vs = (float)(1.0 / P->voxel), eps32 = (float)P->eps, tau32 = (float)P->tau;
     float cx = (float)P->cx, cy = (float)P->cy;
     float ifx = (float)(1.0 / P->fx), ify = (float)(1.0 / P->fy);
-    long kmax = P->max_depth > 0 ? (long)floor(P->max_depth / P->eps) : 0x7fffffffL;
-    int total = npix > 0 && pix ? npix : P->width * P->height;
     int64_t nsamp = 0;
-    for (int n = 0; n < total; ++n) {
-        int p = pix ? pix[n] : n;
+    for (long n = begin; n < end; ++n) {
+        int p = X->pix ? X->pix[n] : (int)n;
         int u = p % P->width, v = p / P->width;
         /* ray direction r = R dir_c / |R dir_c|, dir_c = ((u-cx)/fx, (v-cy)/fy, 1) */
         float dx = ((float)u - cx) * ifx, dy = ((float)v - cy) * ify;
         float w[3], r[3], cg[3], rg[3];
-        for (int a = 0; a < 3; ++a) w[a] = fmaf(R32[3 * a], dx, fmaf(R32[3 * a + 1], dy, R32[3 * a + 2]));
+        for (int a = 0; a < 3; ++a) w[a] = fmaf(X->R32[3 * a], dx, fmaf(X->R32[3 * a + 1], dy, X->R32[3 * a + 2]));
         float inv_n = 1.0f / sqrtf(fmaf(w[0], w[0], fmaf(w[1], w[1], w[2] * w[2])));
         for (int a = 0; a < 3; ++a) {
             r[a] = w[a] * inv_n;
-            cg[a] = fmaf(c32[a] - o32[a], inv_vs, -0.5f);
+            cg[a] = fmaf(X->c32[a] - X->o32[a], inv_vs, -0.5f);
             rg[a] = r[a] * inv_vs;
         }
         /* march: first k with f_occ(p_k) > tau */
         cell_t prev, cur;
         int k = 1, hit = 0;
-        for (; k <= kmax; ++k) {
+        for (; k <= X->kmax; ++k) {
             if (!sample_cell(P, cg, rg, eps32, k, &cur)) break;
             ++nsamp;
-            if (trilinear32(P, occ, 1, 0, &cur) > tau32) { hit = 1; break; }
+            if (trilinear32(P, X->occ, 1, 0, &cur) > tau32) { hit = 1; break; }
             prev = cur;
         }
         double d_out = 0.0, col[3] = {0, 0, 0};
@@ -337,7 +418,7 @@ int or_render(const or_params* P, const double* occ, const double* rgb, const do
         if (hit && k == 1) hk = -1;          /* camera inside matter: no valid depth */
         if (hit && k >= 2) {
             hk = k;
-            double f0 = trilinear64(P, occ, 1, 0, &prev), f1 = trilinear64(P, occ, 1, 0, &cur);
+            double f0 = trilinear64(P, X->occ, 1, 0, &prev), f1 = trilinear64(P, X->occ, 1, 0, &cur);
             double alpha = (P->tau - f0) / (f1 - f0);
             double dk = k * P->eps, dk1 = (k - 1) * P->eps;
             double dstar = alpha * dk + (1.0 - alpha) * dk1;
@@ -345,15 +426,37 @@ int or_render(const or_params* P, const double* occ, const double* rgb, const do
             double dcx = (u - P->cx) / P->fx, dcy = (v - P->cy) / P->fy;
             d_out = dstar / sqrt(dcx * dcx + dcy * dcy + 1.0);
             for (int ch = 0; ch < 3; ++ch)
-                col[ch] = alpha * trilinear64(P, rgb, 3, ch, &cur) +
-                          (1.0 - alpha) * trilinear64(P, rgb, 3, ch, &prev);
+                col[ch] = alpha * trilinear64(P, X->rgb, 3, ch, &cur) +
+                          (1.0 - alpha) * trilinear64(P, X->rgb, 3, ch, &prev);
         }
-        if (depth) depth[n] = d_out;
-        if (rgb_out) for (int ch = 0; ch < 3; ++ch) rgb_out[3 * n + ch] = col[ch];
-        if (mask) mask[n] = (uint8_t)(hk >= 2);
-        if (hitk) hitk[n] = hk;
+        if (X->depth) X->depth[n] = d_out;
+        if (X->rgb_out) for (int ch = 0; ch < 3; ++ch) X->rgb_out[3 * n + ch] = col[ch];
+        if (X->mask) X->mask[n] = (uint8_t)(hk >= 2);
+        if (X->hitk) X->hitk[n] = hk;
     }
+    X->nsamp[job] += nsamp;
+}
+
+int or_render(const or_params* P, const double* occ, const double* rgb, const double pose_in[7],
+              const int32_t* pix, int32_t npix, double* depth, double* rgb_out, uint8_t* mask,
+              int32_t* hitk, int64_t* n_samples) {
+    render_ctx* X = (render_ctx*)calloc(1, sizeof(render_ctx));
+    if (!X) return -2;
+    double R[9];
+    normalise_pose(pose_in, X->pose);
+    quat_to_R(X->pose + 3, R);
+    /* FP32 ray set-up (decision recipe) */
+    for (int i = 0; i < 9; ++i) X->R32[i] = (float)R[i];
+    for (int a = 0; a < 3; ++a) { X->c32[a] = (float)X->pose[a]; X->o32[a] = (float)P->origin[a]; }
+    X->kmax = P->max_depth > 0 ? (long)floor(P->max_depth / P->eps) : 0x7fffffffL;
+    X->P = P; X->occ = occ; X->rgb = rgb; X->pix = npix > 0 && pix ? pix : NULL;
+    X->depth = depth; X->rgb_out = rgb_out; X->mask = mask; X->hitk = hitk;
+    long total = npix > 0 && pix ? npix : (long)P->width * P->height;
+    int jobs = parallel_for(total, 64, render_rays, X);
+    int64_t nsamp = 0;
+    for (int j = 0; j < jobs; ++j) nsamp += X->nsamp[j];
     if (n_samples) *n_samples = nsamp;
+    free(X);
     return 0;
 }
 
@@ -483,10 +586,20 @@ int or_render_backward(const or_params* P, const double* occ, const double* rgb,
 /* ============================================================ depth validity */
 /* Pixel valid iff D > 0, finite, and every in-image 4-neighbour Dn satisfies
  * fabsf(D - Dn) <= disc in FP32 (App. F.3: invalid or discontinuous depth). */
-void or_depth_mask(const or_params* P, const float* depth, uint8_t* mask) {
-    int W = P->width, H = P->height;
-    float disc = (float)P->disc;
-    for (int v = 0; v < H; ++v)
+typedef struct {
+    const or_params* P;
+    const float* depth;
+    uint8_t* mask;
+} mask_ctx;
+
+/* Rows v in [begin, end). */
+static void mask_rows(void* arg, long begin, long end, int job) {
+    (void)job;
+    mask_ctx* X = (mask_ctx*)arg;
+    int W = X->P->width, H = X->P->height;
+    const float* depth = X->depth;
+    float disc = (float)X->P->disc;
+    for (int v = (int)begin; v < (int)end; ++v)
         for (int u = 0; u < W; ++u) {
             float d = depth[v * W + u];
             int ok = (d > 0.0f) && isfinite(d);
@@ -495,8 +608,13 @@ void or_depth_mask(const or_params* P, const float* depth, uint8_t* mask) {
                 if (nu[e] < 0 || nu[e] >= W || nv[e] < 0 || nv[e] >= H) continue;
                 if (!(fabsf(d - depth[nv[e] * W + nu[e]]) <= disc)) ok = 0;
             }
-            mask[v * W + u] = (uint8_t)ok;
+            X->mask[v * W + u] = (uint8_t)ok;
         }
+}
+
+void or_depth_mask(const or_params* P, const float* depth, uint8_t* mask) {
+    mask_ctx X = {P, depth, mask};
+    parallel_for(P->height, 8, mask_rows, &X);
 }
 
 /* ============================================================ anchor normals */
@@ -504,10 +622,27 @@ void or_depth_mask(const or_params* P, const float* depth, uint8_t* mask) {
  * the camera; valid iff the pixel and its 4 neighbours are valid and it is
  * not on the image border.  FP32 recipe for n32 (used for decisions) and the
  * same construction in FP64 for n64 (used for values). */
-void or_anchor_normals(const or_params* P, const float* depth, const uint8_t* mask,
-                       double* n64, float* n32, uint8_t* nvalid) {
+typedef struct {
+    const or_params* P;
+    const float* depth;
+    const uint8_t* mask;
+    double* n64;
+    float* n32;
+    uint8_t* nvalid;
+} normals_ctx;
+
+/* Rows v in [begin, end). */
+static void normal_rows(void* arg, long begin, long end, int job) {
+    (void)job;
+    normals_ctx* X = (normals_ctx*)arg;
+    const or_params* P = X->P;
+    const float* depth = X->depth;
+    const uint8_t* mask = X->mask;
+    double* n64 = X->n64;
+    float* n32 = X->n32;
+    uint8_t* nvalid = X->nvalid;
     int W = P->width, H = P->height;
-    for (int v = 0; v < H; ++v)
+    for (int v = (int)begin; v < (int)end; ++v)
         for (int u = 0; u < W; ++u) {
             int p = v * W + u;
             int ok = u >= 1 && u <= W - 2 && v >= 1 && v <= H - 2 && mask[p] && mask[p - 1] &&
@@ -561,85 +696,69 @@ void or_anchor_normals(const or_params* P, const float* depth, const uint8_t* ma
         }
 }
 
-/* ===================================================== residuals + normal equations */
-/* Residuals of the objective of App. E.3 (Eq. pointtoplanelaplace) for every
- * observed pixel at camera pose `pose`, against the anchor observation
- * rendered at `anchor_pose`:
- *   r[4p]     = <p_hat - X, n_hat>            (point-to-plane, anchor frame)
- *   r[4p+1+c] = I_hat_c(pi(X)) - I_c(p)       (photometric, bilinear in the anchor)
- * X is the observed point moved into the anchor camera; p_hat, n_hat come
- * from the nearest anchor pixel.  J[24p + 6k + i] is d r_k / d xi_i for a
- * world-frame perturbation of the camera pose, t' = t + dt, R' = Exp(dtheta) R,
- * xi = (dt, dtheta).  kept[p] = 1 iff the pixel passed every validity check
- * and both gates (App. F.2); assoc[2p] = nearest anchor pixel, assoc[2p+1] =
- * the bilinear cell's top-left pixel (-1 when not associated). */
-int or_residuals(const or_params* P, const double anchor_in[7], const float* a_depth,
-                 const float* a_rgb, const double pose_in[7], const float* o_depth, const float* o_rgb,
-                 double* r, double* J, int32_t* assoc, uint8_t* kept) {
-    double anchor_pose[7], pose[7];
-    normalise_pose(anchor_in, anchor_pose);
-    normalise_pose(pose_in, pose);
-    int W = P->width, H_ = P->height, N = W * H_;
-    uint8_t* a_mask = (uint8_t*)malloc(N);
-    uint8_t* o_mask = (uint8_t*)malloc(N);
-    uint8_t* a_nval = (uint8_t*)malloc(N);
-    float* a_n32 = (float*)malloc(sizeof(float) * 3 * N);
-    double* a_n64 = (double*)malloc(sizeof(double) * 3 * N);
-    if (!a_mask || !o_mask || !a_nval || !a_n32 || !a_n64) {
-        free(a_mask); free(o_mask); free(a_nval); free(a_n32); free(a_n64);
-        return -2;
-    }
-    or_depth_mask(P, a_depth, a_mask);
-    or_depth_mask(P, o_depth, o_mask);
-    or_anchor_normals(P, a_depth, a_mask, a_n64, a_n32, a_nval);
+void or_anchor_normals(const or_params* P, const float* depth, const uint8_t* mask,
+                       double* n64, float* n32, uint8_t* nvalid) {
+    normals_ctx X = {P, depth, mask, n64, n32, nvalid};
+    parallel_for(P->height, 8, normal_rows, &X);
+}
 
-    double R[9], Ra[9], Mrel[9], d[3], brel[3];
-    quat_to_R(pose + 3, R);
-    quat_to_R(anchor_pose + 3, Ra);
-    /* FP64 recipe of the relative transform current-camera -> anchor-camera,
-     * rounded once to FP32 for the decisions:
-     * Mrel = Ra^T R (sum order k = 0, 1, 2), brel = Ra^T (t - ta). */
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            Mrel[3 * i + j] = (Ra[i] * R[j] + Ra[3 + i] * R[3 + j]) + Ra[6 + i] * R[6 + j];
-    for (int a = 0; a < 3; ++a) d[a] = pose[a] - anchor_pose[a];
-    for (int i = 0; i < 3; ++i) brel[i] = (Ra[i] * d[0] + Ra[3 + i] * d[1]) + Ra[6 + i] * d[2];
+/* ===================================================== residuals + normal equations */
+typedef struct {
+    const or_params* P;
+    const float *a_depth, *a_rgb, *o_depth, *o_rgb;
+    const uint8_t *a_mask, *o_mask, *a_nval;
+    const float* a_n32;
+    const double* a_n64;
+    double pose[7], anchor_pose[7], R[9], Ra[9];
     float M32[9], b32[3];
-    for (int i = 0; i < 9; ++i) M32[i] = (float)Mrel[i];
-    for (int i = 0; i < 3; ++i) b32[i] = (float)brel[i];
+    double* r;
+    double* J;
+    int32_t* assoc;
+    uint8_t* kept;
+} resid_ctx;
+
+/* Pixels p in [begin, end). */
+static void residual_pixels(void* arg, long begin, long end, int job) {
+    (void)job;
+    resid_ctx* X = (resid_ctx*)arg;
+    const or_params* P = X->P;
+    const int W = P->width, H_ = P->height;
+    const float *a_depth = X->a_depth, *a_rgb = X->a_rgb, *o_depth = X->o_depth, *o_rgb = X->o_rgb;
+    const double *R = X->R, *Ra = X->Ra, *pose = X->pose, *anchor_pose = X->anchor_pose;
+    double *r = X->r, *J = X->J;
     float fx32 = (float)P->fx, fy32 = (float)P->fy, cx32 = (float)P->cx, cy32 = (float)P->cy;
     float gate_geo = (float)P->gate_geo, gate_rgb = (float)P->gate_rgb;
-
-    for (int v = 0; v < H_; ++v)
-        for (int u = 0; u < W; ++u) {
-            int p = v * W + u;
-            kept[p] = 0;
-            assoc[2 * p] = assoc[2 * p + 1] = -1;
+    for (long pl = begin; pl < end; ++pl) {
+            const int p = (int)pl, u = p % W, v = p / W;
+            X->kept[p] = 0;
+            X->assoc[2 * p] = X->assoc[2 * p + 1] = -1;
             for (int k = 0; k < 4; ++k) r[4 * p + k] = 0.0;
             for (int k = 0; k < 24; ++k) J[24 * p + k] = 0.0;
-            if (!o_mask[p]) continue;
+            if (!X->o_mask[p]) continue;
             /* ---- decisions, FP32 recipe ---- */
             float z = o_depth[p], P32[3], X32[3];
             backproject32(P, u, v, z, P32);
-            affine32(M32, b32, P32, X32);
+            affine32(X->M32, X->b32, P32, X32);
             if (!(X32[2] > 0.0f)) continue;
             float iz = 1.0f / X32[2];
             float up = fmaf(fx32 * X32[0], iz, cx32), vp = fmaf(fy32 * X32[1], iz, cy32);
             float nu = floorf(up + 0.5f), nv = floorf(vp + 0.5f);
             if (!(nu >= 0.0f && nu <= (float)(W - 1) && nv >= 0.0f && nv <= (float)(H_ - 1))) continue;
             int iu = (int)nu, iv = (int)nv, q = iv * W + iu;
-            if (!a_nval[q]) continue;
+            if (!X->a_nval[q]) continue;
             float bu = floorf(up), bv = floorf(vp);
             if (!(bu >= 0.0f && bu <= (float)(W - 2) && bv >= 0.0f && bv <= (float)(H_ - 2))) continue;
             int ju = (int)bu, jv = (int)bv, b00 = jv * W + ju;
-            if (!(a_mask[b00] && a_mask[b00 + 1] && a_mask[b00 + W] && a_mask[b00 + W + 1])) continue;
-            assoc[2 * p] = q;
-            assoc[2 * p + 1] = b00;
+            const uint8_t* am = X->a_mask;
+            if (!(am[b00] && am[b00 + 1] && am[b00 + W] && am[b00 + W + 1])) continue;
+            X->assoc[2 * p] = q;
+            X->assoc[2 * p + 1] = b00;
             float a32 = up - bu, c32 = vp - bv;
             float ph[3], e[3];
+            const float* n32 = X->a_n32;
             backproject32(P, iu, iv, a_depth[q], ph);
             for (int i = 0; i < 3; ++i) e[i] = ph[i] - X32[i];
-            float rg32 = fmaf(a_n32[3 * q], e[0], fmaf(a_n32[3 * q + 1], e[1], a_n32[3 * q + 2] * e[2]));
+            float rg32 = fmaf(n32[3 * q], e[0], fmaf(n32[3 * q + 1], e[1], n32[3 * q + 2] * e[2]));
             if (!(fabsf(rg32) <= gate_geo)) continue;
             int gated = 0;
             for (int ch = 0; ch < 3 && !gated; ++ch) {
@@ -649,7 +768,7 @@ int or_residuals(const or_params* P, const double anchor_in[7], const float* a_d
                 if (!(fabsf(r32) <= gate_rgb)) gated = 1;
             }
             if (gated) continue;
-            kept[p] = 1;
+            X->kept[p] = 1;
             /* ---- values, FP64 ---- */
             double Pc[3] = {z * (u - P->cx) / P->fx, z * (v - P->cy) / P->fy, (double)z};
             double y[3], rel[3], Xa[3];
@@ -658,7 +777,7 @@ int or_residuals(const or_params* P, const double anchor_in[7], const float* a_d
             mat3_tvec(Ra, rel, Xa);                              /* point in the anchor frame */
             double za = a_depth[q];
             double ph64[3] = {za * (iu - P->cx) / P->fx, za * (iv - P->cy) / P->fy, za};
-            const double* nq = a_n64 + 3 * q;
+            const double* nq = X->a_n64 + 3 * q;
             double aX[4][3];
             r[4 * p] = nq[0] * (ph64[0] - Xa[0]) + nq[1] * (ph64[1] - Xa[1]) + nq[2] * (ph64[2] - Xa[2]);
             for (int i = 0; i < 3; ++i) aX[0][i] = -nq[i];
@@ -683,52 +802,139 @@ int or_residuals(const or_params* P, const double anchor_in[7], const float* a_d
                 Jk[0] = aw[0]; Jk[1] = aw[1]; Jk[2] = aw[2];
                 cross3(y, aw, Jk + 3);                           /* d r / d dtheta = y x aw */
             }
-        }
+    }
+}
+
+/* Residuals of the objective of App. E.3 (Eq. pointtoplanelaplace) for every
+ * observed pixel at camera pose `pose`, against the anchor observation
+ * rendered at `anchor_pose`:
+ *   r[4p]     = <p_hat - X, n_hat>            (point-to-plane, anchor frame)
+ *   r[4p+1+c] = I_hat_c(pi(X)) - I_c(p)       (photometric, bilinear in the anchor)
+ * X is the observed point moved into the anchor camera; p_hat, n_hat come
+ * from the nearest anchor pixel.  J[24p + 6k + i] is d r_k / d xi_i for a
+ * world-frame perturbation of the camera pose, t' = t + dt, R' = Exp(dtheta) R,
+ * xi = (dt, dtheta).  kept[p] = 1 iff the pixel passed every validity check
+ * and both gates (App. F.2); assoc[2p] = nearest anchor pixel, assoc[2p+1] =
+ * the bilinear cell's top-left pixel (-1 when not associated). */
+int or_residuals(const or_params* P, const double anchor_in[7], const float* a_depth,
+                 const float* a_rgb, const double pose_in[7], const float* o_depth, const float* o_rgb,
+                 double* r, double* J, int32_t* assoc, uint8_t* kept) {
+    resid_ctx X;
+    memset(&X, 0, sizeof(X));
+    normalise_pose(anchor_in, X.anchor_pose);
+    normalise_pose(pose_in, X.pose);
+    int W = P->width, H_ = P->height, N = W * H_;
+    uint8_t* a_mask = (uint8_t*)malloc(N);
+    uint8_t* o_mask = (uint8_t*)malloc(N);
+    uint8_t* a_nval = (uint8_t*)malloc(N);
+    float* a_n32 = (float*)malloc(sizeof(float) * 3 * N);
+    double* a_n64 = (double*)malloc(sizeof(double) * 3 * N);
+    if (!a_mask || !o_mask || !a_nval || !a_n32 || !a_n64) {
+        free(a_mask); free(o_mask); free(a_nval); free(a_n32); free(a_n64);
+        return -2;
+    }
+    or_depth_mask(P, a_depth, a_mask);
+    or_depth_mask(P, o_depth, o_mask);
+    or_anchor_normals(P, a_depth, a_mask, a_n64, a_n32, a_nval);
+
+    double Mrel[9], d[3], brel[3];
+    const double *pose = X.pose, *anchor_pose = X.anchor_pose;
+    double *R = X.R, *Ra = X.Ra;
+    quat_to_R(pose + 3, R);
+    quat_to_R(anchor_pose + 3, Ra);
+    /* FP64 recipe of the relative transform current-camera -> anchor-camera,
+     * rounded once to FP32 for the decisions:
+     * Mrel = Ra^T R (sum order k = 0, 1, 2), brel = Ra^T (t - ta). */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            Mrel[3 * i + j] = (Ra[i] * R[j] + Ra[3 + i] * R[3 + j]) + Ra[6 + i] * R[6 + j];
+    for (int a = 0; a < 3; ++a) d[a] = pose[a] - anchor_pose[a];
+    for (int i = 0; i < 3; ++i) brel[i] = (Ra[i] * d[0] + Ra[3 + i] * d[1]) + Ra[6 + i] * d[2];
+    for (int i = 0; i < 9; ++i) X.M32[i] = (float)Mrel[i];
+    for (int i = 0; i < 3; ++i) X.b32[i] = (float)brel[i];
+    X.P = P;
+    X.a_depth = a_depth; X.a_rgb = a_rgb; X.o_depth = o_depth; X.o_rgb = o_rgb;
+    X.a_mask = a_mask; X.o_mask = o_mask; X.a_nval = a_nval; X.a_n32 = a_n32; X.a_n64 = a_n64;
+    X.r = r; X.J = J; X.assoc = assoc; X.kept = kept;
+    parallel_for(N, 1024, residual_pixels, &X);
     free(a_mask); free(o_mask); free(a_nval); free(a_n32); free(a_n64);
     return 0;
+}
+
+/* Sums over the kept residuals of one chunk of pixels [begin, end), in
+ * pixel order: H (36), g (6), Ht (36), cost, count. */
+#define OR_NE_CHUNK 1024
+#define OR_NE_VALUES 80
+typedef struct {
+    const or_params* P;
+    const double *r, *J;
+    const uint8_t* kept;
+    long npix;
+    double* chunk_sums;   /* OR_NE_VALUES per chunk */
+} ne_ctx;
+
+static void ne_chunks(void* arg, long begin, long end, int job) {
+    (void)job;
+    ne_ctx* X = (ne_ctx*)arg;
+    const or_params* P = X->P;
+    for (long c = begin; c < end; ++c) {
+        double* S = X->chunk_sums + OR_NE_VALUES * c;
+        double *H = S, *g = S + 36, *Ht = S + 42;
+        memset(S, 0, sizeof(double) * OR_NE_VALUES);
+        long p_end = (c + 1) * OR_NE_CHUNK < X->npix ? (c + 1) * OR_NE_CHUNK : X->npix;
+        for (long p = c * OR_NE_CHUNK; p < p_end; ++p) {
+            if (!X->kept[p]) continue;
+            for (int k = 0; k < 4; ++k) {
+                double b = k == 0 ? P->b_geo : P->b_rgb, fl = k == 0 ? P->floor_geo : P->floor_rgb;
+                double res = X->r[4 * p + k], ar = fabs(res);
+                double w = 1.0 / (b * (ar > fl ? ar : fl)), ib2 = 1.0 / (b * b);
+                const double* Jk = X->J + 24 * p + 6 * k;
+                for (int i = 0; i < 6; ++i) {
+                    g[i] += w * Jk[i] * res;
+                    for (int j = 0; j < 6; ++j) {
+                        H[6 * i + j] += w * Jk[i] * Jk[j];
+                        Ht[6 * i + j] += ib2 * Jk[i] * Jk[j];
+                    }
+                }
+                S[78] += ar / b;
+            }
+            S[79] += 1.0;
+        }
+    }
 }
 
 /* Sums over the kept residuals (or_residuals):
  *   H  = sum w J^T J,  g = sum w J^T r   with IRLS weights w = 1/(b max(|r|, floor)),
  *   Ht = sum J^T J / b^2                  (Laplace, Sec. 4.1),
- *   stats = (sum |r|/b, kept pixels). */
+ *   stats = (sum |r|/b, kept pixels).
+ * Each sum is formed over chunks of OR_NE_CHUNK consecutive pixels (pixel
+ * order within a chunk), then over the chunks in order. */
 int or_normal_equations(const or_params* P, const double anchor_pose[7], const float* a_depth,
                         const float* a_rgb, const double pose[7], const float* o_depth,
                         const float* o_rgb, double H[36], double g[6], double Ht[36],
                         double stats[2]) {
     int N = P->width * P->height;
+    long nchunk = (N + OR_NE_CHUNK - 1) / OR_NE_CHUNK;
     double* r = (double*)malloc(sizeof(double) * 4 * N);
     double* J = (double*)malloc(sizeof(double) * 24 * N);
     int32_t* assoc = (int32_t*)malloc(sizeof(int32_t) * 2 * N);
     uint8_t* kept = (uint8_t*)malloc(N);
-    int rc = (!r || !J || !assoc || !kept) ? -2
+    double* cs = (double*)malloc(sizeof(double) * OR_NE_VALUES * (nchunk > 0 ? nchunk : 1));
+    int rc = (!r || !J || !assoc || !kept || !cs) ? -2
              : or_residuals(P, anchor_pose, a_depth, a_rgb, pose, o_depth, o_rgb, r, J, assoc, kept);
-    if (rc) { free(r); free(J); free(assoc); free(kept); return rc ? rc : -2; }
-    memset(H, 0, sizeof(double) * 36);
-    memset(Ht, 0, sizeof(double) * 36);
-    memset(g, 0, sizeof(double) * 6);
-    double cost = 0.0, n_kept = 0.0;
-    for (int p = 0; p < N; ++p) {
-        if (!kept[p]) continue;
-        for (int k = 0; k < 4; ++k) {
-            double b = k == 0 ? P->b_geo : P->b_rgb, fl = k == 0 ? P->floor_geo : P->floor_rgb;
-            double res = r[4 * p + k], ar = fabs(res);
-            double w = 1.0 / (b * (ar > fl ? ar : fl)), ib2 = 1.0 / (b * b);
-            const double* Jk = J + 24 * p + 6 * k;
-            for (int i = 0; i < 6; ++i) {
-                g[i] += w * Jk[i] * res;
-                for (int j = 0; j < 6; ++j) {
-                    H[6 * i + j] += w * Jk[i] * Jk[j];
-                    Ht[6 * i + j] += ib2 * Jk[i] * Jk[j];
-                }
-            }
-            cost += ar / b;
-        }
-        n_kept += 1.0;
-    }
-    stats[0] = cost;
-    stats[1] = n_kept;
-    free(r); free(J); free(assoc); free(kept);
+    if (rc) { free(r); free(J); free(assoc); free(kept); free(cs); return rc ? rc : -2; }
+    ne_ctx X = {P, r, J, kept, N, cs};
+    parallel_for(nchunk, 1, ne_chunks, &X);
+    double S[OR_NE_VALUES];
+    memset(S, 0, sizeof(S));
+    for (long c = 0; c < nchunk; ++c)
+        for (int v = 0; v < OR_NE_VALUES; ++v) S[v] += cs[OR_NE_VALUES * c + v];
+    memcpy(H, S, sizeof(double) * 36);
+    memcpy(g, S + 36, sizeof(double) * 6);
+    memcpy(Ht, S + 42, sizeof(double) * 36);
+    stats[0] = S[78];
+    stats[1] = S[79];
+    free(r); free(J); free(assoc); free(kept); free(cs);
     return 0;
 }
 
@@ -1070,44 +1276,43 @@ int or_localise(const or_params* P, const or_prior* pr, const or_state* prev,
  *   L' = L + Lu,  mu' = (L mu + Lu f) / L',  f = [-clamp(sdf, -trunc, trunc), rgb].
  * Colour is updated only where |sdf| <= trunc.  Returns the number of voxels
  * whose occupancy was updated. */
-int64_t or_fuse(const or_params* P, double* occ, double* rgb, double* var_occ, double* var_rgb,
-                const double pose_in[7], const float* depth, const float* rgb_obs) {
-    double pose[7];
-    normalise_pose(pose_in, pose);
-    int W = P->width, H = P->height;
-    uint8_t* mask = (uint8_t*)malloc((size_t)W * H);
-    if (!mask) return -2;
-    or_depth_mask(P, depth, mask);
-    double R[9];
-    quat_to_R(pose + 3, R);
-    /* FP64 recipe of the world->camera transform, rounded once to FP32:
-     * M = R^T, b = -((R0i t0 + R1i t1) + R2i t2). */
+typedef struct {
+    const or_params* P;
+    double *occ, *rgb, *var_occ, *var_rgb;
+    const float *depth, *rgb_obs;
+    const uint8_t* mask;
+    double pose[7], R[9];
     float M32[9], b32[3], o32[3];
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) M32[3 * i + j] = (float)R[3 * j + i];
-        b32[i] = (float)(-((R[i] * pose[0] + R[3 + i] * pose[1]) + R[6 + i] * pose[2]));
-        o32[i] = (float)P->origin[i];
-    }
+    int64_t n_upd[OR_MAX_THREADS];
+} fuse_ctx;
+
+/* Voxel slices z in [begin, end). */
+static void fuse_slices(void* arg, long begin, long end, int job) {
+    fuse_ctx* X = (fuse_ctx*)arg;
+    const or_params* P = X->P;
+    const int W = P->width, H = P->height;
+    const double *pose = X->pose, *R = X->R;
     float vs32 = (float)P->voxel, trunc32 = (float)P->trunc;
     float fx32 = (float)P->fx, fy32 = (float)P->fy, cx32 = (float)P->cx, cy32 = (float)P->cy;
     double Lu = 1.0 / P->update_var;
     int64_t n_upd = 0;
-    for (int k = 0; k < P->nz; ++k)
+    for (long kl = begin; kl < end; ++kl)
         for (int j = 0; j < P->ny; ++j)
             for (int i = 0; i < P->nx; ++i) {
+                const int k = (int)kl;
                 /* ---- decisions, FP32 recipe ---- */
-                float pc[3] = {fmaf((float)i + 0.5f, vs32, o32[0]), fmaf((float)j + 0.5f, vs32, o32[1]),
-                               fmaf((float)k + 0.5f, vs32, o32[2])};
-                float X[3];
-                affine32(M32, b32, pc, X);
-                if (!(X[2] > 0.0f)) continue;
-                float iz = 1.0f / X[2];
-                float u = fmaf(fx32 * X[0], iz, cx32), v = fmaf(fy32 * X[1], iz, cy32);
+                float pc[3] = {fmaf((float)i + 0.5f, vs32, X->o32[0]), fmaf((float)j + 0.5f, vs32, X->o32[1]),
+                               fmaf((float)k + 0.5f, vs32, X->o32[2])};
+                float Xc32[3];
+                affine32(X->M32, X->b32, pc, Xc32);
+                if (!(Xc32[2] > 0.0f)) continue;
+                float iz = 1.0f / Xc32[2];
+                float u = fmaf(fx32 * Xc32[0], iz, cx32), v = fmaf(fy32 * Xc32[1], iz, cy32);
                 float nu = floorf(u + 0.5f), nv = floorf(v + 0.5f);
                 if (!(nu >= 0.0f && nu <= (float)(W - 1) && nv >= 0.0f && nv <= (float)(H - 1))) continue;
                 int p = (int)nv * W + (int)nu;
-                if (!mask[p]) continue;
-                float sdf32 = depth[p] - X[2];
+                if (!X->mask[p]) continue;
+                float sdf32 = X->depth[p] - Xc32[2];
                 if (!(sdf32 >= -trunc32)) continue;
                 int colour = fabsf(sdf32) <= trunc32;
                 /* ---- values, FP64 ---- */
@@ -1115,20 +1320,48 @@ int64_t or_fuse(const or_params* P, double* occ, double* rgb, double* var_occ, d
                                 P->origin[2] + (k + 0.5) * P->voxel};
                 double rel[3] = {pw[0] - pose[0], pw[1] - pose[1], pw[2] - pose[2]}, Xc[3];
                 mat3_tvec(R, rel, Xc);
-                double sdf = (double)depth[p] - Xc[2];
+                double sdf = (double)X->depth[p] - Xc[2];
                 double f = -(sdf < P->trunc ? (sdf > -P->trunc ? sdf : -P->trunc) : P->trunc);
                 long vi = vidx(P, i, j, k);
-                double L = 1.0 / var_occ[vi], Ln = L + Lu;
-                occ[vi] = (L * occ[vi] + Lu * f) / Ln;
-                var_occ[vi] = 1.0 / Ln;
+                double L = 1.0 / X->var_occ[vi], Ln = L + Lu;
+                X->occ[vi] = (L * X->occ[vi] + Lu * f) / Ln;
+                X->var_occ[vi] = 1.0 / Ln;
                 ++n_upd;
                 if (colour) {
-                    double Lc = 1.0 / var_rgb[vi], Lcn = Lc + Lu;
+                    double Lc = 1.0 / X->var_rgb[vi], Lcn = Lc + Lu;
                     for (int ch = 0; ch < 3; ++ch)
-                        rgb[3 * vi + ch] = (Lc * rgb[3 * vi + ch] + Lu * (double)rgb_obs[3 * p + ch]) / Lcn;
-                    var_rgb[vi] = 1.0 / Lcn;
+                        X->rgb[3 * vi + ch] = (Lc * X->rgb[3 * vi + ch] + Lu * (double)X->rgb_obs[3 * p + ch]) / Lcn;
+                    X->var_rgb[vi] = 1.0 / Lcn;
                 }
             }
+    X->n_upd[job] += n_upd;
+}
+
+int64_t or_fuse(const or_params* P, double* occ, double* rgb, double* var_occ, double* var_rgb,
+                const double pose_in[7], const float* depth, const float* rgb_obs) {
+    fuse_ctx* X = (fuse_ctx*)calloc(1, sizeof(fuse_ctx));
+    if (!X) return -2;
+    normalise_pose(pose_in, X->pose);
+    int W = P->width, H = P->height;
+    uint8_t* mask = (uint8_t*)malloc((size_t)W * H);
+    if (!mask) { free(X); return -2; }
+    or_depth_mask(P, depth, mask);
+    const double* pose = X->pose;
+    double* R = X->R;
+    quat_to_R(pose + 3, R);
+    /* FP64 recipe of the world->camera transform, rounded once to FP32:
+     * M = R^T, b = -((R0i t0 + R1i t1) + R2i t2). */
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) X->M32[3 * i + j] = (float)R[3 * j + i];
+        X->b32[i] = (float)(-((R[i] * pose[0] + R[3 + i] * pose[1]) + R[6 + i] * pose[2]));
+        X->o32[i] = (float)P->origin[i];
+    }
+    X->P = P; X->occ = occ; X->rgb = rgb; X->var_occ = var_occ; X->var_rgb = var_rgb;
+    X->depth = depth; X->rgb_obs = rgb_obs; X->mask = mask;
+    int jobs = parallel_for(P->nz, 1, fuse_slices, X);
+    int64_t n_upd = 0;
+    for (int j = 0; j < jobs; ++j) n_upd += X->n_upd[j];
     free(mask);
+    free(X);
     return n_upd;
 }

@@ -84,6 +84,10 @@ typedef struct {
 #ifdef __cplusplus
 extern "C" {
 #endif
+/* Worker threads of the per-ray, per-pixel and per-voxel loops (n <= 0:
+ * every online processor, the default).  Results do not depend on it. */
+void or_set_threads(int32_t n);
+int32_t or_get_threads(void);
 int or_render(const or_params* P, const double* occ, const double* rgb,
               const double pose[7], const int32_t* pix, int32_t npix,
               double* depth, double* rgb_out, uint8_t* mask, int32_t* hitk,
