@@ -122,13 +122,11 @@ __device__ inline void quat_normalise(double* q) {
     for (int i = 0; i < 4; ++i) q[i] *= r;
 }
 
-// normalise(quat_exp(w) (x) q) with w >= 0 (the operations of quat_exp,
-// quat_mul and quat_normalise), computed by the 32 lanes of one warp with
-// quaternion component c = lane & 3 in lane c; returns that component.
-__device__ __forceinline__ double warp_quat_exp_mul(const double w[3], const double* q) {
+// Component c = lane & 3 of quat_exp(w) (the operations of quat_exp), with
+// th2 = |w|^2 given; every lane of the warp must call it.
+__device__ __forceinline__ double warp_quat_exp_component(const double w[3], double th2) {
     const int c = (threadIdx.x & 31) & 3;
     const double w0 = w[0], w1 = w[1], w2 = w[2];
-    const double th2 = fdot3(w0, w0, w1, w1, w2, w2);
     double qe;
     if (th2 < 0.25) {   // the half-angle series of quat_exp: ch (lane c = 0), sh (c > 0)
         const double x = 0.25 * th2;
@@ -146,13 +144,29 @@ __device__ __forceinline__ double warp_quat_exp_mul(const double w[3], const dou
         quat_exp(w, q4);
         qe = c == 0 ? q4[0] : (c == 1 ? q4[1] : (c == 2 ? q4[2] : q4[3]));
     }
-    // Hamilton product qe (x) q, component c (the operations of quat_mul)
-    const double a0 = __shfl_sync(0xffffffffu, qe, 0), a1 = __shfl_sync(0xffffffffu, qe, 1),
-                 a2 = __shfl_sync(0xffffffffu, qe, 2), a3 = __shfl_sync(0xffffffffu, qe, 3);
+    return qe;
+}
+
+// Component c = lane & 3 of the Hamilton product a (x) q (the operations of
+// quat_mul), a given by component in lanes 0..3 (`ac` on lane c); every lane
+// of the warp must call it.
+__device__ __forceinline__ double warp_quat_mul_component(double ac, const double* q) {
+    const int c = (threadIdx.x & 31) & 3;
+    const double a0 = __shfl_sync(0xffffffffu, ac, 0), a1 = __shfl_sync(0xffffffffu, ac, 1),
+                 a2 = __shfl_sync(0xffffffffu, ac, 2), a3 = __shfl_sync(0xffffffffu, ac, 3);
     const int p0 = c, p1 = c ^ 1, p2 = c ^ 2, p3 = c ^ 3;
     const double t3 = a3 * q[p3];
-    const double qm = fma(a0, q[p0], fma((c == 0 || c == 2) ? -a1 : a1, q[p1],
-                                         fma((c == 0 || c == 3) ? -a2 : a2, q[p2], (c == 0 || c == 1) ? -t3 : t3)));
+    return fma(a0, q[p0], fma((c == 0 || c == 2) ? -a1 : a1, q[p1],
+                              fma((c == 0 || c == 3) ? -a2 : a2, q[p2], (c == 0 || c == 1) ? -t3 : t3)));
+}
+
+// normalise(quat_exp(w) (x) q) with w >= 0 (the operations of quat_exp,
+// quat_mul and quat_normalise), computed by the 32 lanes of one warp with
+// quaternion component c = lane & 3 in lane c; returns that component.
+__device__ __forceinline__ double warp_quat_exp_mul(const double w[3], const double* q) {
+    const int c = (threadIdx.x & 31) & 3;
+    const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
+    const double qm = warp_quat_mul_component(warp_quat_exp_component(w, th2), q);
     // normalised, w >= 0 (quat_normalise)
     const double n0 = __shfl_sync(0xffffffffu, qm, 0), n1 = __shfl_sync(0xffffffffu, qm, 1),
                  n2 = __shfl_sync(0xffffffffu, qm, 2), n3 = __shfl_sync(0xffffffffu, qm, 3);
@@ -198,6 +212,103 @@ __device__ inline void R_to_quat(const double* R, double* q) {
 }
 
 // Rotation of a unit quaternion (value path; not the decision recipe).
+
+// ------------------------------------------------ one-warp FP64 6x6 solve
+// GB300's FP64 pipe retires about one warp instruction per 64 cycles per SM
+// sub-partition, so a short FP64 chain costs its instruction count.  The
+// two functions below keep that count low: a reciprocal whose seed comes
+// from the FP32 unit, and a factorisation that needs one reciprocal per
+// column and two FP64 instructions per column for all entries at once.
+
+// Packed lower-triangle position of entry (i, j), i >= j, of a 6x6 matrix.
+__host__ __device__ constexpr int tri6(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// True iff d is a positive, finite, normal double whose exponent leaves
+// room for rcp64 (2^-1022 <= d < 2^1022), tested on its bits.
+__device__ __forceinline__ bool pivot_ok(double d) {
+    const int hi = __double2hiint(d);
+    const int e = (hi >> 20) & 0x7ff;
+    return hi >= 0 && e >= 1 && e <= 2044;
+}
+
+// 1/d for d with pivot_ok(d), by Newton-Raphson iteration for the
+// reciprocal, y' = y + y (1 - d y) (the relative error squares each step).
+// The seed is the single-precision approximate reciprocal (PTX
+// rcp.approx.ftz.f32, relative error about 2^-23) of d's mantissa cut to 20
+// bits, rescaled by the exponent with integer operations: relative error
+// below 2^-19.5, then 2^-39 and, after the second step, the final rounding
+// (a result within one unit in the last place of 1/d).  Only the two steps
+// (four FMAs) use the FP64 pipe.
+__device__ __forceinline__ double rcp64(double d) {
+    const int hi = __double2hiint(d);
+    const int e = (hi >> 20) & 0x7ff;
+    const float m = __int_as_float(0x3f800000 | ((hi & 0xfffff) << 3));   // mantissa in [1, 2)
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));                // in (0.5, 1]
+    const int rb = __float_as_int(r);
+    const int ye = ((rb >> 23) & 0xff) - 127 + 2046 - e;                 // biased exponent of r 2^(1023 - e)
+    const double y0 = __hiloint2double((ye << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
+    const double y1 = fma(y0, fma(-d, y0, 1.0), y0);
+    return fma(y1, fma(-d, y1, 1.0), y1);
+}
+
+// Solves A x = b for a 6x6 symmetric positive definite A on one warp by the
+// square-root-free Cholesky factorisation A = L D L^T (L unit lower
+// triangular, D diagonal).  Lane e < 21 brings entry (i, j), e = tri6(i, j),
+// of A's lower triangle in `a`; lane 21 + i brings b_i.  Column j: the
+// pivot d_j = a_jj, l_ij = a_ij / d_j below it, and every trailing entry and
+// right-hand side row i > j takes a_im -= l_ij a_mj (b_i -= l_ij b_j: the
+// forward substitution with L rides along); then z = D^-1 y and the back
+// substitution with L^T.  Returns x_i in lane 21 + i (other lanes: junk);
+// *pd: every pivot passed pivot_ok (the same on every lane).  All 32 lanes
+// must call it.
+__device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
+    const int lane = threadIdx.x & 31;
+    const bool rhs = lane >= 21 && lane < 27;
+    // this lane's row li and column lm (6: the right-hand side)
+    int li = 0, lm = 0;
+    if (lane < 21) {
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+            if (lane >= tri6(i, 0)) li = i;
+        lm = lane - tri6(li, 0);
+    } else if (rhs) {
+        li = lane - 21;
+        lm = 6;
+    } else {
+        li = 5;
+        lm = 6;
+    }
+    bool ok = true;
+    double rown = 0.0;   // 1 / d_li, for this lane's row
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double d = __shfl_sync(0xffffffffu, a, tri6(j, j));
+        ok = ok && pivot_ok(d);
+        const double rj = rcp64(d);
+        if (li == j) rown = rj;
+        const bool below = li > j;                             // rows that column j updates
+        const double aij = __shfl_sync(0xffffffffu, a, below ? tri6(li, j) : 0);
+        const int src_m = lm == 6 ? 21 + j : (lm > j ? tri6(lm, j) : 0);
+        const double amj = __shfl_sync(0xffffffffu, a, src_m);
+        const double lij = aij * rj;
+        const double upd = fma(-lij, amj, a);
+        if (below && lm == j) a = lij;                         // the factor L_ij, kept for the back substitution
+        else if (below && lm > j) a = upd;                     // trailing entry (lm <= li) or right-hand side (lm = 6)
+    }
+    // z = D^-1 y on the right-hand-side lanes
+    double x = a * rown;
+    // back substitution: x_k is final once the rows below it are done
+#pragma unroll
+    for (int k = 5; k >= 1; --k) {
+        const double xk = __shfl_sync(0xffffffffu, x, 21 + k);
+        const double lki = __shfl_sync(0xffffffffu, a, li < k ? tri6(k, li) : 0);
+        const double nx = fma(-lki, xk, x);
+        if (rhs && li < k) x = nx;
+    }
+    *pd = ok;
+    return x;
+}
 
 // Block-cooperative inverse of an N x N SPD matrix (A and Ainv in shared
 // or global memory): warp 0 factors it (lane i holding row i) into the

@@ -495,51 +495,21 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         __syncthreads();
         if (warp == 0) {
-            // 6x6 FP64 Cholesky (right-looking) and both triangular solves on one
-            // warp, lane i < 6 holding row i: each step is one warp instruction
-            // for all rows.  Every element accumulates its terms in the order of
-            // the left-looking recipe (k increasing); the back substitution
-            // subtracts in the order the steps become known (k decreasing).
-            __shared__ double Ls[36];
-            double a[6], r[6];
-            const int row = lane < 6 ? lane : 5;
+            // The 6x6 FP64 solve by the square-root-free Cholesky factorisation
+            // on one warp (warp_ldlt6_solve): lane e < 21 brings entry (i, j) of
+            // Hx's lower triangle, lane 21 + i the right-hand side gx_i.
+            int li = 0, lm = 0;
+            if (lane < 21) {
 #pragma unroll
-            for (int j = 0; j < 6; ++j) a[j] = Hx[6 * row + j];
-            double bi = gx[row];
-            bool pd = true;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const double d = __shfl_sync(0xffffffffu, a[j], j);
-                pd = pd && d > 0.0 && isfinite(d);
-                const double rj = rsqrt(d);
-                r[j] = rj;
-                if (lane > j) a[j] = a[j] * rj;   // L_ij
-#pragma unroll
-                for (int m = j + 1; m < 6; ++m) {
-                    const double lmj = __shfl_sync(0xffffffffu, a[j], m);
-                    if (lane >= m) a[m] = fma(-a[j], lmj, a[m]);
-                }
+                for (int i = 1; i < 6; ++i)
+                    if (lane >= tri6(i, 0)) li = i;
+                lm = lane - tri6(li, 0);
             }
-            // forward: y_j = b_j r_j, then b_i -= L_ij y_j below it
-#pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const double yj = __shfl_sync(0xffffffffu, bi, j) * r[j];
-                if (lane == j) bi = yj;
-                else if (lane > j) bi = fma(-a[j], yj, bi);
-            }
-            if (lane < 6) {
-#pragma unroll
-                for (int j = 0; j < 6; ++j) Ls[6 * lane + j] = a[j];
-            }
-            __syncwarp();
-            // backward: step_k = y_k r_k, then y_i -= L_ki step_k above it
-#pragma unroll
-            for (int k = 5; k >= 0; --k) {
-                const double sk = __shfl_sync(0xffffffffu, bi, k) * r[k];
-                if (lane == k) bi = sk;
-                else if (lane < k) bi = fma(-Ls[6 * k + row], sk, bi);
-            }
-            if (pd && lane < 6) xn[lane] = st[36 + lane] + bi;
+            const bool rhs = lane >= 21 && lane < 27;
+            const double a = rhs ? gx[lane - 21] : Hx[6 * li + lm];
+            bool pd;
+            const double x = warp_ldlt6_solve(a, &pd);
+            if (pd && rhs) xn[lane - 21] = st[36 + lane - 21] + x;
             if (lane == 0) s_pd = pd;
         }
         __syncthreads();
