@@ -146,6 +146,9 @@ class Filter:
         self.h = h
         self.W, self.H = cfg.width, cfg.height
         self.N = cfg.nx * cfg.ny * cfg.nz
+        # Counts calls that may change the map (load, update, step, descent):
+        # autograd.PrismRender reloads its map only when this or its tensors changed.
+        self.map_version = 0
 
     # ------------------------------------------------------------- plumbing
     def _check(self, status: int, h):
@@ -182,6 +185,7 @@ class Filter:
 
     def update_map(self, depth, rgb):
         d, c = self._img(depth, rgb)
+        self.map_version += 1
         self._check(self.L.prism_update_map(self.h, d, c), self.h)
 
     def render(self, pose7=None, depth=None, rgb=None, mask=None, hitk=None, alloc: bool = True):
@@ -204,6 +208,7 @@ class Filter:
         imu = np.zeros((0, 7)) if imu is None else np.ascontiguousarray(imu, dtype=np.float64)
         d, c = self._img(depth, rgb)
         out = State() if want_state else None
+        self.map_version += 1
         self._check(self.L.prism_step(self.h, _hptr(imu) if len(imu) else None, len(imu), dt, d, c,
                                       C.byref(out) if out is not None else None), self.h)
         return out
@@ -256,6 +261,7 @@ class Filter:
         d = _host_img(depth, (self.H, self.W), "depth")
         c = _host_img(rgb, (self.H, self.W, 3), "rgb")
         out = State() if want_state else None
+        self.map_version += 1
         self._check(self.L.prism_step_host(self.h, _hptr(imu) if len(imu) else None, len(imu), dt, d, c,
                                            C.byref(out) if out is not None else None), self.h)
         return out
@@ -270,6 +276,7 @@ class Filter:
         d = _dptr(depth, (n, self.H, self.W), name="depth")
         c = _dptr(rgb, (n, self.H, self.W, 3), name="rgb")
         out = np.zeros(1) if want_loss else None
+        self.map_version += 1
         self._check(self.L.prism_map_descent(self.h, n, _hptr(poses), d, c, sd, sc, lr_occ, lr_rgb,
                                              _hptr(out)), self.h)
         return float(out[0]) if want_loss else None
@@ -286,6 +293,7 @@ class Filter:
         """Load map arrays (None leaves that part of the map unchanged)."""
         N = self.N
         f = lambda a, n, name: None if a is None else _dptr(a.reshape(-1), (n,), name=name)
+        self.map_version += 1
         self._check(self.L.prism_map_load(self.h, f(occ, N, "occ"), f(rgb, 3 * N, "rgb"),
                                           f(var_occ, N, "var_occ"), f(var_rgb, N, "var_rgb")), self.h)
 

@@ -167,3 +167,42 @@ def test_autograd_function(oracle_mod):
         _, gm = F.render_backward(base, wd.contiguous(), wc.contiguous(), None, None)
         assert gm[3 + j] == pytest.approx(fd, rel=2e-2, abs=2e-3 * np.abs(g7[3:]).max()), (j, gm[3 + j], fd)
     F.close()
+
+
+def test_autograd_loads_the_map_only_when_it_changed(oracle_mod):
+    """A forward and its backward load the map once; an in-place update of
+    the map tensors, or another map in the filter, makes the next forward
+    load it again."""
+    from paper_2212_02988_gb300.autograd import render
+    w = synth.ROOM64
+    s = synth.Sequence(w)
+    occ, rgb, vo, vr = s.settled_map()
+    F, _ = make_pair(w, oracle_mod, map_arrays=(occ, rgb, vo, vr))
+    loads = []
+    load = F.map_load
+    F.map_load = lambda *a, **k: (loads.append(1), load(*a, **k))[1]
+    pose = torch.tensor(s.pose7(5), dtype=torch.float64)
+    occ_t = t(occ).requires_grad_(True)
+    rgb_t = t(rgb).requires_grad_(True)
+    first = None
+    for it in range(3):
+        d, c = render(pose, occ_t, rgb_t, F)
+        (d.sum() + c.sum()).backward()
+        assert len(loads) == it + 1
+        if first is None:
+            first = occ_t.grad.clone()
+        with torch.no_grad():
+            occ_t.sub_(1e-6 * torch.sign(occ_t.grad))   # an in-place step: the next forward reloads
+        occ_t.grad = None
+        rgb_t.grad = None
+    F.map_load(t(occ), t(rgb))                           # another map in the filter
+    d, c = render(pose, occ_t, rgb_t, F)
+    assert len(loads) == 5
+    # the gradient of the reloaded map is that of a fresh filter holding it
+    G, _ = make_pair(w, oracle_mod, map_arrays=(occ_t.detach().cpu().numpy(), rgb, vo, vr))
+    o2 = occ_t.detach().clone().requires_grad_(True)
+    d2, c2 = render(pose, o2, rgb_t.detach().clone().requires_grad_(True), G)
+    assert torch.equal(d, d2) and torch.equal(c, c2)
+    assert first.abs().sum() > 0
+    F.close()
+    G.close()
