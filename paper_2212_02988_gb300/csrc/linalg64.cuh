@@ -175,6 +175,23 @@ __device__ __forceinline__ double warp_quat_exp_mul(const double w[3], const dou
     return (c == 0 ? n0 : (c == 1 ? n1 : (c == 2 ? n2 : n3))) * rn;
 }
 
+// normalise(quat_exp(w) (x) q) for a unit q, the normalisation by the
+// first-order term of 1 / sqrt(n) around n = 1: with both factors unit to
+// rounding, n = |qe (x) q|^2 = 1 + delta, |delta| ~ 1e-15, and
+// 1 / sqrt(1 + delta) = 1 - delta / 2 + O(delta^2) is 1.5 - 0.5 n to FP64
+// rounding (one FMA in place of the reciprocal square root's chain); w >= 0
+// as in warp_quat_exp_mul.  Every lane of the warp must call it.
+__device__ __forceinline__ double warp_quat_exp_mul_unit(const double w[3], const double* q) {
+    const int c = (threadIdx.x & 31) & 3;
+    const double th2 = fdot3(w[0], w[0], w[1], w[1], w[2], w[2]);
+    const double qm = warp_quat_mul_component(warp_quat_exp_component(w, th2), q);
+    const double n0 = __shfl_sync(0xffffffffu, qm, 0), n1 = __shfl_sync(0xffffffffu, qm, 1),
+                 n2 = __shfl_sync(0xffffffffu, qm, 2), n3 = __shfl_sync(0xffffffffu, qm, 3);
+    double rn = fma(-0.5, fma(n0, n0, fdot3(n1, n1, n2, n2, n3, n3)), 1.5);
+    if (n0 < 0.0) rn = -rn;
+    return (c == 0 ? n0 : (c == 1 ? n1 : (c == 2 ? n2 : n3))) * rn;
+}
+
 __device__ inline void mat3inv(const double* A, double* B) {
     double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
     double det = A[0] * c00 + A[1] * c01 + A[2] * c02;

@@ -90,6 +90,11 @@ struct DevState {
     // (L = prior pose precision)
     double gn_C[18];
     double gn_Lxi[6];
+    // constants of one localisation for the FP32 matrices of each iterate:
+    // q0 = conj(q_anchor) (x) q_prior (the rotation Ra^T R_prior) and
+    // b0 = Ra^T (t_prior - t_anchor)
+    double gn_q0[4];
+    double gn_b0[3];
     // FP32 decision matrices, each computed once per pose by the FP64 recipe:
     float c2w[12];             // state mean, camera -> world: R (9), centre (3)
     float w2c[12];             // state mean, world -> camera: M (9), b (3)

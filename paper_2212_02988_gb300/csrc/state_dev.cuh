@@ -256,6 +256,17 @@ __device__ __forceinline__ void prep_mats_warp(DevState* dev, int kind, const Po
                 for (int k = 0; k < 6; ++k) lx = fma(dev->prec_pp[6 * r + k], dev->xi[k], lx);
                 dev->gn_Lxi[r] = lx;
             }
+            // the localisation's constants: q0 = conj(q_anchor) (x) q_prior on
+            // lanes 24..27, b0 = Ra^T (t_prior - t_anchor) on lanes 28..30
+            const int c = lane & 3;
+            const double q0 = warp_quat_mul_component(c == 0 ? qa[0] : -qa[c], dev->pq);
+            if (lane >= 24 && lane < 28) dev->gn_q0[c] = q0;
+            const int i2 = lane >= 28 && lane < 31 ? lane - 28 : 0;
+            const double rb0 = __shfl_sync(0xffffffffu, v, i2), rb1 = __shfl_sync(0xffffffffu, v, 3 + i2),
+                         rb2 = __shfl_sync(0xffffffffu, v, 6 + i2);
+            const double b0 = fdot3(rb0, dev->pt[0] - anchor[0], rb1, dev->pt[1] - anchor[1], rb2,
+                                    dev->pt[2] - anchor[2]);
+            if (lane >= 28 && lane < 31) dev->gn_b0[i2] = b0;
         }
     }
 }

@@ -99,7 +99,7 @@ __device__ __forceinline__ void accumulate(float* acc, const float J[6], float r
 
 // The FP64 state the finish reads, slot e of the staging array: prec_pp
 // 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55; Gauss-Newton also
-// the tangent map C 56..73 and L xi 74..79; Laplace also D 56..91, the pose
+// the tangent map C 56..73, L xi 74..79, q0 80..83 and b0 84..86; Laplace also D 56..91, the pose
 // block of the previous covariance 92..127, cov_vel 128..163, pv 164..166,
 // pw 167..169.  nullptr past the mode's last slot.
 template <int MODE>
@@ -112,6 +112,8 @@ __device__ __forceinline__ const double* stage_src(const DevState* dev, int e) {
     if (MODE == TRACK_GN) {
         if (e < 74) return dev->gn_C + (e - 56);
         if (e < 80) return dev->gn_Lxi + (e - 74);
+        if (e < 84) return dev->gn_q0 + (e - 80);
+        if (e < 87) return dev->gn_b0 + (e - 84);
     }
     if (MODE == TRACK_LAPLACE) {
         if (e < 92) return dev->D + (e - 56);
@@ -517,31 +519,42 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             if (tid == 0) dev->flags |= FLAG_GN_NOTPD;
             return;
         }
-        if (warp == 0) {   // retraction and the FP32 matrices of the next pass, one quaternion component a lane
-            const double qn = warp_quat_exp_mul(xn + 3, st + 49);
-            double pose[7];
-            pose[3] = __shfl_sync(0xffffffffu, qn, 0);
-            pose[4] = __shfl_sync(0xffffffffu, qn, 1);
-            pose[5] = __shfl_sync(0xffffffffu, qn, 2);
-            pose[6] = __shfl_sync(0xffffffffu, qn, 3);
-            const int ta = lane < 3 ? lane : 0;
-            const double tv = st[53 + ta] + xn[ta];
-            pose[0] = __shfl_sync(0xffffffffu, tv, 0);
-            pose[1] = __shfl_sync(0xffffffffu, tv, 1);
-            pose[2] = __shfl_sync(0xffffffffu, tv, 2);
-            warp_mats_rel(pose, st + 42, dev->rel);
+        if (warp == 0) {
+            // The FP32 pose -> anchor matrices of the next pass, straight from
+            // xi (the critical path): Ra^T Exp(xi_theta) R_prior = Exp(w) A0 with
+            // w = Ra^T xi_theta and A0 = Ra^T R_prior = R(q0), so
+            // M = R(quat_exp(w) (x) q0) (unit to rounding) and b = b0 + Ra^T xi_t.
+            // Lanes 0..2: w; lane 3: |xi_theta|^2; lanes 9..11: Ra^T xi_t.
+            const bool tl = lane >= 9 && lane < 12;
+            const int r = lane < 3 ? lane : (tl ? lane - 9 : 0);
+            const bool sq = lane == 3;
+            const double* v = tl ? xn : xn + 3;
+            const double d = fdot3(sq ? v[0] : Cm[3 * r], v[0], sq ? v[1] : Cm[3 * r + 1], v[1],
+                                   sq ? v[2] : Cm[3 * r + 2], v[2]);
+            const double w[3] = {__shfl_sync(0xffffffffu, d, 0), __shfl_sync(0xffffffffu, d, 1),
+                                 __shfl_sync(0xffffffffu, d, 2)};
+            const double th2 = __shfl_sync(0xffffffffu, d, 3);
+            const double qr = warp_quat_mul_component(warp_quat_exp_component(w, th2), st + 80);
+            const double q0 = __shfl_sync(0xffffffffu, qr, 0), q1 = __shfl_sync(0xffffffffu, qr, 1),
+                         q2 = __shfl_sync(0xffffffffu, qr, 2), q3 = __shfl_sync(0xffffffffu, qr, 3);
+            const double me = quat_R_entry_rn(q0, q1, q2, q3, lane < 9 ? lane : 0);
+            const double be = st[84 + r] + d;
+            if (lane < 9) dev->rel[lane] = (float)me;
+            else if (tl) dev->rel[lane] = (float)be;
+        } else if (warp == 1) {   // the FP64 pose of the new iterate (the state mean after the last pass)
+            const double qn = warp_quat_exp_mul_unit(xn + 3, st + 49);
+            if (lane < 4) dev->cur_pose[3 + lane] = qn;
+            if (lane < 3) dev->cur_pose[lane] = st[53 + lane] + xn[lane];
             if (lane < 6) dev->xi[lane] = xn[lane];
-            if (lane < 7) dev->cur_pose[lane] = pose[lane];
-        } else if (tid >= 32 && tid < 41) {   // meanwhile: the tangent map of the new iterate
-            const int e = tid - 32, i = e / 3, j = e % 3;
-            Jn[e] = so3_jl_entry(xn + 3, i, j);
+        } else if (warp == 2 && lane < 9) {   // meanwhile: the tangent map of the new iterate
+            const int i = lane / 3, j = lane % 3;
+            Jn[lane] = so3_jl_entry(xn + 3, i, j);
             __syncwarp(0x1ffu);
-            dev->gn_C[9 + e] = fdot3(Cm[3 * i], Jn[j], Cm[3 * i + 1], Jn[3 + j], Cm[3 * i + 2], Jn[6 + j]);
-        } else if (tid >= 64 && tid < 70) {
-            const int i = tid - 64;
+            dev->gn_C[9 + lane] = fdot3(Cm[3 * i], Jn[j], Cm[3 * i + 1], Jn[3 + j], Cm[3 * i + 2], Jn[6 + j]);
+        } else if (warp == 3 && lane < 6) {
             double lx = 0.0;
-            for (int k = 0; k < 6; ++k) lx = fma(st[6 * i + k], xn[k], lx);
-            dev->gn_Lxi[i] = lx;
+            for (int k = 0; k < 6; ++k) lx = fma(st[6 * lane + k], xn[k], lx);
+            dev->gn_Lxi[lane] = lx;
         }
         return;
     }
