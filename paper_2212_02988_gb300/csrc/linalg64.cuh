@@ -13,6 +13,17 @@ __device__ __forceinline__ double fdot3(double a0, double b0, double a1, double 
     return fma(a0, b0, fma(a1, b1, a2 * b2));
 }
 
+// c ? x : y as one predicated select (PTX selp.f64).  Both operands are
+// computed by every lane, so that a lane-dependent choice does not split a
+// warp into groups that each issue the FP64 instructions feeding it (each
+// issue costs ~64 cycles on GB300's FP64 pipe, whatever lanes are active).
+__device__ __forceinline__ double sel64(bool c, double x, double y) {
+    double r;
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %3, 0;\n\tselp.f64 %0, %1, %2, p;\n\t}"
+        : "=d"(r) : "d"(x), "d"(y), "r"((int)c));
+    return r;
+}
+
 __device__ inline void mat3vec(const double* A, const double* x, double* y) {
     for (int i = 0; i < 3; ++i) y[i] = fdot3(A[3 * i], x[0], A[3 * i + 1], x[1], A[3 * i + 2], x[2]);
 }
@@ -138,7 +149,7 @@ __device__ __forceinline__ double warp_quat_exp_component(const double w[3], dou
                                     c0 ? -0.5 : -1.0 / 6),
                              1.0);
         const double sh = 0.5 * p;
-        qe = c0 ? p : sh * (c == 1 ? w0 : (c == 2 ? w1 : w2));
+        qe = sel64(c0, p, sh * (c == 1 ? w0 : (c == 2 ? w1 : w2)));
     } else {
         double q4[4];
         quat_exp(w, q4);
@@ -156,8 +167,8 @@ __device__ __forceinline__ double warp_quat_mul_component(double ac, const doubl
                  a2 = __shfl_sync(0xffffffffu, ac, 2), a3 = __shfl_sync(0xffffffffu, ac, 3);
     const int p0 = c, p1 = c ^ 1, p2 = c ^ 2, p3 = c ^ 3;
     const double t3 = a3 * q[p3];
-    return fma(a0, q[p0], fma((c == 0 || c == 2) ? -a1 : a1, q[p1],
-                              fma((c == 0 || c == 3) ? -a2 : a2, q[p2], (c == 0 || c == 1) ? -t3 : t3)));
+    return fma(a0, q[p0], fma(sel64(c == 0 || c == 2, -a1, a1), q[p1],
+                              fma(sel64(c == 0 || c == 3, -a2, a2), q[p2], sel64(c == 0 || c == 1, -t3, t3))));
 }
 
 // normalise(quat_exp(w) (x) q) with w >= 0 (the operations of quat_exp,
@@ -298,20 +309,22 @@ __device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
     }
     bool ok = true;
     double rown = 0.0;   // 1 / d_li, for this lane's row
+    __syncwarp();
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         const double d = __shfl_sync(0xffffffffu, a, tri6(j, j));
         ok = ok && pivot_ok(d);
         const double rj = rcp64(d);
-        if (li == j) rown = rj;
+        rown = sel64(li == j, rj, rown);
         const bool below = li > j;                             // rows that column j updates
         const double aij = __shfl_sync(0xffffffffu, a, below ? tri6(li, j) : 0);
         const int src_m = lm == 6 ? 21 + j : (lm > j ? tri6(lm, j) : 0);
         const double amj = __shfl_sync(0xffffffffu, a, src_m);
         const double lij = aij * rj;
         const double upd = fma(-lij, amj, a);
-        if (below && lm == j) a = lij;                         // the factor L_ij, kept for the back substitution
-        else if (below && lm > j) a = upd;                     // trailing entry (lm <= li) or right-hand side (lm = 6)
+        // the factor L_ij, kept for the back substitution; a trailing entry
+        // (lm <= li) or a right-hand side (lm = 6)
+        a = sel64(below && lm == j, lij, sel64(below && lm > j, upd, a));
     }
     // z = D^-1 y on the right-hand-side lanes
     double x = a * rown;
@@ -321,10 +334,69 @@ __device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
         const double xk = __shfl_sync(0xffffffffu, x, 21 + k);
         const double lki = __shfl_sync(0xffffffffu, a, li < k ? tri6(k, li) : 0);
         const double nx = fma(-lki, xk, x);
-        if (rhs && li < k) x = nx;
+        x = sel64(rhs && li < k, nx, x);
     }
     *pd = ok;
     return x;
+}
+
+// The prior's terms of a Gauss-Newton iterate in anchor-frame coordinates.
+// The normal equations (C^T H' C + L) dxi = -(C^T g' + L xi), with
+// C = diag(Ra^T, Ra^T J_l(xi_theta)) mapping tangent steps to anchor-frame
+// perturbations, become (H' + L') y = -(g' + m) in y = C dxi, with
+// Ci = C^-1 = diag(Ra, J_l(xi_theta)^-1 Ra), L' = Ci^T L Ci and m = Ci^T L xi;
+// then dxi = Ci y.  One warp (all 32 lanes call it) computes, from Ra (3x3
+// row-major), L (6x6) and xi: ci1 = J_l(xi_theta)^-1 Ra (9), lp = L' (36,
+// row-major) and m (6).  scratch: 69 doubles of shared memory.
+__device__ __forceinline__ void warp_gn_prior_terms(const double* Ra, const double* L, const double* xi, double* ci1,
+                                                    double* lp, double* m, double* scratch) {
+    const int lane = threadIdx.x & 31;
+    double* Ji = scratch;         // J_l^-1 (9)
+    double* Ci = scratch + 9;     // diag blocks of Ci: Ra (9), J_l^-1 Ra (9)
+    double* T = scratch + 27;     // L Ci (36)
+    double* Lx = scratch + 63;    // L xi (6)
+    if (lane < 9) Ji[lane] = so3_jl_inv_entry(xi + 3, lane / 3, lane % 3);
+    else if (lane < 18) Ci[lane - 9] = Ra[lane - 9];
+    __syncwarp();
+    if (lane < 6) {
+        double lx = 0.0;
+        for (int k = 0; k < 6; ++k) lx = fma(L[6 * lane + k], xi[k], lx);
+        Lx[lane] = lx;
+    } else if (lane >= 8 && lane < 17) {   // J_l^-1 Ra
+        const int e = lane - 8, i = e / 3, j = e % 3;
+        const double v = fdot3(Ji[3 * i], Ra[j], Ji[3 * i + 1], Ra[3 + j], Ji[3 * i + 2], Ra[6 + j]);
+        Ci[9 + e] = v;
+        ci1[e] = v;
+    }
+    __syncwarp();
+    // T[k][j] = sum over the block of j: L[k][3 bj + l] Ci_bj[l][jj]; lanes 4..9 of the
+    // second round: m_i = sum over the block of i: Ci_bi[k][ii] (L xi)[3 bi + k]
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+        const int e = lane + 32 * round;
+        const bool tm = e < 36, mm = round == 1 && lane >= 4 && lane < 10;
+        const int k = tm ? e / 6 : 0, j = tm ? e % 6 : 0, bj = j / 3, jj = j % 3;
+        const int i = mm ? lane - 4 : 0, bi = i / 3, ii = i % 3;
+        const double* Cb = Ci + 9 * (mm ? bi : bj);
+        const double a0 = mm ? Cb[ii] : L[6 * k + 3 * bj], a1 = mm ? Cb[3 + ii] : L[6 * k + 3 * bj + 1],
+                     a2 = mm ? Cb[6 + ii] : L[6 * k + 3 * bj + 2];
+        const double c0 = mm ? Lx[3 * bi] : Cb[jj], c1 = mm ? Lx[3 * bi + 1] : Cb[3 + jj],
+                     c2 = mm ? Lx[3 * bi + 2] : Cb[6 + jj];
+        const double v = fdot3(a0, c0, a1, c1, a2, c2);
+        if (tm) T[e] = v;
+        else if (mm) m[i] = v;
+    }
+    __syncwarp();
+    // L' = Ci^T T: L'[i][j] = sum over the block of i: Ci_bi[k][ii] T[3 bi + k][j]
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+        const int e = lane + 32 * round;
+        if (round == 1 && e >= 36) break;
+        const int i = e / 6, j = e % 6, bi = i / 3, ii = i % 3;
+        const double* Cb = Ci + 9 * bi;
+        lp[e] = fdot3(Cb[ii], T[6 * (3 * bi) + j], Cb[3 + ii], T[6 * (3 * bi + 1) + j], Cb[6 + ii],
+                      T[6 * (3 * bi + 2) + j]);
+    }
 }
 
 // Block-cooperative inverse of an N x N SPD matrix (A and Ainv in shared

@@ -85,11 +85,13 @@ struct DevState {
     double ne_out[80];
     // render-adjoint pose gradient (world-frame perturbation)
     double grad_pose[6];
-    // Gauss-Newton tangent map of the current iterate, ready for the next
-    // pass's finish: C0 = R_a^T, C1 = R_a^T J_l(xi_theta) (3x3 each), and L xi
-    // (L = prior pose precision)
-    double gn_C[18];
-    double gn_Lxi[6];
+    // The prior's terms of the current Gauss-Newton iterate in anchor-frame
+    // coordinates (linalg64.cuh, warp_gn_prior_terms), ready for the next
+    // pass's finish: Ci = diag(R_a, J_l(xi_theta)^-1 R_a) (two 3x3 blocks),
+    // L' = Ci^T L Ci and m = Ci^T L xi (L = prior pose precision)
+    double gn_Ci[18];
+    double gn_Lp[36];
+    double gn_m[6];
     // constants of one localisation for the FP32 matrices of each iterate:
     // q0 = conj(q_anchor) (x) q_prior (the rotation Ra^T R_prior) and
     // b0 = Ra^T (t_prior - t_anchor)

@@ -233,29 +233,17 @@ __device__ __forceinline__ void prep_mats_warp(DevState* dev, int kind, const Po
             // t[3] and q[4] are contiguous: the state mean's pose
             const double* anchor = kind == PREP_REL_NEXT ? dev->t : dev->anchor_pose;
             warp_mats_rel(dev->cur_pose, anchor, dev->rel);
-            // C0 = Ra^T, C1 = Ra^T J_l(xi_theta): lanes 0..8 hold Ra entries,
-            // lanes 9..17 J_l entries; lanes 18..23 L xi
+            // Ra (lanes 0..8), then the prior's terms of the iterate in anchor-frame
+            // coordinates
             const double* qa = anchor + 3;
-            const int e = lane < 9 ? lane : (lane < 18 ? lane - 9 : 0);
-            const double ra = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], e);
-            const double jl = so3_jl_entry(dev->xi + 3, e / 3, e % 3);
-            const double v = lane < 9 ? ra : jl;
-            const int i = e / 3, j = e % 3;
-            const double ra_i0 = __shfl_sync(0xffffffffu, v, i), ra_i1 = __shfl_sync(0xffffffffu, v, 3 + i),
-                         ra_i2 = __shfl_sync(0xffffffffu, v, 6 + i);
-            const double jl_0j = __shfl_sync(0xffffffffu, v, 9 + j), jl_1j = __shfl_sync(0xffffffffu, v, 12 + j),
-                         jl_2j = __shfl_sync(0xffffffffu, v, 15 + j);
-            const double c0 = __shfl_sync(0xffffffffu, v, 3 * j + i);
+            const double v = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], lane < 9 ? lane : 0);
+            __shared__ double s_ra[9], s_scr[69];
             if (lane < 9) {
-                dev->gn_C[lane] = c0;
-                dev->gn_C[9 + lane] = fdot3(ra_i0, jl_0j, ra_i1, jl_1j, ra_i2, jl_2j);
+                s_ra[lane] = v;
+                dev->gn_Ci[lane] = v;
             }
-            if (lane >= 18 && lane < 24) {
-                const int r = lane - 18;
-                double lx = 0.0;
-                for (int k = 0; k < 6; ++k) lx = fma(dev->prec_pp[6 * r + k], dev->xi[k], lx);
-                dev->gn_Lxi[r] = lx;
-            }
+            __syncwarp();
+            warp_gn_prior_terms(s_ra, dev->prec_pp, dev->xi, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, s_scr);
             // the localisation's constants: q0 = conj(q_anchor) (x) q_prior on
             // lanes 24..27, b0 = Ra^T (t_prior - t_anchor) on lanes 28..30
             const int c = lane & 3;

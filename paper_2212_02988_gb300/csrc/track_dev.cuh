@@ -99,7 +99,8 @@ __device__ __forceinline__ void accumulate(float* acc, const float J[6], float r
 
 // The FP64 state the finish reads, slot e of the staging array: prec_pp
 // 0..35, xi 36..41, anchor 42..48, pq 49..52, pt 53..55; Gauss-Newton also
-// the tangent map C 56..73, L xi 74..79, q0 80..83 and b0 84..86; Laplace also D 56..91, the pose
+// the prior's anchor-frame terms Ci 56..73, L' 74..109, m 110..115, and q0
+// 116..119, b0 120..122; Laplace also D 56..91, the pose
 // block of the previous covariance 92..127, cov_vel 128..163, pv 164..166,
 // pw 167..169.  nullptr past the mode's last slot.
 template <int MODE>
@@ -110,10 +111,11 @@ __device__ __forceinline__ const double* stage_src(const DevState* dev, int e) {
     if (e < 53) return dev->pq + (e - 49);
     if (e < 56) return dev->pt + (e - 53);
     if (MODE == TRACK_GN) {
-        if (e < 74) return dev->gn_C + (e - 56);
-        if (e < 80) return dev->gn_Lxi + (e - 74);
-        if (e < 84) return dev->gn_q0 + (e - 80);
-        if (e < 87) return dev->gn_b0 + (e - 84);
+        if (e < 74) return dev->gn_Ci + (e - 56);
+        if (e < 110) return dev->gn_Lp + (e - 74);
+        if (e < 116) return dev->gn_m + (e - 110);
+        if (e < 120) return dev->gn_q0 + (e - 116);
+        if (e < 123) return dev->gn_b0 + (e - 120);
     }
     if (MODE == TRACK_LAPLACE) {
         if (e < 92) return dev->D + (e - 56);
@@ -418,7 +420,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         const double re = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], tid < 9 ? tid : 0);
         if (tid < 9) Ra[tid] = re;
     }
-    if (L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
+    if (MODE != TRACK_GN && L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
         const int e = tid - 32;
         int i = 0, r = e;
         while (r >= 6 - i) { r -= 6 - i; ++i; }
@@ -432,7 +434,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         const int j = i + r;
         sm[2][6 * i + j] = sm[2][6 * j + i] = S[L::oHT + e];
     }
-    __syncthreads();
+    if (MODE != TRACK_GN) __syncthreads();   // (the Gauss-Newton finish reads S directly)
     double* Hw = sm[3];
     double* Htw = sm[4];
     if (MODE != TRACK_GN) {
@@ -462,44 +464,22 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (MODE == TRACK_GN) {
         // In the anchor frame J' = J T^T... the tangent step dxi maps to the
         // anchor-frame perturbation through C = T M = diag(Ra^T, Ra^T J_l(xi_theta)),
-        // so (M^T H M + L) = C^T H' C + L and M^T g = C^T g'.  C and L xi of the
-        // current iterate were prepared by the previous pass's finish (or by the
-        // pose matrices before the first pass), off this pass's critical path.
-        const double* Cm = st + 56;   // 3x3 blocks: C0 = Ra^T, C1 = Ra^T J_l
-        const double* Lx = st + 74;
-        double* T1 = sx[1];
-        double* Hx = sx[2];
-        double* gx = sx[3];
+        // so the step solves (C^T H' C + L) dxi = -(C^T g' + L xi).  In y = C dxi
+        // this is (H' + L') y = -(g' + m) with L' = Ci^T L Ci, m = Ci^T L xi and
+        // Ci = C^-1 = diag(Ra, J_l^-1 Ra), and dxi = Ci y (warp_gn_prior_terms):
+        // the sums enter the FP64 solve with one addition each.  Ci, L' and m of
+        // the current iterate were prepared by the previous pass's finish (or
+        // with the start matrices before the first pass), off this pass's
+        // critical path.
+        const double* Ci = st + 56;   // 3x3 blocks: Ra, J_l^-1 Ra
+        const double* Lp = st + 74;
+        const double* mv = st + 110;
         double* xn = sx[4];
-        double* Jn = sx[5];
         __shared__ int s_pd;
-        if (tid < 36) {   // T1 = H' C  (C block diagonal)
-            const int i = tid / 6, j = tid % 6, bj = j / 3, jj = j % 3;
-            const double* Cb = Cm + 9 * bj;
-            T1[tid] = fdot3(sm[1][6 * i + 3 * bj], Cb[jj], sm[1][6 * i + 3 * bj + 1], Cb[3 + jj],
-                            sm[1][6 * i + 3 * bj + 2], Cb[6 + jj]);
-        } else if (tid >= 64 && tid < 70) {   // gx = -(C^T g' + L xi)
-            const int i = tid - 64, bi = i / 3, ii = i % 3;
-            const double* Cb = Cm + 9 * bi;
-            const double* gp = S + L::oG + 3 * bi;
-            gx[i] = -fma(Cb[ii], gp[0], fma(Cb[3 + ii], gp[1], fma(Cb[6 + ii], gp[2], Lx[i])));
-        }
-        __syncthreads();
-        if (tid < 36) {   // Hx = C^T T1 + L, symmetrised
-            const int i = tid / 6, j = tid % 6, bi = i / 3, ii = i % 3, bj = j / 3, jj = j % 3;
-            const double* Ci = Cm + 9 * bi;
-            const double* Cj = Cm + 9 * bj;
-            const double a1 = fdot3(Ci[ii], T1[6 * (3 * bi) + j], Ci[3 + ii], T1[6 * (3 * bi + 1) + j],
-                                    Ci[6 + ii], T1[6 * (3 * bi + 2) + j]);
-            const double a2 = fdot3(Cj[jj], T1[6 * (3 * bj) + i], Cj[3 + jj], T1[6 * (3 * bj + 1) + i],
-                                    Cj[6 + jj], T1[6 * (3 * bj + 2) + i]);
-            Hx[tid] = 0.5 * (a1 + a2) + 0.5 * (st[tid] + st[6 * j + i]);
-        }
-        __syncthreads();
         if (warp == 0) {
-            // The 6x6 FP64 solve by the square-root-free Cholesky factorisation
-            // on one warp (warp_ldlt6_solve): lane e < 21 brings entry (i, j) of
-            // Hx's lower triangle, lane 21 + i the right-hand side gx_i.
+            // lane e < 21: entry (li, lm) of the lower triangle of H' + L'; lane
+            // 21 + li: -(g' + m)_li (the layout of warp_ldlt6_solve).  H' is stored
+            // as its upper triangle, row-major: (r, c), r <= c, at 5 r - r (r - 1) / 2 + c.
             int li = 0, lm = 0;
             if (lane < 21) {
 #pragma unroll
@@ -508,10 +488,22 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                 lm = lane - tri6(li, 0);
             }
             const bool rhs = lane >= 21 && lane < 27;
-            const double a = rhs ? gx[lane - 21] : Hx[6 * li + lm];
+            const int ri = rhs ? lane - 21 : 0;
+            // one addition for every lane (operands selected by index), the
+            // right-hand side negated by a select
+            const double s0 = S[rhs ? L::oG + ri : L::oH + 5 * lm - lm * (lm - 1) / 2 + li];
+            const double s1 = rhs ? mv[ri] : Lp[6 * li + lm];
+            const double sum = s0 + s1;
+            const double a = sel64(rhs, -sum, sum);
             bool pd;
-            const double x = warp_ldlt6_solve(a, &pd);
-            if (pd && rhs) xn[lane - 21] = st[36 + lane - 21] + x;
+            const double y = warp_ldlt6_solve(a, &pd);
+            // dxi = Ci y on lanes 21..26: row ri of block bi of Ci against y's block bi
+            const int bi = ri / 3, ii = ri % 3;
+            const double y0 = __shfl_sync(0xffffffffu, y, 21 + 3 * bi), y1 = __shfl_sync(0xffffffffu, y, 22 + 3 * bi),
+                         y2 = __shfl_sync(0xffffffffu, y, 23 + 3 * bi);
+            const double* Cb = Ci + 9 * bi;
+            const double dx = fdot3(Cb[3 * ii], y0, Cb[3 * ii + 1], y1, Cb[3 * ii + 2], y2);
+            if (pd && rhs) xn[ri] = st[36 + ri] + dx;
             if (lane == 0) s_pd = pd;
         }
         __syncthreads();
@@ -529,16 +521,16 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             const int r = lane < 3 ? lane : (tl ? lane - 9 : 0);
             const bool sq = lane == 3;
             const double* v = tl ? xn : xn + 3;
-            const double d = fdot3(sq ? v[0] : Cm[3 * r], v[0], sq ? v[1] : Cm[3 * r + 1], v[1],
-                                   sq ? v[2] : Cm[3 * r + 2], v[2]);
+            const double d = fdot3(sq ? v[0] : Ci[r], v[0], sq ? v[1] : Ci[3 + r], v[1],
+                                   sq ? v[2] : Ci[6 + r], v[2]);
             const double w[3] = {__shfl_sync(0xffffffffu, d, 0), __shfl_sync(0xffffffffu, d, 1),
                                  __shfl_sync(0xffffffffu, d, 2)};
             const double th2 = __shfl_sync(0xffffffffu, d, 3);
-            const double qr = warp_quat_mul_component(warp_quat_exp_component(w, th2), st + 80);
+            const double qr = warp_quat_mul_component(warp_quat_exp_component(w, th2), st + 116);
             const double q0 = __shfl_sync(0xffffffffu, qr, 0), q1 = __shfl_sync(0xffffffffu, qr, 1),
                          q2 = __shfl_sync(0xffffffffu, qr, 2), q3 = __shfl_sync(0xffffffffu, qr, 3);
             const double me = quat_R_entry_rn(q0, q1, q2, q3, lane < 9 ? lane : 0);
-            const double be = st[84 + r] + d;
+            const double be = st[120 + r] + d;
             if (lane < 9) dev->rel[lane] = (float)me;
             else if (tl) dev->rel[lane] = (float)be;
         } else if (warp == 1) {   // the FP64 pose of the new iterate (the state mean after the last pass)
@@ -546,15 +538,8 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             if (lane < 4) dev->cur_pose[3 + lane] = qn;
             if (lane < 3) dev->cur_pose[lane] = st[53 + lane] + xn[lane];
             if (lane < 6) dev->xi[lane] = xn[lane];
-        } else if (warp == 2 && lane < 9) {   // meanwhile: the tangent map of the new iterate
-            const int i = lane / 3, j = lane % 3;
-            Jn[lane] = so3_jl_entry(xn + 3, i, j);
-            __syncwarp(0x1ffu);
-            dev->gn_C[9 + lane] = fdot3(Cm[3 * i], Jn[j], Cm[3 * i + 1], Jn[3 + j], Cm[3 * i + 2], Jn[6 + j]);
-        } else if (warp == 3 && lane < 6) {
-            double lx = 0.0;
-            for (int k = 0; k < 6; ++k) lx = fma(st[6 * lane + k], xn[k], lx);
-            dev->gn_Lxi[lane] = lx;
+        } else if (warp == 2) {   // meanwhile: the prior's anchor-frame terms of the new iterate
+            warp_gn_prior_terms(Ci, st, xn, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, &sm[2][0]);
         }
         return;
     }
