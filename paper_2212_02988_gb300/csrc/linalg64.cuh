@@ -340,6 +340,61 @@ __device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
     return x;
 }
 
+// The inverse of a 6x6 symmetric positive definite A on one warp: the
+// factorisation A = L D L^T of warp_ldlt6_solve (lane e < 21 brings entry
+// (i, j), e = tri6(i, j), of A's lower triangle; the other lanes' values are
+// not used), then lane c < 6 solves L D L^T x = e_c (forward substitution,
+// D^-1, back substitution), so that x[0..5] of lane c is column c of A^-1
+// (other lanes: junk).  *pd: every pivot passed pivot_ok (every lane).  All
+// 32 lanes must call it.
+__device__ __forceinline__ void warp_spd6_inverse(double a, bool* pd, double x[6]) {
+    const int lane = threadIdx.x & 31;
+    const bool tri = lane < 21;
+    int li = 5, lm = 6;
+    if (tri) {
+        li = 0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i)
+            if (lane >= tri6(i, 0)) li = i;
+        lm = lane - tri6(li, 0);
+    }
+    bool ok = true;
+    double r[6];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const double d = __shfl_sync(0xffffffffu, a, tri6(j, j));
+        ok = ok && pivot_ok(d);
+        r[j] = rcp64(d);
+        const bool below = tri && li > j;
+        const double aij = __shfl_sync(0xffffffffu, a, below ? tri6(li, j) : 0);
+        const double amj = __shfl_sync(0xffffffffu, a, below && lm > j ? tri6(lm, j) : 0);
+        const double lij = aij * r[j];
+        const double upd = fma(-lij, amj, a);
+        a = sel64(below && lm == j, lij, sel64(below && lm > j, upd, a));
+    }
+    // column c = lane of A^-1; L_ik (i > k) is in lane tri6(i, k)
+    const int c = lane < 6 ? lane : 0;
+    double y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double s = sel64(i == c, 1.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < i; ++k) s = fma(-__shfl_sync(0xffffffffu, a, tri6(i, k)), y[k], s);
+        y[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] *= r[i];
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) s = fma(-__shfl_sync(0xffffffffu, a, tri6(k, i)), x[k], s);
+        x[i] = s;
+    }
+    *pd = ok;
+}
+
 // The prior's terms of a Gauss-Newton iterate in anchor-frame coordinates.
 // The normal equations (C^T H' C + L) dxi = -(C^T g' + L xi), with
 // C = diag(Ra^T, Ra^T J_l(xi_theta)) mapping tangent steps to anchor-frame
@@ -347,16 +402,22 @@ __device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
 // Ci = C^-1 = diag(Ra, J_l(xi_theta)^-1 Ra), L' = Ci^T L Ci and m = Ci^T L xi;
 // then dxi = Ci y.  One warp (all 32 lanes call it) computes, from Ra (3x3
 // row-major), L (6x6) and xi: ci1 = J_l(xi_theta)^-1 Ra (9), lp = L' (36,
-// row-major) and m (6).  scratch: 69 doubles of shared memory.
+// row-major), m (6) and ji = J_l(xi_theta)^-1 (9).  scratch: 69 doubles of
+// shared memory.
 __device__ __forceinline__ void warp_gn_prior_terms(const double* Ra, const double* L, const double* xi, double* ci1,
-                                                    double* lp, double* m, double* scratch) {
+                                                    double* lp, double* m, double* ji, double* scratch) {
     const int lane = threadIdx.x & 31;
     double* Ji = scratch;         // J_l^-1 (9)
     double* Ci = scratch + 9;     // diag blocks of Ci: Ra (9), J_l^-1 Ra (9)
     double* T = scratch + 27;     // L Ci (36)
     double* Lx = scratch + 63;    // L xi (6)
-    if (lane < 9) Ji[lane] = so3_jl_inv_entry(xi + 3, lane / 3, lane % 3);
-    else if (lane < 18) Ci[lane - 9] = Ra[lane - 9];
+    if (lane < 9) {
+        const double v = so3_jl_inv_entry(xi + 3, lane / 3, lane % 3);
+        Ji[lane] = v;
+        ji[lane] = v;
+    } else if (lane < 18) {
+        Ci[lane - 9] = Ra[lane - 9];
+    }
     __syncwarp();
     if (lane < 6) {
         double lx = 0.0;

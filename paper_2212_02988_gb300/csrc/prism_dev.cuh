@@ -92,6 +92,7 @@ struct DevState {
     double gn_Ci[18];
     double gn_Lp[36];
     double gn_m[6];
+    double gn_Ji[9];           // J_l(xi_theta)^-1 of the current iterate
     // constants of one localisation for the FP32 matrices of each iterate:
     // q0 = conj(q_anchor) (x) q_prior (the rotation Ra^T R_prior) and
     // b0 = Ra^T (t_prior - t_anchor)

@@ -243,7 +243,8 @@ __device__ __forceinline__ void prep_mats_warp(DevState* dev, int kind, const Po
                 dev->gn_Ci[lane] = v;
             }
             __syncwarp();
-            warp_gn_prior_terms(s_ra, dev->prec_pp, dev->xi, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, s_scr);
+            warp_gn_prior_terms(s_ra, dev->prec_pp, dev->xi, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, dev->gn_Ji,
+                                s_scr);
             // the localisation's constants: q0 = conj(q_anchor) (x) q_prior on
             // lanes 24..27, b0 = Ra^T (t_prior - t_anchor) on lanes 28..30
             const int c = lane & 3;

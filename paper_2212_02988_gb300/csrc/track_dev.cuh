@@ -102,7 +102,8 @@ __device__ __forceinline__ void accumulate(float* acc, const float J[6], float r
 // the prior's anchor-frame terms Ci 56..73, L' 74..109, m 110..115, and q0
 // 116..119, b0 120..122; Laplace also D 56..91, the pose
 // block of the previous covariance 92..127, cov_vel 128..163, pv 164..166,
-// pw 167..169.  nullptr past the mode's last slot.
+// pw 167..169, and of the final iterate L' 170..205, J_l^-1 206..214 and
+// Ra 215..223.  nullptr past the mode's last slot.
 template <int MODE>
 __device__ __forceinline__ const double* stage_src(const DevState* dev, int e) {
     if (e < 36) return dev->prec_pp + e;
@@ -123,10 +124,13 @@ __device__ __forceinline__ const double* stage_src(const DevState* dev, int e) {
         if (e < 164) return dev->cov_vel + (e - 128);
         if (e < 167) return dev->pv + (e - 164);
         if (e < 170) return dev->pw + (e - 167);
+        if (e < 206) return dev->gn_Lp + (e - 170);
+        if (e < 215) return dev->gn_Ji + (e - 206);
+        if (e < 224) return dev->gn_Ci + (e - 215);
     }
     return nullptr;
 }
-constexpr int kStage = 176;
+constexpr int kStage = 224;
 
 // Asynchronous global -> shared copies (no registers held, no stall until
 // the wait).
@@ -307,8 +311,10 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (tid < kStage) {
         const double* src = stage_src<MODE>(dev, tid);
         if (src) cp_async(&st[tid], src, 8);
-        else if (MODE == TRACK_LAPLACE && tid == 170) cp_async(&s_nloc, &dev->n_localised, 4);
-        else if (MODE == TRACK_LAPLACE && tid == 171) cp_async(&s_flags, &dev->flags, 4);
+    } else if (MODE == TRACK_LAPLACE && tid == kStage) {
+        cp_async(&s_nloc, &dev->n_localised, 4);
+    } else if (MODE == TRACK_LAPLACE && tid == kStage + 1) {
+        cp_async(&s_flags, &dev->flags, 4);
     }
     if (tid < 12) {
         const float* mats = MODE == TRACK_EXPORT ? dev->aux : dev->rel;
@@ -415,29 +421,29 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
 
     // sm[0]: Ra; sm[1]: H' (sym); sm[2]: Ht' (sym); sm[3], sm[4]: world-frame H, Ht
     double* Ra = sm[0];
-    if (MODE != TRACK_GN && tid < 32) {   // the anchor rotation, one entry a lane
+    if (MODE == TRACK_EXPORT && tid < 32) {   // the anchor rotation, one entry a lane
         const double* qa = st + 45;
         const double re = quat_R_entry_rn(qa[0], qa[1], qa[2], qa[3], tid < 9 ? tid : 0);
         if (tid < 9) Ra[tid] = re;
     }
-    if (MODE != TRACK_GN && L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
+    if (MODE == TRACK_EXPORT && L::H && tid >= 32 && tid < 53) {   // unpack the upper triangles in parallel
         const int e = tid - 32;
         int i = 0, r = e;
         while (r >= 6 - i) { r -= 6 - i; ++i; }
         const int j = i + r;
         sm[1][6 * i + j] = sm[1][6 * j + i] = S[L::oH + e];
     }
-    if (L::HT && tid >= 64 && tid < 85) {
+    if (MODE == TRACK_EXPORT && L::HT && tid >= 64 && tid < 85) {
         const int e = tid - 64;
         int i = 0, r = e;
         while (r >= 6 - i) { r -= 6 - i; ++i; }
         const int j = i + r;
         sm[2][6 * i + j] = sm[2][6 * j + i] = S[L::oHT + e];
     }
-    if (MODE != TRACK_GN) __syncthreads();   // (the Gauss-Newton finish reads S directly)
+    if (MODE == TRACK_EXPORT) __syncthreads();   // (the Gauss-Newton and Laplace finishes read S directly)
     double* Hw = sm[3];
     double* Htw = sm[4];
-    if (MODE != TRACK_GN) {
+    if (MODE == TRACK_EXPORT) {
         if (L::H) rotate_to_world(Ra, sm[1], Hw);
         if (L::HT) rotate_to_world(Ra, sm[2], Htw);
         __syncthreads();
@@ -539,7 +545,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             if (lane < 3) dev->cur_pose[lane] = st[53 + lane] + xn[lane];
             if (lane < 6) dev->xi[lane] = xn[lane];
         } else if (warp == 2) {   // meanwhile: the prior's anchor-frame terms of the new iterate
-            warp_gn_prior_terms(Ci, st, xn, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, &sm[2][0]);
+            warp_gn_prior_terms(Ci, st, xn, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, dev->gn_Ji, &sm[2][0]);
         }
         return;
     }
@@ -556,40 +562,61 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         return;
     }
-    // Sigma = (2 Ht + Mi^T L Mi)^-1, Mi = diag(I, J_l(xi_theta)^-1)
-    double* Mi = sx[0];
-    double* T1 = sx[1];
-    double* Hl = sx[2];
-    double* Sl = sx[3];
-    double* Sp = sx[4];
-    double* Dp = sx[5];
-    double* DS = sx[6];
-    double* Lf = sx[7];
-    __shared__ double rdg[6];
-    if (tid < 64) {   // one entry a thread (warps 0 and 1)
-        const int i = tid / 6, j = tid % 6, bi = i < 3 ? 0 : i - 3, bj = j < 3 ? 0 : j - 3;
-        const double jv = so3_jl_inv_entry(st + 39, bi, bj);
-        if (tid < 36) Mi[tid] = (i < 3 || j < 3) ? (i == j ? 1.0 : 0.0) : jv;
-    }
-    __syncthreads();
-    if (tid < 36) {   // T1 = L Mi
-        const int i = tid / 6, j = tid % 6;
-        double a = 0.0;
-        for (int k = 0; k < 6; ++k) a = fma(st[6 * i + k], Mi[6 * k + j], a);
-        T1[tid] = a;
-    }
-    __syncthreads();
-    if (tid < 36) {   // Hl = 2 Ht + Mi^T T1, symmetrised
-        const int i = tid / 6, j = tid % 6;
-        double a1 = 0.0, a2 = 0.0;
-        for (int k = 0; k < 6; ++k) {
-            a1 = fma(Mi[6 * k + i], T1[6 * k + j], a1);
-            a2 = fma(Mi[6 * k + j], T1[6 * k + i], a2);
+    // Sigma = (2 Ht + Mi^T L Mi)^-1 in world-frame perturbations, Mi =
+    // diag(I, J_l(xi_theta)^-1).  With Ht = T Ht' T^T (T = diag(Ra, Ra), Ht' the
+    // anchor-frame sum) and Mi^T L Mi = T L' T^T (L' = Ci^T L Ci of the final
+    // iterate, warp_gn_prior_terms), Sigma = T (2 Ht' + L')^-1 T^T: the sums
+    // enter the FP64 inverse with one FMA each, and the inverse is rotated once.
+    const double* Lp = st + 170;
+    const double* Ji = st + 206;
+    const double* Rs = st + 215;   // Ra of the anchor
+    double* Sa = sx[0];   // (2 Ht' + L')^-1
+    double* U = sx[1];    // Sa T^T
+    double* Sp = sx[4];   // pose covariance after the EMA
+    double* Dp = sx[5];   // D' = D Mi
+    double* DS = sx[6];   // D' Sp
+    double* mats = sx[7]; // the new mean's FP32 matrices (c2w, w2c), as doubles
+    double vel = 0.0;
+    if (warp == 0) {
+        // lane e < 21: entry (li, lm) of the lower triangle of 2 Ht' + L' (Ht' as its
+        // upper triangle, row-major: (r, c), r <= c, at 5 r - r (r - 1) / 2 + c)
+        int li = 0, lm = 0;
+        if (lane < 21) {
+#pragma unroll
+            for (int i = 1; i < 6; ++i)
+                if (lane >= tri6(i, 0)) li = i;
+            lm = lane - tri6(li, 0);
         }
-        Hl[tid] = Htw[tid] + Htw[6 * j + i] + 0.5 * (a1 + a2);
+        const double a = fma(2.0, S[L::oHT + 5 * lm - lm * (lm - 1) / 2 + li], Lp[6 * li + lm]);
+        bool pd;
+        double x[6];
+        warp_spd6_inverse(a, &pd, x);
+        if (lane < 6)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Sa[6 * k + lane] = x[k];
+        if (lane == 0) s_ok = pd;
+    } else if (warp == 1) {   // meanwhile: D' = D Mi (D' = D on the translation columns)
+#pragma unroll
+        for (int round = 0; round < 2; ++round) {
+            const int e = lane + 32 * round;
+            const int i = e < 36 ? e / 6 : 0, j = e < 36 ? e % 6 : 3, jj = j < 3 ? 0 : j - 3;
+            const double* Dr = st + 56 + 6 * i;
+            const double v = fdot3(Dr[3], Ji[jj], Dr[4], Ji[3 + jj], Dr[5], Ji[6 + jj]);
+            if (e < 36) Dp[e] = sel64(j < 3, Dr[j < 3 ? j : 0], v);
+        }
+    } else if (warp == 2 && lane < 6) {   // v = vbar + D xi
+        double dv = 0.0;
+        for (int k = 0; k < 6; ++k) dv = fma(st[56 + 6 * lane + k], st[36 + k], dv);
+        vel = (lane < 3 ? st[164 + lane] : st[167 + lane - 3]) + dv;
+    } else if (warp == 3) {   // the new mean's FP32 matrices
+        double pose[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) pose[i] = dev->cur_pose[i];
+        warp_mats_c2w(pose, (float*)&mats[0]);    // 12 floats in mats[0..5]
+        warp_mats_w2c(pose, (float*)&mats[6]);    // 12 floats in mats[6..11]
     }
     __syncthreads();
-    if (!spd_inverse_block<6>(Hl, Sl, Lf, rdg, &s_ok)) {
+    if (!s_ok) {
         if (tid == 0) {
             dev->flags |= FLAG_LAPLACE_NOTPD;
             dev->rejected = 1;
@@ -598,13 +625,18 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         return;
     }
+    if (tid < 36) {   // U = Sa T^T: U[r][j] = sum_l Sa[r][3 bj + l] Ra[jj][l]
+        const int r = tid / 6, j = tid % 6, bj = j / 3, jj = j % 3;
+        U[tid] = fdot3(Sa[6 * r + 3 * bj], Rs[3 * jj], Sa[6 * r + 3 * bj + 1], Rs[3 * jj + 1], Sa[6 * r + 3 * bj + 2],
+                       Rs[3 * jj + 2]);
+    }
+    __syncthreads();
     const bool first = s_nloc == 0;
-    if (tid < 36) {   // EMA (App. F.2) and D' = D Mi
-        const int i = tid / 6, j = tid % 6;
-        Sp[tid] = first ? Sl[tid] : fma(P.ema, st[92 + tid], (1.0 - P.ema) * Sl[tid]);
-        double a = 0.0;
-        for (int k = 0; k < 6; ++k) a = fma(st[56 + 6 * i + k], Mi[6 * k + j], a);
-        Dp[tid] = a;
+    if (tid < 36) {   // the Laplace covariance T U, then the EMA (App. F.2)
+        const int i = tid / 6, j = tid % 6, bi = i / 3, ii = i % 3;
+        const double sl = fdot3(Rs[3 * ii], U[6 * (3 * bi) + j], Rs[3 * ii + 1], U[6 * (3 * bi + 1) + j], Rs[3 * ii + 2],
+                                U[6 * (3 * bi + 2) + j]);
+        Sp[tid] = first ? sl : fma(P.ema, st[92 + tid], (1.0 - P.ema) * sl);
     }
     __syncthreads();
     if (tid < 36) {   // DS = D' Sp
@@ -612,12 +644,6 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         double a = 0.0;
         for (int k = 0; k < 6; ++k) a = fma(Dp[6 * i + k], Sp[6 * k + j], a);
         DS[tid] = a;
-    } else if (tid >= 64 && tid < 70) {   // v = vbar + D xi
-        const int i = tid - 64;
-        double dv = 0.0;
-        for (int k = 0; k < 6; ++k) dv = fma(st[56 + 6 * i + k], st[36 + k], dv);
-        if (i < 3) dev->v[i] = st[164 + i] + dv;
-        else dev->w[i - 3] = st[167 + i - 3] + dv;
     }
     __syncthreads();
     if (tid < 144) {   // cov = [[Sp, Sp D'^T], [D' Sp, D' Sp D'^T + S_vel]]
@@ -640,14 +666,17 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         dev->cov[tid] = c;
     }
-    if (warp == 0) {   // the new mean and its FP32 matrices, one entry a lane
-        double pose[7];
-#pragma unroll
-        for (int i = 0; i < 7; ++i) pose[i] = dev->cur_pose[i];
-        warp_mats_c2w(pose, dev->c2w);
-        warp_mats_w2c(pose, dev->w2c);
-        if (lane < 3) dev->t[lane] = pose[lane];
-        if (lane < 4) dev->q[lane] = pose[3 + lane];
+    if (warp == 2 && lane < 6) {
+        if (lane < 3) dev->v[lane] = vel;
+        else dev->w[lane - 3] = vel;
+    } else if (warp == 5) {   // the new mean, its FP32 matrices, the count
+        const float* m32 = (const float*)mats;
+        if (lane < 12) {
+            dev->c2w[lane] = m32[lane];
+            dev->w2c[lane] = m32[12 + lane];
+        }
+        if (lane < 3) dev->t[lane] = dev->cur_pose[lane];
+        if (lane < 4) dev->q[lane] = dev->cur_pose[3 + lane];
         if (lane == 0) {
             dev->n_localised += 1;
             dev->rejected = 0;
