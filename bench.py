@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="length of the serving run (default 120 with --serve, 12 inside the default run)")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving run of the default bench")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the bf16-map sub-run (configuration 3)")
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
     return ap.parse_args(argv)
 
@@ -140,17 +141,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def render_source_hash():
+# the sources each profiled kernel is built from (a committed ncu summary
+# counts only while their hash matches)
+KERNEL_SOURCES = {"k_render": ("render.cu", "render_dev.cuh", "prism_dev.cuh"),
+                  "k_track_gn": ("track.cu", "track_dev.cuh", "prism_dev.cuh", "linalg64.cuh")}
+
+
+def source_hash(kernel: str = "k_render"):
     h = hashlib.sha256()
-    for f in ("render.cu", "render_dev.cuh", "prism_dev.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2212_02988_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per render launch from the committed ncu summary, if it
-    was taken on the current render source; else None."""
-    path = os.path.join(ROOT, "profiles", f"k_render_{workload}.md")
+def render_source_hash():
+    return source_hash("k_render")
+
+
+def profiled_traffic(workload: str, kernel: str = "k_render"):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, if
+    it was taken on the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -158,12 +169,90 @@ def profiled_traffic(workload: str):
         if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch")):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256") != render_source_hash():
+    if vals.get("source_sha256") != source_hash(kernel):
         return None
     try:
         return int(float(vals["dram_bytes_per_launch"]))
     except (KeyError, ValueError):
         return None
+
+
+def timed_filter(cfg, s1, maps, w, D, C, imus, K, W, T, local_rank):
+    """A filter on the device-resident frames: W warm-up steps (with the
+    render's detail counters on), K timed steps bracketed by a barrier and a
+    device synchronisation, clocks sampled meanwhile, then T steps with the
+    library's phase timers on (their events break the launch overlap
+    between phases, so they stay off in the timed loop).  Returns the
+    filter (still open) and the measurements."""
+    import torch
+    from paper_2212_02988_gb300 import Filter
+    F = Filter(cfg, s1, device=local_rank)
+    F.map_load(*maps)
+    F.step(None, w.dt, D[0], C[0])
+    F.set_detail_counters(True)
+    st_w0 = F.stats()
+    for i in range(1, 1 + W):
+        F.step(imus[i], w.dt, D[i], C[i])
+    st_w1 = F.stats()
+    F.set_detail_counters(False)
+    st0 = F.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    gc.collect()
+    gc.disable()   # as timeit does: no cyclic collection pauses inside the timed loops
+    sampler.start()
+    e_start.record()
+    for j in range(K):
+        i = 1 + W + j
+        ev[j][0].record()
+        F.step(imus[i], w.dt, D[i], C[i])
+        ev[j][1].record()
+    e_end.record()
+    torch.cuda.synchronize()
+    gc.enable()
+    barrier()
+    clocks = sampler.stop()
+    st1 = F.stats()
+    F.set_timing(True)
+    F.timing_reset()
+    for j in range(T):
+        i = 1 + W + K + j
+        F.step(imus[i], w.dt, D[i], C[i])
+    torch.cuda.synchronize()
+    tm = F.timing()
+    F.set_timing(False)
+    return F, {"total_ms": e_start.elapsed_time(e_end), "step_ms": [a.elapsed_time(b) for a, b in ev],
+               "tm": tm, "clocks": clocks, "st0": st0, "st1": st1, "st_w0": st_w0, "st_w1": st_w1}
+
+
+def render_bytes(run, K, storage):
+    """Render byte counts per launch: G (logical gathered voxel bytes of the
+    evaluated samples) and U (per-ray unique bytes, from the fraction of
+    distinct corners counted in the warm-up steps)."""
+    st0, st1, w0, w1 = run["st0"], run["st1"], run["st_w0"], run["st_w1"]
+    d = {k: st1[k] - st0[k] for k in st1}
+    warm = {k: w1[k] - w0[k] for k in w1}
+    b = 2 if storage == "bf16" else 4
+    samp, hits = d["render_samples"] / max(K, 1), d["render_hits"] / max(K, 1)
+    u_ratio = warm["render_unique_corners"] / max(warm["render_samples"] * 8, 1)
+    return {"rays": d["render_rays"] / max(K, 1), "samples": samp, "hits": hits, "bytes_per_corner": b,
+            "G": samp * 8 * b + hits * 2 * 8 * 3 * b, "U": samp * 8 * b * u_ratio + hits * 8 * 3 * b}
+
+
+def gn_pass_ms(tm, n_gn):
+    """The Gauss-Newton pass's live duration: the localisation phase less its
+    Laplace pass, over the passes (the first also evaluates the depth
+    validity)."""
+    return (tm["localise_ms"] / max(tm["localise_n"], 1) - tm["laplace_ms"] / max(tm["laplace_n"], 1)) / n_gn
+
+
+# the localisation pass's algorithmic bytes per observed pixel (observation
+# 16 B: depth and colour; anchor gathers 56 B: the nearest pixel's normal and
+# depth, the bilinear colour taps)
+GN_BYTES_PER_PIXEL = 72
 
 
 # ------------------------------------------------------------- our arm
@@ -196,49 +285,9 @@ def run_ours(args, rank, world, local_rank):
     s1 = make_state(seq.pose7(0), seq.velocity(0))
 
     # ---- device-resident run ----
-    F = Filter(cfg, s1, device=local_rank)
-    F.map_load(*maps)
-    F.step(None, w.dt, D[0], C[0])
-    F.set_detail_counters(True)
-    st_w0 = F.stats()
-    for i in range(1, 1 + W):
-        F.step(imus[i], w.dt, D[i], C[i])
-    st_w1 = F.stats()
-    F.set_detail_counters(False)
-    st0 = F.stats()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local_rank)
-    barrier()
-    torch.cuda.synchronize()
-    gc.collect()
-    gc.disable()   # as timeit does: no cyclic collection pauses inside the timed loops
-    sampler.start()
-    e_start.record()
-    for j in range(K):
-        i = 1 + W + j
-        ev[j][0].record()
-        F.step(imus[i], w.dt, D[i], C[i])
-        ev[j][1].record()
-    e_end.record()
-    torch.cuda.synchronize()
-    gc.enable()
-    barrier()
-    clocks = sampler.stop()
-    total_ms = e_start.elapsed_time(e_end)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    st1 = F.stats()
-    # Phase breakdown on the next T frames: the timers record events between
-    # the phases, which also breaks the launch overlap there, so they stay off
-    # in the timed loop.
-    F.set_timing(True)
-    F.timing_reset()
-    for j in range(T):
-        i = 1 + W + K + j
-        F.step(imus[i], w.dt, D[i], C[i])
-    torch.cuda.synchronize()
-    tm = F.timing()
-    F.set_timing(False)
+    F, run = timed_filter(cfg, s1, maps, w, D, C, imus, K, W, T, local_rank)
+    total_ms, step_ms, tm, clocks = run["total_ms"], run["step_ms"], run["tm"], run["clocks"]
+    st0, st1, st_w0, st_w1 = run["st0"], run["st1"], run["st_w0"], run["st_w1"]
     elapsed, frames = combine_over_ranks(total_ms / 1000.0, float(K))
     # render adjoint (config with the differentiation path): timed separately,
     # at the final state's pose, with resident upstream gradients
@@ -364,24 +413,57 @@ def run_ours(args, rank, world, local_rank):
         Fa.close()
 
     d_st = {k: st1[k] - st0[k] for k in st1}
-    rays_per = d_st["render_rays"] / max(K, 1)      # one anchor render per timed step
-    samp_per = d_st["render_samples"] / max(K, 1)
-    hits_per = d_st["render_hits"] / max(K, 1)
+    rb = render_bytes(run, K, storage)
+    rays_per, samp_per, G, U, b = rb["rays"], rb["samples"], rb["G"], rb["U"], rb["bytes_per_corner"]
     render_ms = tm["render_ms"] / max(tm["render_n"], 1)
-    b = 2 if storage == "bf16" else 4
-    G = samp_per * 8 * b + hits_per * 2 * 8 * 3 * b              # logical gathered voxel bytes
-    warm = {k: st_w1[k] - st_w0[k] for k in st_w1}
-    u_ratio = warm["render_unique_corners"] / max(warm["render_samples"] * 8, 1)
-    U = samp_per * 8 * b * u_ratio + hits_per * 8 * 3 * b         # per-ray unique bytes (estimate from the counted fraction)
     peak, peak_kind = measured_peaks()
     achieved_G = G / (render_ms * 1e-3) / 1e9
-    achieved = U / (render_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.workload)
-    # localisation passes: per pass the observed frame (depth 4 B + mask 1 B + colour 12 B per
-    # pixel) and the packed anchor (2 x 16 B per pixel) are the bytes the method must read
+    achieved_U = U / (render_ms * 1e-3) / 1e9
+    # the dominant kernel by device time: the Gauss-Newton pass
     npx = w.width * w.height
-    loc_bytes = (cfg.n_gn + 1) * npx * (4 + 1 + 12 + 32)
+    gn_ms = gn_pass_ms(tm, cfg.n_gn)
+    gn_bytes = GN_BYTES_PER_PIXEL * npx
     loc_ms = tm["localise_ms"] / max(tm["localise_n"], 1)
+
+    # bf16 map storage (configuration 3: the same 256^3 map and 640x480 frames)
+    bf16 = None
+    if not args.no_bf16 and storage == "f32" and K > 0:
+        wb = synth.PRESETS[w.name + "_bf16"] if (w.name + "_bf16") in synth.PRESETS else None
+        if wb is not None:
+            Kb, Tb = min(K, 200), min(T, 40)
+            nb = 1 + W + Kb + Tb
+            sb = synth.Sequence(wb, n_frames=nb, seed=wb.seed + 100 * rank)
+            mb = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in sb.settled_map()]
+            Db, Cb = [], []
+            for c0 in range(0, nb, 64):
+                d, c = raycast_frames(sb, range(c0, min(nb, c0 + 64)), dev)
+                Db.append(d)
+                Cb.append(c)
+            Db, Cb = torch.cat(Db), torch.cat(Cb)
+            ib = [None] + [sb.imu_window(i) for i in range(1, nb)]
+            cfgb = config(wb.n, wb.extent, wb.width, wb.height, storage="bf16")
+            Fb, rbn = timed_filter(cfgb, make_state(sb.pose7(0), sb.velocity(0)), mb, wb, Db, Cb, ib, Kb, W, Tb,
+                                   local_rank)
+            Fb.close()
+            tb = rbn["tm"]
+            rbb = render_bytes(rbn, Kb, "bf16")
+            rms = tb["render_ms"] / max(tb["render_n"], 1)
+            gnb = gn_pass_ms(tb, cfgb.n_gn)
+            bf16 = {"workload": wb.name, "steps": Kb, "warmup": W,
+                    "frames_per_s": Kb / (rbn["total_ms"] * 1e-3), "ms_per_step": rbn["total_ms"] / Kb,
+                    "p50_step_ms": statistics.median(rbn["step_ms"]),
+                    "p99_step_ms": float(np.percentile(rbn["step_ms"], 99)),
+                    "phase_ms_per_step": {k[:-3]: tb[k] / max(tb[k[:-3] + "_n"], 1) for k in
+                                          ("predict_ms", "localise_ms", "fuse_ms", "render_ms", "anchor_ms")},
+                    "gauss_newton_pass_ms": gnb,
+                    "render_mrays_per_s": rbb["rays"] / (rms * 1e-3) / 1e6,
+                    "render_samples_per_launch": rbb["samples"],
+                    "render_frac_unique": rbb["U"] / (rms * 1e-3) / 1e9 / peak,
+                    "render_frac_gathered": rbb["G"] / (rms * 1e-3) / 1e9 / peak,
+                    "clocks": rbn["clocks"],
+                    "note": "map means and variances stored in bf16 (2 B a value), render and fuse math FP32, "
+                            "6x6 solve and state covariance FP64; its own seeded scene"}
+            del Db, Cb, mb
 
     # ---- end to end through the same public call ----
     e2e = calib = None
@@ -457,19 +539,30 @@ def run_ours(args, rank, world, local_rank):
                                       "samples the kernel evaluates"},
         "phase_ms_per_step": {k[:-3]: tm[k] / max(tm[k[:-3] + "_n"], 1) for k in
                               ("predict_ms", "localise_ms", "fuse_ms", "render_ms", "anchor_ms")},
-        "roofline": {"kernel": "k_render", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": traffic,
-                     "algorithmic_bytes": "U = distinct occupancy corners per ray x %d B + hits x 8 x 3 x %d B "
-                                          "colour corners, per launch" % (b, b),
-                     "bytes_per_launch": U, "samples_per_launch": samp_per,
-                     "gathered_bytes_per_launch": G, "frac_gathered": achieved_G / peak,
-                     "ms_per_launch": render_ms},
-        "roofline_localise": {"kernels": "k_track (Gauss-Newton x %d, Laplace) + mask + pose matrices" % cfg.n_gn,
-                              "bound": "latency (FP64 tail of each pass)",
-                              "achieved": loc_bytes / (loc_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                              "frac": loc_bytes / (loc_ms * 1e-3) / 1e9 / peak, "bytes_per_step": loc_bytes,
-                              "ms_per_step": loc_ms},
+        "roofline": {"kernel": "k_track<GN> (one Gauss-Newton pass)", "bound": "hbm",
+                     "achieved": gn_bytes / (gn_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": gn_bytes / (gn_ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
+                     "traffic": profiled_traffic(args.workload, "k_track_gn"),
+                     "algorithmic_bytes": "%d B per observed pixel (observation 16 B + anchor gathers 56 B) x %d "
+                                          "pixels, per launch" % (GN_BYTES_PER_PIXEL, npx),
+                     "bytes_per_launch": gn_bytes, "ms_per_launch": gn_ms, "launches_per_step": cfg.n_gn,
+                     "note": "the dominant kernel by device time (10 launches a step); latency-bound: the pixel "
+                             "loop over all SMs, then a one-block FP64 finish (solve, retraction) while the "
+                             "other SMs wait; ms_per_launch = (localisation - Laplace pass) / passes, from "
+                             "the library's CUDA events on its stream"},
+        "roofline_render": {"kernel": "k_render", "bound": "instruction issue (ncu: issue-active, L1-resident "
+                                                           "map; DRAM carries a few MB a launch)",
+                            "achieved_unique": achieved_U, "achieved_gathered": achieved_G, "peak": peak,
+                            "unit": "GB/s", "frac_unique": achieved_U / peak, "frac_gathered": achieved_G / peak,
+                            "peak_source": peak_kind, "traffic": profiled_traffic(args.workload, "k_render"),
+                            "algorithmic_bytes": "U = distinct occupancy corners per ray x %d B + hits x 8 x 3 x "
+                                                 "%d B colour corners; G = evaluated samples x 8 x %d B + hits x "
+                                                 "2 x 8 x 3 x %d B, per launch" % (b, b, b, b),
+                            "unique_bytes_per_launch": U, "gathered_bytes_per_launch": G,
+                            "samples_per_launch": samp_per, "ms_per_launch": render_ms},
+        "localisation": {"ms_per_step": loc_ms, "gauss_newton_passes": cfg.n_gn, "gauss_newton_pass_ms": gn_ms,
+                         "laplace_pass_ms": tm["laplace_ms"] / max(tm["laplace_n"], 1)},
+        "bf16_map": bf16,
         "e2e": e2e,
         "render_adjoint": adj,
         "pose_optimiser_adam": adam,

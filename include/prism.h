@@ -136,6 +136,8 @@ typedef struct {
 typedef struct {
     double predict_ms, localise_ms, fuse_ms, render_ms, anchor_ms;
     int64_t predict_n, localise_n, fuse_n, render_n, anchor_n;
+    double laplace_ms;   /* the Laplace pass alone (inside localise_ms) */
+    int64_t laplace_n;
 } prism_timing;
 
 /* Paper defaults for an n^3 grid of edge `extent` metres centred on the

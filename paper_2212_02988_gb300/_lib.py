@@ -51,7 +51,8 @@ class Stats(C.Structure):
 class Timing(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("predict_ms", "localise_ms", "fuse_ms", "render_ms",
                                           "anchor_ms")] + \
-               [(n, C.c_int64) for n in ("predict_n", "localise_n", "fuse_n", "render_n", "anchor_n")]
+               [(n, C.c_int64) for n in ("predict_n", "localise_n", "fuse_n", "render_n", "anchor_n")] + \
+               [("laplace_ms", C.c_double), ("laplace_n", C.c_int64)]
 
 
 class ServeConfig(C.Structure):

@@ -127,7 +127,7 @@ bool finite_pose(const double* p) {
 
 namespace {
 
-enum Phase { PH_PREDICT = 0, PH_LOCALISE, PH_FUSE, PH_RENDER, PH_ANCHOR, PH_COUNT };
+enum Phase { PH_PREDICT = 0, PH_LOCALISE, PH_FUSE, PH_RENDER, PH_ANCHOR, PH_LAPLACE, PH_COUNT };
 
 struct TimedPair {
     int phase;
@@ -199,8 +199,8 @@ struct prism_ctx {
     int64_t launches = 0;
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> pool;
-    double acc_ms[PH_COUNT] = {0, 0, 0, 0, 0};
-    int64_t acc_n[PH_COUNT] = {0, 0, 0, 0, 0};
+    double acc_ms[PH_COUNT] = {0, 0, 0, 0, 0, 0};
+    int64_t acc_n[PH_COUNT] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -458,9 +458,12 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb, b
                            h->counter, h->max_blocks, h->dstats, h->stream, !(prepped && it == 0),
                            it == 0 ? h->o_mask : nullptr),
            "Gauss-Newton pass");
-    LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
-                       h->counter, h->max_blocks, h->dstats, h->stream),
-       "Laplace pass");
+    {
+        PhaseTimer tl(h, PH_LAPLACE);
+        LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+                           h->counter, h->max_blocks, h->dstats, h->stream),
+           "Laplace pass");
+    }
     CK(h, cudaEventRecord(h->ev_state, h->stream), "state event");
     h->has_prior = false;
     h->anchor_at_mean = false;
@@ -1142,6 +1145,8 @@ prism_status prism_get_timing(prism_handle h, prism_timing* out) {
     out->fuse_ms = h->acc_ms[PH_FUSE];
     out->render_ms = h->acc_ms[PH_RENDER];
     out->anchor_ms = h->acc_ms[PH_ANCHOR];
+    out->laplace_ms = h->acc_ms[PH_LAPLACE];
+    out->laplace_n = h->acc_n[PH_LAPLACE];
     out->predict_n = h->acc_n[PH_PREDICT];
     out->localise_n = h->acc_n[PH_LOCALISE];
     out->fuse_n = h->acc_n[PH_FUSE];
