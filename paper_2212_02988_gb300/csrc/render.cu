@@ -5,8 +5,11 @@
 
 namespace prism {
 
+// Without DETAIL counters the march takes two samples a step (render_tile's
+// NS): 8 blocks an SM (64 registers) with two samples' loads in flight beat
+// 10 blocks with one, on the rays that march longest.
 template <bool BF16, bool DETAIL, int PX>
-__global__ void __launch_bounds__(128, 10) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
+__global__ void __launch_bounds__(128, DETAIL ? 10 : 8) k_render(KParams P, const float* __restrict__ mats, MapPlanes M,
                                                 float* __restrict__ depth, float* __restrict__ rgb,
                                                 uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
                                                 DevStats* __restrict__ stats, const double* __restrict__ anchor_src,
@@ -19,7 +22,7 @@ __global__ void __launch_bounds__(128, 10) k_render(KParams P, const float* __re
     }
     if (anchor_dst && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 7) anchor_dst[threadIdx.x] = anchor_src[threadIdx.x];
     __syncthreads();
-    render_tile<BF16, DETAIL, PX>(P, sR, sc, M, depth, rgb, mask, hitk, stats, blockIdx.x, blockIdx.y);
+    render_tile<BF16, DETAIL, PX, DETAIL ? 1 : 2>(P, sR, sc, M, depth, rgb, mask, hitk, stats, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_depth_mask(KParams P, const float* __restrict__ depth, uint8_t* __restrict__ mask) {

@@ -192,8 +192,14 @@ __device__ __forceinline__ int brick_exit(const KParams& P, int lv, int bx, int 
 // P.skip) jumps over 4^3 bricks whose occupancy bound shows that no sample
 // in them can be a hit.  The samples evaluated, their corner indices and
 // the hit index are those of the one-loop march over every sample; the
-// value of a jumped-over sample k - 1 is recomputed at the hit.
-template <bool BF16, bool DETAIL, int PX>
+// value of a jumped-over sample k - 1 is recomputed at the hit.  With NS > 1
+// (not with DETAIL) the march evaluates NS consecutive samples per step, so
+// that a long ray has NS samples' loads in flight; it may also evaluate up
+// to NS - 1 samples past the hit, or inside a brick it would have jumped
+// from, none of which can change the hit (the first sample above tau) or
+// the outputs.  The sample count (DevStats::render_samples) leaves out
+// the samples evaluated past the hit.
+template <bool BF16, bool DETAIL, int PX, int NS = 1>
 __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, const float* sc, const MapPlanes& M,
                                             float* __restrict__ depth, float* __restrict__ rgb,
                                             uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
@@ -291,6 +297,57 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
                 uniq += fresh ? 8u : 8u - (8u >> ch);
                 pfx = flx; pfy = fly; pfz = flz;
                 fresh = false;
+            }
+            if constexpr (NS > 1 && !DETAIL) {
+                // samples k .. k + NS - 1 together: their 8 NS corner loads are
+                // in flight at once.  A sample past kmax or leaving the grid
+                // ends the group (it re-reads sample k's corners, in bounds, and
+                // is ignored); one in a skippable brick is evaluated (its value
+                // cannot pass tau).  The first value above tau is the hit.
+                render_detail::Sample cs[NS];
+                bool ok[NS];
+                float fv[NS];
+                cs[0] = cur;
+                ok[0] = true;
+#pragma unroll
+                for (int j = 1; j < NS; ++j) {
+                    const float dj = __fmul_rn(kf + (float)j, P.eps32);
+                    const float jx = __fmaf_rn(dj, rgx, cgx), jy = __fmaf_rn(dj, rgy, cgy), jz = __fmaf_rn(dj, rgz, cgz);
+                    ok[j] = ok[j - 1] && k + j <= P.kmax &&
+                            (k + j <= k_safe || (jx >= -0.5f && jx < hx && jy >= -0.5f && jy < hy && jz >= -0.5f && jz < hz));
+                    const render_detail::Sample sj = render_detail::cell_of(px, pxy, jx, jy, jz);
+                    cs[j] = cur;
+                    if (ok[j]) cs[j] = sj;
+                }
+#pragma unroll
+                for (int j = 0; j < NS; ++j)
+                    fv[j] = render_detail::trilinear<BF16, PX>(M.occ, cs[j].base, px, pxy, cs[j].fx, cs[j].fy, cs[j].fz);
+                int jh = -1, nv = 1;
+                float f_last = fv[0];
+#pragma unroll
+                for (int j = NS - 1; j >= 0; --j)
+                    if (ok[j] && fv[j] > P.tau32) jh = j;
+#pragma unroll
+                for (int j = 1; j < NS; ++j)
+                    if (ok[j]) { nv = j + 1; f_last = fv[j]; }
+                if (jh >= 0) {
+#pragma unroll
+                    for (int j = 0; j < NS; ++j)
+                        if (j == jh) {
+                            f = fv[j];
+                            if (j > 0) { f_prev = fv[j - 1]; prev_ok = true; cur = cs[j]; }
+                        }
+                    nsamp += jh;
+                    k += jh;
+                    hit = true;
+                    break;
+                }
+                nsamp += nv - 1;
+                f_prev = f_last;
+                prev_ok = true;
+                k += nv;
+                kf += (float)nv;
+                continue;
             }
             f = render_detail::trilinear<BF16, PX>(M.occ, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
             if (f > P.tau32) { hit = true; break; }
