@@ -44,12 +44,29 @@ struct MapPlanes {
     float2* bb;
 };
 
+// The tile order of an anchor render and what the next one is planned from
+// (render_plan_block, render_dev.cuh); tiles are 16x8 pixels, row-major.
+struct RenderPlan {
+    const int* order = nullptr;   // the tiles in launch order (a permutation), or null for row-major
+    uint32_t* cost = nullptr;     // out, per tile: the sum over its warps of the largest sample count
+    float* rot = nullptr;         // out: this render's camera-to-world rotation (9 floats)
+};
+struct RenderPlanIn {
+    const uint32_t* cost;   // the last anchor render's RenderPlan::cost
+    const float* rot_last;  // and its rotation
+    const float* c2w;       // the next anchor render's mats
+    uint32_t* key;          // scratch, one word per tile
+    int* order;             // out
+};
+
 // render.cu — mats: 12 FP32 values on the device (DevState::c2w or ::aux);
 // anchor_src/anchor_dst: when given, block 0 copies the 7 pose doubles
 // (the anchor's pose) from src to dst.
 cudaError_t launch_render(const KParams& P, const float* mats, const MapPlanes& M, float* depth, float* rgb,
                           uint8_t* mask, int32_t* hitk, DevStats* stats, const double* anchor_src,
-                          double* anchor_dst, bool detail, cudaStream_t s);
+                          double* anchor_dst, bool detail, cudaStream_t s, const RenderPlan& plan = RenderPlan{});
+// The next anchor render's tile order (one block).
+cudaError_t launch_render_plan(const KParams& P, const RenderPlanIn& in, cudaStream_t s);
 cudaError_t launch_depth_mask(const KParams& P, const float* depth, uint8_t* mask, cudaStream_t s);
 // The render's compile-time plane-stride specialisation for P (0: none).
 int render_px_specialisation(const KParams& P);

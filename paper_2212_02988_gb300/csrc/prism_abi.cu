@@ -155,6 +155,19 @@ struct prism_ctx {
     int* fuse_list = nullptr;
     unsigned int* fuse_ctr = nullptr;
     unsigned int* counter = nullptr;
+    // the anchor render's tile order (render_plan_block): the last anchor
+    // render's tile costs and rotation, the planned order and its scratch,
+    // in one block; planned on its own stream once the posterior is final
+    // (beside the map update), the render waits for ev_plan.  plan_ready: an
+    // anchor render has recorded its costs; plan_fresh: the order was
+    // planned for the next anchor render
+    void* plan_block = nullptr;
+    RenderPlanIn plan_in{};
+    RenderPlan plan_out{};
+    cudaStream_t plan_stream = nullptr;
+    cudaEvent_t ev_plan = nullptr;
+    bool plan_ready = false;
+    bool plan_fresh = false;
     DevState* h_state = nullptr;       // pinned host copy of the device state (read_state)
     int max_blocks = 0;
     double* d_imu = nullptr;
@@ -288,7 +301,8 @@ void collect_timing(prism_handle h) {
 
 void free_all(prism_handle h) {
     void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a0, h->a1, h->o_mask,
-                    h->dstate, h->dstats, h->partials, h->counter, h->d_imu, h->fuse_list, h->fuse_ctr};
+                    h->dstate, h->dstats, h->partials, h->counter, h->d_imu, h->fuse_list, h->fuse_ctr,
+                    h->plan_block};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -297,6 +311,11 @@ void free_all(prism_handle h) {
         cudaStreamSynchronize(h->side);
         cudaStreamDestroy(h->side);
     }
+    if (h->plan_stream) {
+        cudaStreamSynchronize(h->plan_stream);
+        cudaStreamDestroy(h->plan_stream);
+    }
+    if (h->ev_plan) cudaEventDestroy(h->ev_plan);
     for (int k = 0; k < prism_ctx::kImuRing; ++k) {
         if (h->h_imu[k]) cudaFreeHost(h->h_imu[k]);
         if (h->ev_imu[k]) cudaEventDestroy(h->ev_imu[k]);
@@ -410,9 +429,14 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
     {
         PhaseTimer t(h, PH_RENDER);
         // t[3] and q[4] are contiguous: the state mean pose becomes the anchor's pose
+        RenderPlan plan = h->plan_out;
+        if (h->plan_fresh) CK(h, cudaStreamWaitEvent(h->stream, h->ev_plan, 0), "wait for the tile order");
+        else plan.order = nullptr;
         LAUNCH(h, launch_render(h->kp, h->dstate->c2w, h->map, h->a_depth, h->a_rgb, mask, hitk, h->dstats,
-                                h->dstate->t, h->dstate->anchor_pose, h->detail, h->stream),
+                                h->dstate->t, h->dstate->anchor_pose, h->detail, h->stream, plan),
                "render");
+        h->plan_ready = true;
+        h->plan_fresh = false;
     }
     PhaseTimer t(h, PH_ANCHOR);
     LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a0, h->a1, h->stream), "anchor pack");
@@ -479,6 +503,17 @@ prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool 
            "fuse");
     ++h->launches;   // (two kernels: the frustum list and the update)
     if (h->kp.skip) LAUNCH(h, launch_brick_bounds(h->kp, h->map, h->stream), "brick bounds");
+    return PRISM_OK;
+}
+
+// The tile order of the anchor render that follows at the posterior mean,
+// planned on its own stream once the posterior is final (ev_state).
+prism_status do_plan(prism_handle h) {
+    if (!h->plan_ready) return PRISM_OK;
+    CK(h, cudaStreamWaitEvent(h->plan_stream, h->ev_state, 0), "wait for the posterior");
+    LAUNCH(h, launch_render_plan(h->kp, h->plan_in, h->plan_stream), "tile order");
+    CK(h, cudaEventRecord(h->ev_plan, h->plan_stream), "tile-order event");
+    h->plan_fresh = true;
     return PRISM_OK;
 }
 
@@ -666,6 +701,16 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         dalloc(h, &h->fuse_list, (size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(int)) ||
         dalloc(h, &h->fuse_ctr, 2 * sizeof(unsigned int)))
         return cleanup(PRISM_ENOMEM, "device allocation failed");
+    {   // tile costs, order and scratch (one word each per 16x8 tile), the rotation
+        const size_t nt = (size_t)((cfg->width + 15) / 16) * ((cfg->height + 7) / 8);
+        const size_t words = ((nt + 63) / 64) * 64;
+        if (dalloc(h, &h->plan_block, 3 * words * 4 + 64) != cudaSuccess)
+            return cleanup(PRISM_ENOMEM, "device allocation failed");
+        uint32_t* w = (uint32_t*)h->plan_block;
+        float* rot = (float*)(w + 3 * words);
+        h->plan_out = RenderPlan{(const int*)(w + words), w, rot};
+        h->plan_in = RenderPlanIn{w, rot, h->dstate->c2w, w + 2 * words, (int*)(w + words)};
+    }
     if (cudaMallocHost(&h->h_state, sizeof(DevState)) != cudaSuccess)
         return cleanup(PRISM_ENOMEM, "host allocation failed");
     cudaGetLastError();
@@ -673,6 +718,8 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         int least = 0, greatest = 0;
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if ((e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&h->plan_stream, cudaStreamNonBlocking, greatest)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_plan, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&h->ev_pred, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&h->ev_read, cudaEventDisableTiming)) != cudaSuccess)
@@ -838,6 +885,7 @@ prism_status step_checked(prism_handle h, const double* imu, int32_t n, double d
         const bool prep = h->anchor_at_mean;
         if ((st = do_predict_side(h, imu, n, dt, prep)) != PRISM_OK) return st;
         if ((st = do_localise(h, depth, rgb, true, prep, wait_in)) != PRISM_OK) return st;
+        if ((st = do_plan(h)) != PRISM_OK) return st;
         mask_ready = true;
     }
     if ((st = do_fuse(h, depth, rgb, mask_ready)) != PRISM_OK) return st;

@@ -183,8 +183,8 @@ __device__ __forceinline__ int brick_exit(const KParams& P, int lv, int bx, int 
 
 // One 16x8-pixel tile (128 threads; warp w covers the 8x4 pixels at
 // ((w & 1) 8, (w >> 1) 4) of the tile).  sR / sc: camera-to-world rotation
-// and centre in shared memory.  anchor_src / anchor_dst: when given, the
-// tile at (0, 0) copies the 7 pose doubles.
+// and centre in shared memory.  Returns the thread's evaluated samples (0
+// outside the image).
 //
 // The march tests the grid bounds only for samples after k_safe, which a
 // conservative FP32 bound (one voxel of margin, far above the rounding of the
@@ -200,7 +200,7 @@ __device__ __forceinline__ int brick_exit(const KParams& P, int lv, int bx, int 
 // the outputs.  The sample count (DevStats::render_samples) leaves out
 // the samples evaluated past the hit.
 template <bool BF16, bool DETAIL, int PX, int NS = 1>
-__device__ __forceinline__ void render_tile(const KParams& P, const float* sR, const float* sc, const MapPlanes& M,
+__device__ __forceinline__ int render_tile(const KParams& P, const float* sR, const float* sc, const MapPlanes& M,
                                             float* __restrict__ depth, float* __restrict__ rgb,
                                             uint8_t* __restrict__ mask, int32_t* __restrict__ hitk,
                                             DevStats* __restrict__ stats, int tile_x, int tile_y) {
@@ -399,6 +399,81 @@ __device__ __forceinline__ void render_tile(const KParams& P, const float* sR, c
             atomicAdd(&stats->render_rays, (unsigned long long)rays);
         }
     }
+    return nsamp;
+}
+
+// The order of an anchor render's tiles, heaviest predicted first.  A ray's
+// march length varies by two orders of magnitude across the image (rays
+// grazing a surface evaluate a sample at every step of a long run of bricks
+// that cannot be skipped); rendered in raster order, the heavy tiles start
+// last and their blocks run on after the other SMs have emptied.  The
+// prediction is the last anchor render's cost (per tile, the sum over its
+// warps of the warp's largest sample count) at the tile each tile's centre
+// ray falls in when turned into the last camera (rotation only), maximised
+// over its 3x3 tile neighbourhood; a ray outside the last image counts as
+// heaviest.  Tiles go into 64 cost buckets, the buckets are laid out
+// heaviest first; within a bucket the order is arbitrary.  The order only
+// decides when a tile is rendered, never what it renders.  One block (a
+// multiple of 32 threads); key: one word of scratch per tile.
+__device__ __forceinline__ void render_plan_block(const KParams& P, const RenderPlanIn& in) {
+    constexpr int kBuckets = 64;
+    constexpr uint32_t kUnknown = 0xffffffffu;
+    __shared__ uint32_t hist[kBuckets], base[kBuckets], s_max;
+    const int gx = (P.W + 15) >> 4, gy = (P.H + 7) >> 3, nt = gx * gy;
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_max = 0u;
+    // R = R_lastᵀ R_next: the next camera's ray directions in the last camera's frame
+    float R[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            R[3 * i + j] = in.rot_last[i] * in.c2w[j] + in.rot_last[3 + i] * in.c2w[3 + j] +
+                           in.rot_last[6 + i] * in.c2w[6 + j];
+    __syncthreads();
+    uint32_t lmax = 0u;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const float dx = ((float)((t % gx) * 16 + 8) - P.cx32) * P.ifx32;
+        const float dy = ((float)((t / gx) * 8 + 4) - P.cy32) * P.ify32;
+        const float ex = R[0] * dx + R[1] * dy + R[2], ey = R[3] * dx + R[4] * dy + R[5];
+        const float ez = R[6] * dx + R[7] * dy + R[8];
+        uint32_t e = kUnknown;
+        if (ez > 1e-6f) {
+            const float u = P.fx32 * ex / ez + P.cx32, v = P.fy32 * ey / ez + P.cy32;
+            if (u >= 0.0f && u < (float)P.W && v >= 0.0f && v < (float)P.H) {
+                const int tx = min((int)u >> 4, gx - 1), ty = min((int)v >> 3, gy - 1);
+                const int x0 = max(tx - 1, 0), x2 = min(tx + 1, gx - 1);
+                const int y0 = max(ty - 1, 0), y2 = min(ty + 1, gy - 1);
+                const uint32_t* r0 = in.cost + y0 * gx;
+                const uint32_t* r1 = in.cost + ty * gx;
+                const uint32_t* r2 = in.cost + y2 * gx;
+                e = max(max(max(r0[x0], r0[tx]), max(r0[x2], r1[x0])), max(max(r1[tx], r1[x2]), max(r2[x0], r2[tx])));
+                e = max(e, r2[x2]);
+                lmax = max(lmax, e);
+            }
+        }
+        in.key[t] = e;
+    }
+    lmax = __reduce_max_sync(0xffffffffu, lmax);
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_max, lmax);
+    __syncthreads();
+    const unsigned long long mx = s_max > 0u ? s_max : 1u;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {   // the same thread wrote key[t] above
+        const uint32_t e = in.key[t];
+        const uint32_t k = e == kUnknown ? kBuckets - 1 : (uint32_t)((unsigned long long)e * (kBuckets - 1) / mx);
+        in.key[t] = k;
+        atomicAdd(&hist[k], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0u;
+        for (int k = kBuckets - 1; k >= 0; --k) {
+            base[k] = run;
+            run += hist[k];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) in.order[atomicAdd(&base[in.key[t]], 1u)] = t;
 }
 
 __device__ __forceinline__ void depth_mask_px(const KParams& P, const float* __restrict__ depth,

@@ -96,17 +96,23 @@ def test_skipping_on_a_non_cubic_grid(oracle_mod):
     assert out[1][1] < out[0][1]
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
-def test_skipping_changes_no_filter_step(oracle_mod, storage):
+@pytest.mark.parametrize("name,storage,start", [("room128_320x240", "f32", "prior"),
+                                                ("room128_320x240", "bf16", "prior"),
+                                                ("room256_640x480", "f32", "settled")])
+def test_skipping_changes_no_filter_step(oracle_mod, name, storage, start):
     """From the prior map the fuse writes the tile bounds the render skips
-    by; every state and the final map agree bit for bit."""
+    by; every state and the final map agree bit for bit.  With skipping, the
+    brick-bound launch also plans the anchor render's tile order from the
+    last anchor render's tile costs (from the second step on), which must
+    change nothing either."""
     from paper_2212_02988_gb300 import state_arrays
-    w = synth.ROOM128
+    w = synth.PRESETS[name]
     s = synth.Sequence(w, n_frames=6)
     frames = [s.frame(i) for i in range(5)]
     runs = {}
     for skip in (0, 1):
-        F, _ = make_pair(w, oracle_mod, storage=storage, map_arrays=s.prior_map(), s1_pose=s.pose7(0),
+        F, _ = make_pair(w, oracle_mod, storage=storage,
+                         map_arrays=s.prior_map() if start == "prior" else s.settled_map(), s1_pose=s.pose7(0),
                          vel=s.velocity(0), skip_empty=skip)
         states = [state_arrays(F.step(s.imu_window(i) if i else None, w.dt, t(f["depth"]), t(f["rgb"]),
                                       want_state=True)) for i, f in enumerate(frames)]
