@@ -168,6 +168,7 @@ struct prism_ctx {
     cudaEvent_t ev_plan = nullptr;
     bool plan_ready = false;
     bool plan_fresh = false;
+    bool plan_waited = false;   // the main stream already waits for ev_plan
     DevState* h_state = nullptr;       // pinned host copy of the device state (read_state)
     int max_blocks = 0;
     double* d_imu = nullptr;
@@ -430,13 +431,14 @@ prism_status do_render_anchor(prism_handle h, uint8_t* mask = nullptr, int32_t* 
         PhaseTimer t(h, PH_RENDER);
         // t[3] and q[4] are contiguous: the state mean pose becomes the anchor's pose
         RenderPlan plan = h->plan_out;
-        if (h->plan_fresh) CK(h, cudaStreamWaitEvent(h->stream, h->ev_plan, 0), "wait for the tile order");
-        else plan.order = nullptr;
+        if (!h->plan_fresh) plan.order = nullptr;
+        else if (!h->plan_waited) CK(h, cudaStreamWaitEvent(h->stream, h->ev_plan, 0), "wait for the tile order");
         LAUNCH(h, launch_render(h->kp, h->dstate->c2w, h->map, h->a_depth, h->a_rgb, mask, hitk, h->dstats,
                                 h->dstate->t, h->dstate->anchor_pose, h->detail, h->stream, plan),
                "render");
         h->plan_ready = true;
         h->plan_fresh = false;
+        h->plan_waited = false;
     }
     PhaseTimer t(h, PH_ANCHOR);
     LAUNCH(h, launch_anchor_pack(h->kp, h->a_depth, h->a_rgb, h->a0, h->a1, h->stream), "anchor pack");
@@ -502,7 +504,15 @@ prism_status do_fuse(prism_handle h, const float* depth, const float* rgb, bool 
                                  h->fuse_ctr, mask_ready ? &h->dstate->rejected : nullptr, h->stream),
            "fuse");
     ++h->launches;   // (two kernels: the frustum list and the update)
-    if (h->kp.skip) LAUNCH(h, launch_brick_bounds(h->kp, h->map, h->stream), "brick bounds");
+    if (h->kp.skip) {
+        // the tile order is done long before (it started with the map update):
+        // waiting here keeps the brick bounds and the render back to back
+        if (h->plan_fresh && !h->plan_waited) {
+            CK(h, cudaStreamWaitEvent(h->stream, h->ev_plan, 0), "wait for the tile order");
+            h->plan_waited = true;
+        }
+        LAUNCH(h, launch_brick_bounds(h->kp, h->map, h->stream), "brick bounds");
+    }
     return PRISM_OK;
 }
 
@@ -514,6 +524,7 @@ prism_status do_plan(prism_handle h) {
     LAUNCH(h, launch_render_plan(h->kp, h->plan_in, h->plan_stream), "tile order");
     CK(h, cudaEventRecord(h->ev_plan, h->plan_stream), "tile-order event");
     h->plan_fresh = true;
+    h->plan_waited = false;
     return PRISM_OK;
 }
 
