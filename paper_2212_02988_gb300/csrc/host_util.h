@@ -4,10 +4,21 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "prism.h"
 #include "prism_dev.cuh"
 
 namespace prism {
+
+// An NVTX range over a scope of the host thread that enqueues the work (a
+// no-op unless a tool such as Nsight Systems is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Checks a configuration; on failure `why` says what is wrong.
 bool valid_config(const prism_config* c, std::string& why);

@@ -128,6 +128,8 @@ bool finite_pose(const double* p) {
 namespace {
 
 enum Phase { PH_PREDICT = 0, PH_LOCALISE, PH_FUSE, PH_RENDER, PH_ANCHOR, PH_LAPLACE, PH_COUNT };
+const char* const kPhaseName[PH_COUNT] = {"prism predict", "prism localise", "prism fuse",
+                                          "prism render",  "prism anchor",   "prism laplace"};
 
 struct TimedPair {
     int phase;
@@ -267,12 +269,16 @@ cudaEvent_t take_event(prism_handle h) {
     return e;
 }
 
+// A phase's CUDA events (with prism_set_timing) and its NVTX range on the
+// host thread that enqueues it (an NVTX call is a no-op unless a tool such
+// as Nsight Systems is attached).
 struct PhaseTimer {
     prism_handle h;
     int phase;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
     PhaseTimer(prism_handle h_, int ph, cudaStream_t s_ = nullptr) : h(h_), phase(ph), s(s_ ? s_ : h_->stream) {
+        nvtxRangePushA(kPhaseName[ph]);
         if (h->timing) {
             a = take_event(h);
             cudaEventRecord(a, s);
@@ -284,6 +290,7 @@ struct PhaseTimer {
             cudaEventRecord(b, s);
             h->pending.push_back({phase, a, b});
         }
+        nvtxRangePop();
     }
 };
 
@@ -890,6 +897,7 @@ namespace {
 
 prism_status step_checked(prism_handle h, const double* imu, int32_t n, double dt, const float* depth,
                           const float* rgb, prism_state* out, bool wait_in) {
+    NvtxRange range("prism step");
     prism_status st;
     bool mask_ready = false;
     if (h->steps > 0) {

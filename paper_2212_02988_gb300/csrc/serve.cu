@@ -382,6 +382,7 @@ void run_batch(prism_server* S, std::unique_lock<std::mutex>& lk) {
     const int n_gn = S->cfg.n_gn;
     const bool use_graph = S->gexec != nullptr;
     lk.unlock();
+    NvtxRange range("prism serve batch");
     cudaError_t e = cudaSuccess;
     for (const Up& u : ups) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(u.dd, u.hd, u.npix * 4, cudaMemcpyDefault, S->stream);
