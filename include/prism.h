@@ -366,6 +366,26 @@ prism_status prism_set_detail_counters(prism_handle h, int32_t enabled);
 prism_status prism_get_timing(prism_handle h, prism_timing* out);   /* synchronises */
 prism_status prism_timing_reset(prism_handle h);
 
+/* Bounds-check build.  libprism_checked.so is this library compiled with
+ * PRISM_CHECKED: its kernels test the data-dependent index of every gather
+ * and scatter (a trilinear cell's last corner in a map plane, a brick bound,
+ * an anchor gather of the localisation, a block's partial column, a listed
+ * fuse tile, a voxel and its nearest pixel in the map update, a corner of the
+ * render adjoint, a tile of the anchor render's order) before the access, skip
+ * any access outside its buffer, and keep the handle's first violation.
+ * prism_checked_build returns 1 in that library, 0 in libprism.so.
+ * prism_check_status synchronises the handle's stream and writes its first
+ * violation to *word: 0 for none, else (site << 48) | (index & (2^48 - 1)),
+ * site 1 render corner, 2 brick bound, 3 anchor gather, 4 partial column,
+ * 5 fuse tile, 6 fuse voxel, 7 fuse pixel, 8 adjoint corner, 9 tile order;
+ * always 0 in libprism.so, whose kernels carry no tests.  A violation means
+ * a wrong result, never an access outside a buffer.  PRISM_EINVAL for a
+ * NULL argument, PRISM_ECUDA if the read fails.  The allocation-free entry
+ * point (prism_normal_equations_noalloc) runs without a word: its accesses
+ * are tested and skipped but not recorded. */
+int32_t prism_checked_build(void);
+prism_status prism_check_status(prism_handle h, uint64_t* word);
+
 /* Bytes of device memory the handle owns. */
 int64_t prism_device_bytes(prism_handle h);
 

@@ -145,6 +145,13 @@ prism_status prism_serve_drain(prism_server_handle s, int32_t timeout_ms);
 
 prism_status prism_serve_get_stats(prism_server_handle s, prism_serve_stats* out);
 
+/* Bounds-check build (libprism_checked.so, see prism_check_status in
+ * prism.h): synchronises the server's stream and writes the first index
+ * violation of any of its streams' kernels to *word (0 for none); always 0
+ * in libprism.so.  PRISM_EINVAL for a NULL argument, PRISM_ECUDA if the
+ * read fails. */
+prism_status prism_serve_check_status(prism_server_handle s, uint64_t* word);
+
 /* Copies a resident stream's map to the caller's dense device arrays (any
  * may be NULL), after the requests already on the device; returns when the
  * copy is complete.  PRISM_ESTATE if the stream is not resident. */

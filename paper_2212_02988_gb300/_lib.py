@@ -11,7 +11,9 @@ import os
 import re
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libprism.so")
+# PRISM_CHECKED=1 in the environment loads the bounds-check build instead
+# (libprism_checked.so, built beside it; prism_check_status in prism.h).
+LIB_PATH = os.path.join(PKG, "libprism_checked.so" if os.environ.get("PRISM_CHECKED") == "1" else "libprism.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "prism.h")
 HEADERS = [HEADER, os.path.join(os.path.dirname(PKG), "include", "prism_serve.h")]
 
@@ -119,6 +121,8 @@ def load() -> C.CDLL:
         "prism_get_timing": (st, [H, P(Timing)]),
         "prism_timing_reset": (st, [H]),
         "prism_device_bytes": (C.c_int64, [H]),
+        "prism_checked_build": (C.c_int32, []),
+        "prism_check_status": (st, [H, P(C.c_uint64)]),
         "prism_last_error": (C.c_char_p, [H]),
         "prism_status_string": (C.c_char_p, [C.c_int32]),
         "prism_render_backward": (st, [H, dp, fp, fp, fp, fp, dp, dp]),
@@ -137,6 +141,7 @@ def load() -> C.CDLL:
         "prism_serve_poll": (st, [H, P(ServeResult), C.c_int32, C.c_int32, P(C.c_int32)]),
         "prism_serve_drain": (st, [H, C.c_int32]),
         "prism_serve_get_stats": (st, [H, P(ServeStats)]),
+        "prism_serve_check_status": (st, [H, P(C.c_uint64)]),
         "prism_serve_map_store": (st, [H, C.c_int32, fp, fp, fp, fp]),
         "prism_serve_last_error": (C.c_char_p, [H]),
     }

@@ -90,6 +90,7 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
                                           const uint8_t* __restrict__ mask, DevStats* __restrict__ stats,
                                           uint32_t tile) {
     __shared__ int s_skip;
+    if (!PRISM_IN_RANGE(P, CHK_FUSE_TILE, tile, (long long)P.nbx * P.nby * P.nbz)) return;   // block-uniform
     const int bx = tile % P.nbx, by = (tile / P.nbx) % P.nby, bz = tile / (P.nbx * P.nby);
     if (CULL) {
         if (threadIdx.x == 0) s_skip = tile_outside_frustum(P, sM, sb, bx, by, bz);
@@ -131,6 +132,7 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
             const float nu = floorf(__fadd_rn(u, 0.5f)), nv = floorf(__fadd_rn(v, 0.5f));
             ok = nu >= 0.0f && nu <= fW1 && nv >= 0.0f && nv <= fH1;
             if (ok) pix[h] = (int)nv * P.W + (int)nu;
+            ok = ok && PRISM_IN_RANGE(P, CHK_FUSE_PIXEL, pix[h], (long long)P.W * P.H);
         }
         in[h] = ok;
     }
@@ -142,7 +144,8 @@ __device__ __forceinline__ void fuse_tile(const KParams& P, const MapPlanes& M, 
             mk[h] = mask[pix[h]] != 0;
             dep[h] = depth[pix[h]];
         }
-        mu[h] = map_load_rw<BF16>(M.occ, idx[h]);
+        mu[h] = PRISM_IN_RANGE(P, CHK_FUSE_VOXEL, idx[h], P.npad) ? map_load_rw<BF16>(M.occ, idx[h]) : 0.0f;
+        if (!PRISM_IN_RANGE(P, CHK_FUSE_VOXEL, idx[h], P.npad)) mk[h] = false;
     }
     bool upd[2], colour[2];
     float sdf[2], var[2], cvar[2], cr[2], cg[2], cb[2], o0[2], o1[2], o2[2];

@@ -163,6 +163,7 @@ struct prism_ctx {
     // (beside the map update), the render waits for ev_plan.  plan_ready: an
     // anchor render has recorded its costs; plan_fresh: the order was
     // planned for the next anchor render
+    unsigned long long* check = nullptr;   // bounds-check build: the first index violation
     void* plan_block = nullptr;
     RenderPlanIn plan_in{};
     RenderPlan plan_out{};
@@ -310,7 +311,7 @@ void collect_timing(prism_handle h) {
 void free_all(prism_handle h) {
     void* ptrs[] = {h->map_block, h->a_depth, h->a_rgb, h->a0, h->a1, h->o_mask,
                     h->dstate, h->dstats, h->partials, h->counter, h->d_imu, h->fuse_list, h->fuse_ctr,
-                    h->plan_block};
+                    h->plan_block, h->check};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& t : h->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
@@ -729,6 +730,12 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         h->plan_out = RenderPlan{(const int*)(w + words), w, rot};
         h->plan_in = RenderPlanIn{w, rot, h->dstate->c2w, w + 2 * words, (int*)(w + words)};
     }
+#ifdef PRISM_CHECKED
+    if (dalloc(h, &h->check, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(h->check, 0, sizeof(unsigned long long)) != cudaSuccess)
+        return cleanup(PRISM_ENOMEM, "device allocation failed");
+    h->kp.check = h->check;
+#endif
     if (cudaMallocHost(&h->h_state, sizeof(DevState)) != cudaSuccess)
         return cleanup(PRISM_ENOMEM, "host allocation failed");
     cudaGetLastError();
@@ -917,6 +924,27 @@ prism_status step_checked(prism_handle h, const double* imu, int32_t n, double d
 }  // namespace
 
 extern "C" {
+
+int32_t prism_checked_build(void) {
+#ifdef PRISM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+prism_status prism_check_status(prism_handle h, uint64_t* word) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    if (!word) return fail(h, PRISM_EINVAL, "word is NULL");
+    *word = 0;
+    if (!h->check) return PRISM_OK;
+    DeviceGuard g(h->device);
+    unsigned long long v = 0;
+    CK(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    CK(h, cudaMemcpy(&v, h->check, sizeof(v), cudaMemcpyDeviceToHost), "read check word");
+    *word = v;
+    return PRISM_OK;
+}
 
 prism_status prism_get_state(prism_handle h, prism_state* out) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");

@@ -66,7 +66,38 @@ struct KParams {
     double fx, fy, cx, cy;
     double sigma_vel[2], sigma_pose[2];
     double ema, gravity, update_var;
+    unsigned long long* check; // bounds-check build: the first index violation (device word), or null
 };
+
+// ------------------------------------------------------------ checked build
+// Built with -DPRISM_CHECKED (libprism_checked.so), the kernels test the
+// data-dependent indices of their gathers and scatters before the access:
+// an index outside [0, n) skips the access (the result is then wrong, but
+// nothing outside the buffer is touched) and the first violation is kept in
+// *P.check as (site << 48) | (index & (2^48 - 1)).  Without the flag every
+// test is the constant true and compiles away.
+enum CheckSite : int {
+    CHK_RENDER_CORNER = 1,   // a trilinear cell's last corner in a map plane (npad)
+    CHK_RENDER_BRICK = 2,    // a brick bound (bb_len)
+    CHK_TRACK_ANCHOR = 3,    // an anchor gather (W H)
+    CHK_TRACK_PARTIAL = 4,   // a block's partial column (the partials' stride)
+    CHK_FUSE_TILE = 5,       // a listed tile (nbx nby nbz)
+    CHK_FUSE_VOXEL = 6,      // a voxel of a map plane (npad)
+    CHK_FUSE_PIXEL = 7,      // a voxel's nearest pixel (W H)
+    CHK_BWD_CORNER = 8,      // a gradient corner of the render adjoint (npad)
+    CHK_PLAN = 9,            // a tile of the anchor render's order (tiles)
+};
+
+#ifdef PRISM_CHECKED
+__device__ __forceinline__ bool check_index(unsigned long long* word, int site, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    if (word) atomicCAS(word, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+    return false;
+}
+#define PRISM_IN_RANGE(P, site, i, n) ::prism::check_index((P).check, (site), (long long)(i), (long long)(n))
+#else
+#define PRISM_IN_RANGE(P, site, i, n) true
+#endif
 
 // Device-resident filter state (FP64).  One per handle.
 struct DevState {

@@ -31,7 +31,10 @@ __global__ void __launch_bounds__(128, DETAIL ? 10 : 8) k_render(KParams P, cons
     __syncthreads();
     const int gx = (P.W + 15) >> 4, nt = gx * ((P.H + 7) >> 3);
     int tile = plan.order ? plan.order[blockIdx.x] : (int)blockIdx.x;
-    if ((unsigned)tile >= (unsigned)nt) tile = (int)blockIdx.x;   // (never taken: the order is a permutation)
+    if ((unsigned)tile >= (unsigned)nt) {   // (never taken: the order is a permutation)
+        PRISM_IN_RANGE(P, CHK_PLAN, tile, nt);
+        tile = (int)blockIdx.x;
+    }
     const int ns = render_tile<BF16, DETAIL, PX, DETAIL ? 1 : 2>(P, sR, sc, M, depth, rgb, mask, hitk, stats,
                                                                    tile % gx, tile / gx);
     if (plan.cost) {

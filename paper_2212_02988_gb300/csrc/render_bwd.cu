@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(128) k_render_bwd(KParams P, const float* __re
                 const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
                 if (!(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
                 const Cell8 c = cell8(P, gx, gy, gz);
+                if (!PRISM_IN_RANGE(P, CHK_BWD_CORNER, (long long)c.base + P.pxy + P.px + 1, P.npad)) break;
                 float vv[8], gg[3];
                 corners<BF16>(P, M.occ, c, vv);
                 if (tri_value_grad(vv, c.fx, c.fy, c.fz, gg) > P.tau32) { hit = true; break; }
@@ -133,41 +134,44 @@ __global__ void __launch_bounds__(128) k_render_bwd(KParams P, const float* __re
                     cs[s] = cell8(P, __fmaf_rn(ds[s], rgx, cgx), __fmaf_rn(ds[s], rgy, cgy),
                                   __fmaf_rn(ds[s], rgz, cgz));
                 }
-                float vo[2][8], go[2][3], f[2];
-                for (int s = 0; s < 2; ++s) {
-                    corners<BF16>(P, M.occ, cs[s], vo[s]);
-                    f[s] = tri_value_grad(vo[s], cs[s].fx, cs[s].fy, cs[s].fz, go[s]);
-                }
-                const float alpha = (P.tau32 - f[0]) / (f[1] - f[0]);
-                const void* planes[3] = {M.r, M.g, M.b};
-                float col[2][3], gcol[2][3][3];
-                for (int ch = 0; ch < 3; ++ch)
+                if (PRISM_IN_RANGE(P, CHK_BWD_CORNER, (long long)cs[0].base + P.pxy + P.px + 1, P.npad) &&
+                    PRISM_IN_RANGE(P, CHK_BWD_CORNER, (long long)cs[1].base + P.pxy + P.px + 1, P.npad)) {
+                    float vo[2][8], go[2][3], f[2];
                     for (int s = 0; s < 2; ++s) {
-                        float vc[8];
-                        corners<BF16>(P, planes[ch], cs[s], vc);
-                        col[s][ch] = tri_value_grad(vc, cs[s].fx, cs[s].fy, cs[s].fz, gcol[s][ch]);
+                        corners<BF16>(P, M.occ, cs[s], vo[s]);
+                        f[s] = tri_value_grad(vo[s], cs[s].fx, cs[s].fy, cs[s].fz, go[s]);
                     }
-                float gA = gd * (ds[1] - ds[0]) * inv_n;
-                for (int ch = 0; ch < 3; ++ch) gA += gc[ch] * (col[1][ch] - col[0][ch]);
-                const float inv_df = 1.0f / (f[1] - f[0]);
-                const float gf[2] = {gA * (alpha - 1.0f) * inv_df, -gA * alpha * inv_df};
-                const float wa[2] = {1.0f - alpha, alpha};
-                const float r[3] = {r0, r1, r2};
-                for (int s = 0; s < 2; ++s) {
-                    if (g_occ) scatter(P, g_occ, 1, 0, cs[s], gf[s]);
-                    if (g_rgb)
-                        for (int ch = 0; ch < 3; ++ch) scatter(P, g_rgb, 3, ch, cs[s], gc[ch] * wa[s]);
-                    float gp[3];
-                    for (int a = 0; a < 3; ++a) {
-                        gp[a] = gf[s] * go[s][a];
-                        for (int ch = 0; ch < 3; ++ch) gp[a] += gc[ch] * wa[s] * gcol[s][ch][a];
-                        gp[a] *= P.inv_vs32;
+                    const float alpha = (P.tau32 - f[0]) / (f[1] - f[0]);
+                    const void* planes[3] = {M.r, M.g, M.b};
+                    float col[2][3], gcol[2][3][3];
+                    for (int ch = 0; ch < 3; ++ch)
+                        for (int s = 0; s < 2; ++s) {
+                            float vc[8];
+                            corners<BF16>(P, planes[ch], cs[s], vc);
+                            col[s][ch] = tri_value_grad(vc, cs[s].fx, cs[s].fy, cs[s].fz, gcol[s][ch]);
+                        }
+                    float gA = gd * (ds[1] - ds[0]) * inv_n;
+                    for (int ch = 0; ch < 3; ++ch) gA += gc[ch] * (col[1][ch] - col[0][ch]);
+                    const float inv_df = 1.0f / (f[1] - f[0]);
+                    const float gf[2] = {gA * (alpha - 1.0f) * inv_df, -gA * alpha * inv_df};
+                    const float wa[2] = {1.0f - alpha, alpha};
+                    const float r[3] = {r0, r1, r2};
+                    for (int s = 0; s < 2; ++s) {
+                        if (g_occ) scatter(P, g_occ, 1, 0, cs[s], gf[s]);
+                        if (g_rgb)
+                            for (int ch = 0; ch < 3; ++ch) scatter(P, g_rgb, 3, ch, cs[s], gc[ch] * wa[s]);
+                        float gp[3];
+                        for (int a = 0; a < 3; ++a) {
+                            gp[a] = gf[s] * go[s][a];
+                            for (int ch = 0; ch < 3; ++ch) gp[a] += gc[ch] * wa[s] * gcol[s][ch][a];
+                            gp[a] *= P.inv_vs32;
+                        }
+                        // dL/dt += gp; dL/dtheta += d (r x gp)
+                        gpose[0] += gp[0]; gpose[1] += gp[1]; gpose[2] += gp[2];
+                        gpose[3] += ds[s] * (r[1] * gp[2] - r[2] * gp[1]);
+                        gpose[4] += ds[s] * (r[2] * gp[0] - r[0] * gp[2]);
+                        gpose[5] += ds[s] * (r[0] * gp[1] - r[1] * gp[0]);
                     }
-                    // dL/dt += gp; dL/dtheta += d (r x gp)
-                    gpose[0] += gp[0]; gpose[1] += gp[1]; gpose[2] += gp[2];
-                    gpose[3] += ds[s] * (r[1] * gp[2] - r[2] * gp[1]);
-                    gpose[4] += ds[s] * (r[2] * gp[0] - r[0] * gp[2]);
-                    gpose[5] += ds[s] * (r[0] * gp[1] - r[1] * gp[0]);
                 }
             }
         }

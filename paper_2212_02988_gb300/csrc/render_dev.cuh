@@ -269,7 +269,8 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
                 const int brick = bx + 2 * P.nbx * (by + 2 * P.nby * bz);
                 if (brick != cur_brick) {
                     cur_brick = brick;
-                    cur_skip = render_detail::brick_skippable(P, M.bb, brick);
+                    cur_skip = PRISM_IN_RANGE(P, CHK_RENDER_BRICK, brick, P.bb_len) &&
+                               render_detail::brick_skippable(P, M.bb, brick);
                 }
                 if (cur_skip) {   // no sample of this brick can be a hit: jump past it, or past
                                   // the largest skippable brick above it
@@ -277,7 +278,9 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
                     while (lv < P.nlev) {
                         const int qx = ex >> 1, qy = ey >> 1, qz = ez >> 1;
                         const int dlx = (2 * P.nbx) >> (lv + 1), dly = (2 * P.nby) >> (lv + 1);
-                        if (!render_detail::brick_skippable(P, M.bb + P.bb_off[lv + 1], qx + dlx * (qy + dly * qz)))
+                        const int qi = P.bb_off[lv + 1] + qx + dlx * (qy + dly * qz);
+                        if (!PRISM_IN_RANGE(P, CHK_RENDER_BRICK, qi, P.bb_len) ||
+                            !render_detail::brick_skippable(P, M.bb, qi))
                             break;
                         ex = qx; ey = qy; ez = qz;
                         ++lv;
@@ -298,6 +301,7 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
                 pfx = flx; pfy = fly; pfz = flz;
                 fresh = false;
             }
+            if (!PRISM_IN_RANGE(P, CHK_RENDER_CORNER, (long long)cur.base + pxy + px + 1, P.npad)) break;
             if constexpr (NS > 1 && !DETAIL) {
                 // samples k .. k + NS - 1 together: their 8 NS corner loads are
                 // in flight at once.  A sample past kmax or leaving the grid
@@ -313,9 +317,10 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
                 for (int j = 1; j < NS; ++j) {
                     const float dj = __fmul_rn(kf + (float)j, P.eps32);
                     const float jx = __fmaf_rn(dj, rgx, cgx), jy = __fmaf_rn(dj, rgy, cgy), jz = __fmaf_rn(dj, rgz, cgz);
-                    ok[j] = ok[j - 1] && k + j <= P.kmax &&
-                            (k + j <= k_safe || (jx >= -0.5f && jx < hx && jy >= -0.5f && jy < hy && jz >= -0.5f && jz < hz));
                     const render_detail::Sample sj = render_detail::cell_of(px, pxy, jx, jy, jz);
+                    ok[j] = ok[j - 1] && k + j <= P.kmax &&
+                            (k + j <= k_safe || (jx >= -0.5f && jx < hx && jy >= -0.5f && jy < hy && jz >= -0.5f && jz < hz)) &&
+                            PRISM_IN_RANGE(P, CHK_RENDER_CORNER, (long long)sj.base + pxy + px + 1, P.npad);
                     cs[j] = cur;
                     if (ok[j]) cs[j] = sj;
                 }
@@ -363,21 +368,23 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
             const float d1 = __fmul_rn((float)(k - 1), P.eps32);
             const render_detail::Sample prev = render_detail::cell_of(px, pxy, __fmaf_rn(d1, rgx, cgx), __fmaf_rn(d1, rgy, cgy),
                                         __fmaf_rn(d1, rgz, cgz));
-            // sample k - 1 was jumped over: its value, by the same recipe
-            if (!prev_ok) f_prev = render_detail::trilinear<BF16, PX>(M.occ, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            const float alpha = __fdiv_rn(P.tau32 - f_prev, f - f_prev);
-            const float dk = __fmul_rn((float)k, P.eps32);
-            const float dstar = fmaf(alpha, dk - d1, d1);
-            out_d = dstar * inv_n;
-            float a1 = render_detail::trilinear<BF16, PX>(M.r, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            float a0 = render_detail::trilinear<BF16, PX>(M.r, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            out_r = fmaf(alpha, a1 - a0, a0);
-            a1 = render_detail::trilinear<BF16, PX>(M.g, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            a0 = render_detail::trilinear<BF16, PX>(M.g, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            out_g = fmaf(alpha, a1 - a0, a0);
-            a1 = render_detail::trilinear<BF16, PX>(M.b, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
-            a0 = render_detail::trilinear<BF16, PX>(M.b, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
-            out_b = fmaf(alpha, a1 - a0, a0);
+            if (PRISM_IN_RANGE(P, CHK_RENDER_CORNER, (long long)prev.base + pxy + px + 1, P.npad)) {
+                // sample k - 1 was jumped over: its value, by the same recipe
+                if (!prev_ok) f_prev = render_detail::trilinear<BF16, PX>(M.occ, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
+                const float alpha = __fdiv_rn(P.tau32 - f_prev, f - f_prev);
+                const float dk = __fmul_rn((float)k, P.eps32);
+                const float dstar = fmaf(alpha, dk - d1, d1);
+                out_d = dstar * inv_n;
+                float a1 = render_detail::trilinear<BF16, PX>(M.r, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+                float a0 = render_detail::trilinear<BF16, PX>(M.r, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
+                out_r = fmaf(alpha, a1 - a0, a0);
+                a1 = render_detail::trilinear<BF16, PX>(M.g, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+                a0 = render_detail::trilinear<BF16, PX>(M.g, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
+                out_g = fmaf(alpha, a1 - a0, a0);
+                a1 = render_detail::trilinear<BF16, PX>(M.b, cur.base, px, pxy, cur.fx, cur.fy, cur.fz);
+                a0 = render_detail::trilinear<BF16, PX>(M.b, prev.base, px, pxy, prev.fx, prev.fy, prev.fz);
+                out_b = fmaf(alpha, a1 - a0, a0);
+            }
         }
         const int p = v * P.W + u;
         if (depth) depth[p] = out_d;
@@ -473,7 +480,10 @@ __device__ __forceinline__ void render_plan_block(const KParams& P, const Render
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) in.order[atomicAdd(&base[in.key[t]], 1u)] = t;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const uint32_t pos = atomicAdd(&base[in.key[t]], 1u);
+        if (PRISM_IN_RANGE(P, CHK_PLAN, pos, nt)) in.order[pos] = t;
+    }
 }
 
 __device__ __forceinline__ void depth_mask_px(const KParams& P, const float* __restrict__ depth,

@@ -137,6 +137,7 @@ struct prism_server {
     prism_serve_config cfg{};
     int sms = 152;
     cudaStream_t stream = nullptr;
+    unsigned long long* check = nullptr;   // bounds-check build: the first violation of any stream
     BatchGrids grids{};
     SlotDesc* d_slots = nullptr;
     SlotDesc* h_slots = nullptr;   // pinned staging of slot-table entries
@@ -487,6 +488,7 @@ void free_server(prism_server* S) {
     }
     S->streams.clear();
     if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->check) cudaFree(S->check);
     if (S->gexec) cudaGraphExecDestroy(S->gexec);
     if (S->graph) cudaGraphDestroy(S->graph);
     for (auto& R : S->ring) {
@@ -552,6 +554,10 @@ prism_status prism_serve_create(const prism_serve_config* c, prism_server_handle
     ok(cudaMalloc(&S->d_desc, sizeof(BatchDesc)));
     ok(cudaMalloc(&S->d_imu, sizeof(double) * 7 * kImuCap));
     ok(cudaMalloc(&S->d_out, sizeof(ServeOut) * kServeMaxSlots));
+#ifdef PRISM_CHECKED
+    ok(cudaMalloc(&S->check, sizeof(unsigned long long)));
+    if (e == cudaSuccess) ok(cudaMemsetAsync(S->check, 0, sizeof(unsigned long long), S->stream));
+#endif
     for (auto& R : S->ring) {
         ok(cudaMallocHost(&R.desc, sizeof(BatchDesc)));
         ok(cudaMallocHost(&R.imu, sizeof(double) * 7 * kImuCap));
@@ -625,6 +631,7 @@ prism_status prism_serve_open(prism_server_handle S, const prism_config* cfg, co
     st->cfg.storage = S->cfg.storage;
     st->cfg.n_gn = S->cfg.n_gn;
     fill_kparams(&st->cfg, st->kp);
+    st->kp.check = S->check;
     if (s1) {
         st->s1 = *s1;
     } else {
@@ -721,6 +728,21 @@ prism_status prism_serve_drain(prism_server_handle S, int32_t timeout_ms) {
                                         [&] { return idle(S) || S->failed; });
     if (S->failed) return PRISM_ECUDA;
     if (!ok) { S->err = "drain timed out"; return PRISM_ESTATE; }
+    return PRISM_OK;
+}
+
+prism_status prism_serve_check_status(prism_server_handle S, uint64_t* word) {
+    if (!S || !word) return sfail(S, PRISM_EINVAL, "server or word is NULL");
+    *word = 0;
+    if (!S->check) return PRISM_OK;
+    unsigned long long v = 0;
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, S->check, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(S, PRISM_ECUDA, std::string("check status: ") + cudaGetErrorString(e));
+    }
+    *word = v;
     return PRISM_OK;
 }
 

@@ -209,6 +209,12 @@ __device__ __forceinline__ void track_fetch(const KParams& P, const float* sM, c
     q.cc = __fsub_rn(q.vp, bv);
     if (q.ok) {
         const int b00 = (int)bv * W + (int)bu;
+        q.ok = PRISM_IN_RANGE(P, CHK_TRACK_ANCHOR, q.iv * W + q.iu, (long long)W * P.H) &&
+               PRISM_IN_RANGE(P, CHK_TRACK_ANCHOR, b00, (long long)W * P.H) &&
+               PRISM_IN_RANGE(P, CHK_TRACK_ANCHOR, b00 + W + 1, (long long)W * P.H);
+    }
+    if (q.ok) {
+        const int b00 = (int)bv * W + (int)bu;
         q.A = a0[q.iv * W + q.iu];
         q.I00 = a1[b00];
         q.I10 = a1[b00 + 1];
@@ -357,7 +363,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (tid < N) {   // partials are stored value-major: partials[v * pstride + block]
         float s = swarp[0][tid];
         for (int w = 1; w < kWarps; ++w) s += swarp[w][tid];
-        partials[(size_t)tid * pstride + vb] = s;
+        if (PRISM_IN_RANGE(P, CHK_TRACK_PARTIAL, vb, pstride)) partials[(size_t)tid * pstride + vb] = s;
     }
     __syncthreads();
     // Ticket: the acq_rel atomic releases this block's partials (ordered

@@ -366,3 +366,10 @@ class Filter:
 
     def device_bytes(self) -> int:
         return int(self.L.prism_device_bytes(self.h))
+
+    def check_status(self) -> int:
+        """The bounds-check build's first index violation on this handle (0:
+        none; always 0 in the plain build): prism_check_status."""
+        w = C.c_uint64(0)
+        self._check(self.L.prism_check_status(self.h, C.byref(w)), self.h)
+        return int(w.value)

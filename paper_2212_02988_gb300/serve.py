@@ -134,6 +134,13 @@ class Server:
         self._check(self.L.prism_serve_get_stats(self.h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in ServeStats._fields_ if k != "reserved"}
 
+    def check_status(self) -> int:
+        """The bounds-check build's first index violation of any stream (0:
+        none; always 0 in the plain build): prism_serve_check_status."""
+        w = C.c_uint64(0)
+        self._check(self.L.prism_serve_check_status(self.h, C.byref(w)))
+        return int(w.value)
+
     def map_store(self, sid: int, shape) -> dict:
         nz, ny, nx = shape
         dev = torch.device("cuda", self.device)
