@@ -98,7 +98,8 @@ def test_skipping_on_a_non_cubic_grid(oracle_mod):
 
 @pytest.mark.parametrize("name,storage,start", [("room128_320x240", "f32", "prior"),
                                                 ("room128_320x240", "bf16", "prior"),
-                                                ("room256_640x480", "f32", "settled")])
+                                                ("room256_640x480", "f32", "settled"),
+                                                ("tiny_83x61", "f32", "prior")])
 def test_skipping_changes_no_filter_step(oracle_mod, name, storage, start):
     """From the prior map the fuse writes the tile bounds the render skips
     by; every state and the final map agree bit for bit.  With skipping, the
@@ -106,7 +107,8 @@ def test_skipping_changes_no_filter_step(oracle_mod, name, storage, start):
     last anchor render's tile costs (from the second step on), which must
     change nothing either."""
     from paper_2212_02988_gb300 import state_arrays
-    w = synth.PRESETS[name]
+    # tiny_83x61: a ragged image (6 x 8 tiles of 16x8, the last column and row partial)
+    w = synth.tiny(n=32, width=83, height=61) if name == "tiny_83x61" else synth.PRESETS[name]
     s = synth.Sequence(w, n_frames=6)
     frames = [s.frame(i) for i in range(5)]
     runs = {}
