@@ -273,19 +273,23 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
                                render_detail::brick_skippable(P, M.bb, brick);
                 }
                 if (cur_skip) {   // no sample of this brick can be a hit: jump past it, or past
-                                  // the largest skippable brick above it
-                    int lv = 0, ex = bx, ey = by, ez = bz;
-                    while (lv < P.nlev) {
-                        const int qx = ex >> 1, qy = ey >> 1, qz = ez >> 1;
-                        const int dlx = (2 * P.nbx) >> (lv + 1), dly = (2 * P.nby) >> (lv + 1);
-                        const int qi = P.bb_off[lv + 1] + qx + dlx * (qy + dly * qz);
-                        if (!PRISM_IN_RANGE(P, CHK_RENDER_BRICK, qi, P.bb_len) ||
-                            !render_detail::brick_skippable(P, M.bb, qi))
-                            break;
-                        ex = qx; ey = qy; ez = qz;
-                        ++lv;
+                                  // the largest skippable brick above it (the bounds of the
+                                  // ancestors are loaded together, then the unbroken chain
+                                  // of skippable ones is climbed)
+                    bool up[3];
+#pragma unroll
+                    for (int l = 1; l <= 3; ++l) {
+                        up[l - 1] = false;
+                        if (l <= P.nlev) {
+                            const int dlx = (2 * P.nbx) >> l, dly = (2 * P.nby) >> l;
+                            const int qi = P.bb_off[l] + (bx >> l) + dlx * ((by >> l) + dly * (bz >> l));
+                            up[l - 1] = PRISM_IN_RANGE(P, CHK_RENDER_BRICK, qi, P.bb_len) &&
+                                        render_detail::brick_skippable(P, M.bb, qi);
+                        }
                     }
-                    const int kn = render_detail::brick_exit(P, lv, ex, ey, ez, irgx, irgy, irgz, cgx, cgy, cgz, ieps);
+                    const int lv = up[0] ? (up[1] ? (up[2] ? 3 : 2) : 1) : 0;
+                    const int kn = render_detail::brick_exit(P, lv, bx >> lv, by >> lv, bz >> lv, irgx, irgy, irgz,
+                                                             cgx, cgy, cgz, ieps);
                     k = kn > k ? kn : k + 1;
                     kf = (float)k;
                     prev_ok = false;
