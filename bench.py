@@ -159,21 +159,22 @@ def render_source_hash():
 
 
 def profiled_traffic(workload: str, kernel: str = "k_render"):
-    """DRAM bytes per launch of `kernel` from its committed ncu summary, if
-    it was taken on the current sources; else None."""
+    """DRAM bytes per launch (or, where the summary gives it, per pass) of
+    `kernel` from its committed ncu summary, if it was taken on the current
+    sources; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch")):
+        if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch", "dram_bytes_per_pass")):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_sha256") != source_hash(kernel):
         return None
     try:
-        return int(float(vals["dram_bytes_per_launch"]))
-    except (KeyError, ValueError):
+        return int(float(vals.get("dram_bytes_per_pass", vals.get("dram_bytes_per_launch"))))
+    except (TypeError, ValueError):
         return None
 
 
@@ -539,17 +540,18 @@ def run_ours(args, rank, world, local_rank):
                                       "samples the kernel evaluates"},
         "phase_ms_per_step": {k[:-3]: tm[k] / max(tm[k[:-3] + "_n"], 1) for k in
                               ("predict_ms", "localise_ms", "fuse_ms", "render_ms", "anchor_ms")},
-        "roofline": {"kernel": "k_track<GN> (one Gauss-Newton pass)", "bound": "hbm",
+        "roofline": {"kernel": "Gauss-Newton pass (k_track_coop: passes 2-10 in one cooperative launch; "
+                               "k_track<GN>: pass 1)", "bound": "hbm",
                      "achieved": gn_bytes / (gn_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": gn_bytes / (gn_ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
                      "traffic": profiled_traffic(args.workload, "k_track_gn"),
                      "algorithmic_bytes": "%d B per observed pixel (observation 16 B + anchor gathers 56 B) x %d "
-                                          "pixels, per launch" % (GN_BYTES_PER_PIXEL, npx),
-                     "bytes_per_launch": gn_bytes, "ms_per_launch": gn_ms, "launches_per_step": cfg.n_gn,
-                     "note": "the dominant kernel by device time (10 launches a step); latency-bound: the pixel "
-                             "loop over all SMs, then a one-block FP64 finish (solve, retraction) while the "
-                             "other SMs wait; ms_per_launch = (localisation - Laplace pass) / passes, from "
-                             "the library's CUDA events on its stream"},
+                                          "pixels, per pass" % (GN_BYTES_PER_PIXEL, npx),
+                     "bytes_per_pass": gn_bytes, "ms_per_pass": gn_ms, "passes_per_step": cfg.n_gn,
+                     "note": "the dominant kernel by device time (10 passes a step); latency-bound: the pixel "
+                             "loop over all SMs, a grid barrier, then the FP64 finish (solve, retraction) that "
+                             "every block repeats; ms_per_pass = (localisation - Laplace pass) / passes, from "
+                             "the library's CUDA events on its stream; traffic is per pass"},
         "roofline_render": {"kernel": "k_render", "bound": "instruction issue (ncu: issue-active, L1-resident "
                                                            "map; DRAM carries a few MB a launch)",
                             "achieved_unique": achieved_U, "achieved_gathered": achieved_G, "peak": peak,

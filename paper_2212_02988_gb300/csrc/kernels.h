@@ -83,6 +83,16 @@ cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s, bool pdl = true, uint8_t* mask_out = nullptr);
+// Gauss-Newton passes 1 .. passes of a localisation in one cooperative
+// launch (every block resident; a grid barrier between passes, the FP64
+// finish in every block; track_item's COOP).  partials: two buffers of
+// TRACK_NV_MAX x max_blocks floats; barrier: a counter this launch starts
+// from zero (the caller clears it on the stream first).  Returns
+// cudaErrorCooperativeLaunchTooLarge (launching nothing) when the grid
+// cannot be resident at once.
+cudaError_t launch_track_coop(const KParams& P, const float* o_depth, const float* o_rgb, const uint8_t* o_mask,
+                              const float4* a0, const float4* a1, DevState* dev, float* partials,
+                              unsigned int* barrier, int max_blocks, DevStats* stats, int passes, cudaStream_t s);
 int track_grid(const KParams& P, int mode, int max_blocks);
 // The grid launch_track uses for `mode` (one wave of the device at most).
 int track_launch_grid(const KParams& P, int mode, int max_blocks);

@@ -363,6 +363,10 @@ prism_status check_flags(prism_handle h, int flags) {
         if (flags & FLAG_GN_NOTPD) m += " Gauss-Newton system not positive definite;";
         if (flags & FLAG_LAPLACE_NOTPD) m += " Laplace Hessian not positive definite;";
         if (flags & FLAG_PRIOR_NOTPD) m += " prior pose covariance not positive definite;";
+        if (flags & FLAG_SYNC_TIMEOUT) {
+            m += " a grid-wide wait of the localisation timed out; the step was rejected (state and map unchanged)";
+            return fail(h, PRISM_ECUDA, m);
+        }
         m += " the step was rejected (state and map unchanged)";
         return fail(h, PRISM_ENOTPD, m);
     }
@@ -486,12 +490,26 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb, b
         return PRISM_OK;
     }
     // the first pass also evaluates the observation's depth validity into o_mask
-    // (read by the later passes and by the fuse)
-    for (int it = 0; it < h->cfg.n_gn; ++it)
+    // (read by the later passes and by the fuse), and clears the barrier of the
+    // cooperative launch that runs the other passes (a pass per launch where
+    // the device cannot hold that launch's grid at once)
+    int it = 0;
+    for (; it < h->cfg.n_gn; ++it) {
+        if (it == 1) {
+            cudaError_t e = launch_track_coop(h->kp, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
+                                              h->counter + 1, h->max_blocks, h->dstats, h->cfg.n_gn - 1, h->stream);
+            if (e == cudaSuccess) {
+                ++h->launches;
+                break;
+            }
+            if (e != cudaErrorCooperativeLaunchTooLarge) return cuda_fail(h, e, "Gauss-Newton passes");
+            cudaGetLastError();
+        }
         LAUNCH(h, launch_track(h->kp, TRACK_GN, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                            h->counter, h->max_blocks, h->dstats, h->stream, !(prepped && it == 0),
                            it == 0 ? h->o_mask : nullptr),
            "Gauss-Newton pass");
+    }
     {
         PhaseTimer tl(h, PH_LAPLACE);
         LAUNCH(h, launch_track(h->kp, TRACK_LAPLACE, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
@@ -715,8 +733,8 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
     if (dalloc(h, &h->a_depth, npix * 4) || dalloc(h, &h->a_rgb, npix * 12) ||
         dalloc(h, &h->a0, npix * 16) || dalloc(h, &h->a1, npix * 16) || dalloc(h, &h->o_mask, npix) ||
         dalloc(h, &h->dstate, sizeof(DevState)) || dalloc(h, &h->dstats, sizeof(DevStats)) ||
-        dalloc(h, &h->partials, (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(float)) ||
-        dalloc(h, &h->counter, sizeof(unsigned int)) ||
+        dalloc(h, &h->partials, 2 * (size_t)h->max_blocks * TRACK_NV_MAX * sizeof(float)) ||
+        dalloc(h, &h->counter, 2 * sizeof(unsigned int)) ||
         dalloc(h, &h->fuse_list, (size_t)h->kp.nbx * h->kp.nby * h->kp.nbz * sizeof(int)) ||
         dalloc(h, &h->fuse_ctr, 2 * sizeof(unsigned int)))
         return cleanup(PRISM_ENOMEM, "device allocation failed");
@@ -758,7 +776,7 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         (e = launch_tile_bounds(h->kp, h->map, h->stream)) != cudaSuccess)
         return cleanup(PRISM_ECUDA, std::string("map fill: ") + cudaGetErrorString(e));
     if ((e = cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->counter, 0, 2 * sizeof(unsigned int), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->fuse_ctr, 0, 2 * sizeof(unsigned int), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->dstate, 0, sizeof(DevState), h->stream)) != cudaSuccess)
         return cleanup(PRISM_ECUDA, std::string("memset: ") + cudaGetErrorString(e));

@@ -135,14 +135,15 @@ struct DevState {
     float rel[12];             // Gauss-Newton pose -> anchor camera: M (9), b (3)
     float aux[12];             // a pose given by the host (render or one objective evaluation)
     int n_localised;
-    int flags;                 // bit 0: GN system not PD; bit 1: Laplace system not PD; bit 2: prior not PD
+    int flags;                 // bit 0: GN system not PD; bit 1: Laplace system not PD; bit 2: prior not PD;
+                               // bit 3: a grid-wide wait of the localisation timed out
                                // (cleared by each prediction, set by the kernels of that step)
     int rejected;              // the last localisation raised a flag: the posterior was left as it was and
                                // the step's map update lists no tile (0 after creation or a state write)
     int pad1;
 };
 
-enum : int { FLAG_GN_NOTPD = 1, FLAG_LAPLACE_NOTPD = 2, FLAG_PRIOR_NOTPD = 4 };
+enum : int { FLAG_GN_NOTPD = 1, FLAG_LAPLACE_NOTPD = 2, FLAG_PRIOR_NOTPD = 4, FLAG_SYNC_TIMEOUT = 8 };
 
 // Work counters (device, accumulated with warp-aggregated atomics).
 struct DevStats {

@@ -45,6 +45,9 @@ struct Block {
     static constexpr int warps = threads / 32;
 };
 constexpr int kMaxPerLane = 16;   // partials per lane in the last block: grid <= 512
+// The cooperative passes' grid barrier polls at most this often (each poll
+// an L2 round trip of ~0.5 us: about a second) before it gives up.
+constexpr unsigned int kCoopSpinLimit = 1u << 21;
 
 template <int MODE>
 struct NV {
@@ -292,13 +295,24 @@ using namespace track_detail;
 // that takes the virtual blocks one by one give the same bits.  MASKGEN:
 // the observed pixels' depth validity is evaluated from od and written to
 // om_out (the pass then needs no mask pass before it).
-template <int MODE, bool MASKGEN = false>
-__device__ __forceinline__ void track_item(const KParams& P, const float* __restrict__ od,
+//
+// COOP (Gauss-Newton only): pass `pass` of a cooperative launch whose nvb
+// blocks are all resident.  In place of the ticket every block waits at a
+// grid barrier (*counter reaching nvb (pass + 1), a bounded spin), sums all
+// partials in the same fixed order and runs the same FP64 finish, so every
+// block holds the identical next iterate and its matrices in shared memory
+// and goes on to the next pass without a launch; block 0 also writes them
+// to the device state.  Partials alternate between two buffers by pass.
+// Returns false when the launch's passes must stop (a system that is not
+// positive definite, or a barrier that timed out; both raise a flag).
+template <int MODE, bool MASKGEN = false, bool COOP = false>
+__device__ __forceinline__ bool track_item(const KParams& P, const float* __restrict__ od,
                                            const float* __restrict__ orgb, const uint8_t* __restrict__ om,
                                            const float4* __restrict__ a0, const float4* __restrict__ a1,
                                            DevState* dev, float* __restrict__ partials, int pstride,
                                            unsigned int* __restrict__ counter, DevStats* __restrict__ stats,
-                                           int vb, int nvb, uint8_t* __restrict__ om_out = nullptr) {
+                                           int vb, int nvb, uint8_t* __restrict__ om_out = nullptr, int pass = 0) {
+    static_assert(!COOP || MODE == TRACK_GN, "the cooperative passes are Gauss-Newton passes");
     constexpr int N = NV<MODE>::value;
     constexpr int kThreads = Block<MODE>::threads, kWarps = Block<MODE>::warps;
     using L = Layout<MODE>;
@@ -313,21 +327,25 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // Every block starts copying the state the last block's finish will need
     // (written by earlier kernels), so that it is in shared memory when the
-    // last ticket is drawn.
-    if (tid < kStage) {
-        const double* src = stage_src<MODE>(dev, tid);
-        if (src) cp_async(&st[tid], src, 8);
-    } else if (MODE == TRACK_LAPLACE && tid == kStage) {
-        cp_async(&s_nloc, &dev->n_localised, 4);
-    } else if (MODE == TRACK_LAPLACE && tid == kStage + 1) {
-        cp_async(&s_flags, &dev->flags, 4);
-    }
-    if (tid < 12) {
-        const float* mats = MODE == TRACK_EXPORT ? dev->aux : dev->rel;
-        if (tid < 9) sM[tid] = mats[tid];
-        else sb[tid - 9] = mats[tid];
+    // last ticket is drawn.  (A cooperative launch's later passes find it,
+    // and the pass's matrices, in shared memory from the pass before.)
+    if (!COOP || pass == 0) {
+        if (tid < kStage) {
+            const double* src = stage_src<MODE>(dev, tid);
+            if (src) cp_async(&st[tid], src, 8);
+        } else if (MODE == TRACK_LAPLACE && tid == kStage) {
+            cp_async(&s_nloc, &dev->n_localised, 4);
+        } else if (MODE == TRACK_LAPLACE && tid == kStage + 1) {
+            cp_async(&s_flags, &dev->flags, 4);
+        }
+        if (tid < 12) {
+            const float* mats = MODE == TRACK_EXPORT ? dev->aux : dev->rel;
+            if (tid < 9) sM[tid] = mats[tid];
+            else sb[tid - 9] = mats[tid];
+        }
     }
     __syncthreads();
+    float* const pbuf = COOP ? partials + (size_t)(pass & 1) * N * pstride : partials;
 
     float acc[N];
 #pragma unroll
@@ -363,17 +381,44 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
     if (tid < N) {   // partials are stored value-major: partials[v * pstride + block]
         float s = swarp[0][tid];
         for (int w = 1; w < kWarps; ++w) s += swarp[w][tid];
-        if (PRISM_IN_RANGE(P, CHK_TRACK_PARTIAL, vb, pstride)) partials[(size_t)tid * pstride + vb] = s;
+        if (PRISM_IN_RANGE(P, CHK_TRACK_PARTIAL, vb, pstride)) pbuf[(size_t)tid * pstride + vb] = s;
     }
     __syncthreads();
-    // Ticket: the acq_rel atomic releases this block's partials (ordered
-    // before it by the barrier) and, for the last block, acquires everyone's.
-    if (tid == 0) {
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> ticket(*counter);
-        s_last = ticket.fetch_add(1u, cuda::memory_order_acq_rel) == nvb - 1;
+    if constexpr (COOP) {
+        // Grid barrier: the release add publishes this block's partials; the
+        // acquire load that sees all nvb arrivals of this pass makes everyone's
+        // visible.  Bounded: past the limit the block raises FLAG_SYNC_TIMEOUT
+        // and the launch's passes stop (the step is then rejected).
+        if (tid == 0) {
+            cuda::atomic_ref<unsigned int, cuda::thread_scope_device> bar(*counter);
+            bar.fetch_add(1u, cuda::memory_order_release);
+            const unsigned int target = (unsigned int)nvb * (unsigned int)(pass + 1);
+            unsigned int spins = 0;
+            int ok = 1;
+            while (bar.load(cuda::memory_order_acquire) < target) {
+                if (++spins > kCoopSpinLimit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            s_last = ok;
+        }
+        __syncthreads();
+        if (!s_last) {
+            if (tid == 0) atomicOr(&dev->flags, FLAG_SYNC_TIMEOUT);
+            return false;
+        }
+    } else {
+        // Ticket: the acq_rel atomic releases this block's partials (ordered
+        // before it by the barrier) and, for the last block, acquires everyone's.
+        if (tid == 0) {
+            cuda::atomic_ref<unsigned int, cuda::thread_scope_device> ticket(*counter);
+            s_last = ticket.fetch_add(1u, cuda::memory_order_acq_rel) == nvb - 1;
+        }
+        __syncthreads();
+        if (!s_last) return true;
     }
-    __syncthreads();
-    if (!s_last) return;
 
     // ---- last block ----
     // The staged FP64 state (st, s_nloc) arrived during the pixel loop: GB300's
@@ -395,7 +440,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
         const int v = warp + kWarps * q;
-        const float4* row = reinterpret_cast<const float4*>(partials + (size_t)(v < N ? v : 0) * pstride);
+        const float4* row = reinterpret_cast<const float4*>(pbuf + (size_t)(v < N ? v : 0) * pstride);
 #pragma unroll
         for (int j = 0; j < kQuads; ++j) {
             const int b = 4 * (lane + 32 * j);
@@ -420,10 +465,12 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         if (lane == 0 && v < N) S[v] = (double)s;
     }
     __syncthreads();
-    if (tid == 0) {
-        *counter = 0u;
-        if (stats) atomicAdd(&stats->track_pixels, (unsigned long long)S[L::oCount]);
-    }
+    if (tid == 0 && !COOP) *counter = 0u;
+    // the first Gauss-Newton pass of a localisation (the one that evaluates the
+    // depth validity) also clears counter[1], the barrier of the cooperative
+    // launch of the passes that follow it (launch_track_coop)
+    if (tid == 0 && MODE == TRACK_GN && MASKGEN && !COOP) counter[1] = 0u;
+    if (tid == 0 && (!COOP || vb == 0) && stats) atomicAdd(&stats->track_pixels, (unsigned long long)S[L::oCount]);
 
     // sm[0]: Ra; sm[1]: H' (sym); sm[2]: Ht' (sym); sm[3], sm[4]: world-frame H, Ht
     double* Ra = sm[0];
@@ -470,7 +517,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             dev->ne_out[78] = S[L::oCost];
             dev->ne_out[79] = S[L::oCount];
         }
-        return;
+        return true;
     }
 
     if (MODE == TRACK_GN) {
@@ -520,9 +567,12 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
         }
         __syncthreads();
         if (!s_pd) {
-            if (tid == 0) dev->flags |= FLAG_GN_NOTPD;
-            return;
+            if (tid == 0 && (!COOP || vb == 0)) atomicOr(&dev->flags, FLAG_GN_NOTPD);
+            return false;
         }
+        // where the next pass's terms go: the device state, or (COOP) this
+        // block's shared copies, which block 0 also writes to the device
+        const bool to_dev = !COOP || vb == 0;
         if (warp == 0) {
             // The FP32 pose -> anchor matrices of the next pass, straight from
             // xi (the critical path): Ra^T Exp(xi_theta) R_prior = Exp(w) A0 with
@@ -543,17 +593,41 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
                          q2 = __shfl_sync(0xffffffffu, qr, 2), q3 = __shfl_sync(0xffffffffu, qr, 3);
             const double me = quat_R_entry_rn(q0, q1, q2, q3, lane < 9 ? lane : 0);
             const double be = st[120 + r] + d;
-            if (lane < 9) dev->rel[lane] = (float)me;
-            else if (tl) dev->rel[lane] = (float)be;
+            if (COOP) {
+                if (lane < 9) sM[lane] = (float)me;
+                else if (tl) sb[lane - 9] = (float)be;
+            }
+            if (to_dev) {
+                if (lane < 9) dev->rel[lane] = (float)me;
+                else if (tl) dev->rel[lane] = (float)be;
+            }
         } else if (warp == 1) {   // the FP64 pose of the new iterate (the state mean after the last pass)
             const double qn = warp_quat_exp_mul_unit(xn + 3, st + 49);
-            if (lane < 4) dev->cur_pose[3 + lane] = qn;
-            if (lane < 3) dev->cur_pose[lane] = st[53 + lane] + xn[lane];
-            if (lane < 6) dev->xi[lane] = xn[lane];
+            if (to_dev) {
+                if (lane < 4) dev->cur_pose[3 + lane] = qn;
+                if (lane < 3) dev->cur_pose[lane] = st[53 + lane] + xn[lane];
+                if (lane < 6) dev->xi[lane] = xn[lane];
+            }
+            if (COOP && lane < 6) st[36 + lane] = xn[lane];
         } else if (warp == 2) {   // meanwhile: the prior's anchor-frame terms of the new iterate
-            warp_gn_prior_terms(Ci, st, xn, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, dev->gn_Ji, &sm[2][0]);
+            if (!COOP) {
+                warp_gn_prior_terms(Ci, st, xn, dev->gn_Ci + 9, dev->gn_Lp, dev->gn_m, dev->gn_Ji, &sm[2][0]);
+            } else {   // into the staged slots (Ci's second block, L', m), J_l^-1 beside them
+                double* ji = &sm[5][0];   // (the scratch takes sm[2] and part of sm[3])
+                warp_gn_prior_terms(Ci, st, xn, st + 65, st + 74, st + 110, ji, &sm[2][0]);
+                __syncwarp();
+                if (to_dev) {
+                    for (int e = lane; e < 60; e += 32) {
+                        if (e < 9) dev->gn_Ci[9 + e] = st[65 + e];
+                        else if (e < 45) dev->gn_Lp[e - 9] = st[74 + e - 9];
+                        else if (e < 51) dev->gn_m[e - 45] = st[110 + e - 45];
+                        else dev->gn_Ji[e - 51] = ji[e - 51];
+                    }
+                }
+            }
         }
-        return;
+        if (COOP) __syncthreads();   // the next pass reads the new terms and matrices
+        return true;
     }
 
     // MODE == TRACK_LAPLACE.  Divergence guard: a flag raised by this step's
@@ -566,7 +640,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             dev->ne_out[78] = S[L::oCost];
             dev->ne_out[79] = S[L::oCount];
         }
-        return;
+        return true;
     }
     // Sigma = (2 Ht + Mi^T L Mi)^-1 in world-frame perturbations, Mi =
     // diag(I, J_l(xi_theta)^-1).  With Ht = T Ht' T^T (T = diag(Ra, Ra), Ht' the
@@ -629,7 +703,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             dev->ne_out[78] = S[L::oCost];
             dev->ne_out[79] = S[L::oCount];
         }
-        return;
+        return true;
     }
     if (tid < 36) {   // U = Sa T^T: U[r][j] = sum_l Sa[r][3 bj + l] Ra[jj][l]
         const int r = tid / 6, j = tid % 6, bj = j / 3, jj = j % 3;
@@ -690,6 +764,7 @@ __device__ __forceinline__ void track_item(const KParams& P, const float* __rest
             dev->ne_out[79] = S[L::oCount];
         }
     }
+    return true;
 }
 
 }  // namespace prism
