@@ -46,7 +46,7 @@ def main(path):
     words = []
 
     # filter steps from the prior map (the plan orders the anchor render from the second step on)
-    for name, storage in (("room64_80x60", "f32"), ("room64_80x60", "bf16")):
+    for name, storage in (("room64_80x60", "f32"), ("room64_80x60", "bf16"), ("room128_320x240", "f32")):
         w = synth.PRESETS[name]
         s = synth.Sequence(w, n_frames=8)
         F = Filter(config(w.n, w.extent, w.width, w.height, storage=storage), make_state(s.pose7(0), s.velocity(0)),
@@ -57,16 +57,17 @@ def main(path):
             f = s.frame(i)
             st.append(state_arrays(F.step(s.imu_window(i) if i else None, w.dt, t(f["depth"]), t(f["rgb"]),
                                           want_state=True)))
-        out[f"{storage}_pose"] = np.array([x["pose"] for x in st])
-        out[f"{storage}_cov"] = np.array([x["cov"] for x in st])
+        key = f"{name}_{storage}"
+        out[f"{key}_pose"] = np.array([x["pose"] for x in st])
+        out[f"{key}_cov"] = np.array([x["cov"] for x in st])
         m = F.map_store()
-        out[f"{storage}_occ"] = m["occ"].cpu().numpy()
+        out[f"{key}_occ"] = m["occ"].cpu().numpy()
         r = F.render(s.pose7(6))
-        out[f"{storage}_hitk"] = r["hitk"].cpu().numpy()
+        out[f"{key}_hitk"] = r["hitk"].cpu().numpy()
         # rollouts: two sequences of three frames
         wins = [[s.imu_window(i) for i in range(1, 4)], [s.imu_window(i) for i in range(3, 6)]]
         ro = F.rollout(wins, w.dt, hitk=True)
-        out[f"{storage}_roll_hitk"] = ro["hitk"].cpu().numpy()
+        out[f"{key}_roll_hitk"] = ro["hitk"].cpu().numpy()
         words.append(F.check_status())
         F.close()
 

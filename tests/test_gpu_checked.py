@@ -1,13 +1,14 @@
 """The bounds-check build (libprism_checked.so, prism_check_status in
 include/prism.h): on small workloads through every kernel family -- filter
-steps in both storages with the planned anchor-render order, renders of a
-ragged image from cameras inside and outside the grid, the render adjoint,
-rollouts, a map-descent step, two streams through the server -- it records
-no index violation, and its results are bit-identical to the plain
-library's (the tests change no arithmetic) except for the sums formed by
-atomic adds (the adjoint's gradients, the map loss), whose order varies from
-run to run in either library.  Each build runs in its own
-process (the binding loads one library per process)."""
+steps in both storages with the planned anchor-render order (80x60 and
+320x240; the Gauss-Newton passes after the first in one cooperative
+launch), renders of a ragged image from cameras inside and outside the
+grid, the render adjoint, rollouts, a map-descent step, two streams through
+the server -- it records no index violation, and its results are
+bit-identical to the plain library's (the tests change no arithmetic)
+except for the sums formed by atomic adds (the adjoint's gradients, the map
+loss), whose order varies from run to run in either library.  Each build
+runs in its own process (the binding loads one library per process)."""
 import os
 import subprocess
 import sys
@@ -40,7 +41,7 @@ def test_checked_build_records_nothing_and_changes_nothing(tmp_path):
     c = run(tmp_path, True)
     p = run(tmp_path, False)
     assert int(c["checked_build"]) == 1 and int(p["checked_build"]) == 0
-    assert c["words"].shape == (4,) and np.all(c["words"] == 0), [hex(int(x)) for x in c["words"]]
+    assert c["words"].shape == (5,) and np.all(c["words"] == 0), [hex(int(x)) for x in c["words"]]
     assert np.all(p["words"] == 0)
     # the adjoint's gradients and the map loss are sums by atomic adds, whose
     # order varies from run to run: compared to their rounding
