@@ -886,7 +886,11 @@ prism_status prism_step_host(prism_handle h, const double* imu, int32_t n, doubl
                 return fail(h, PRISM_ENOMEM, "host-frame buffers");
             }
         if (!h->ev_in) CK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "host-frame event");
-        if (!h->copy) CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking), "host-frame stream");
+        if (!h->copy) {   // high priority: its upload blocks go ahead of the waiting fuse and render blocks
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            CK(h, cudaStreamCreateWithPriority(&h->copy, cudaStreamNonBlocking, greatest), "host-frame stream");
+        }
     }
     CK(h, cudaEventSynchronize(h->ev_in), "previous host-frame copies");
     const int b = h->in_slot;
