@@ -48,7 +48,7 @@ struct MapPlanes {
 // (render_plan_block, render_dev.cuh); tiles are 16x8 pixels, row-major.
 struct RenderPlan {
     const int* order = nullptr;   // the tiles in launch order (a permutation), or null for row-major
-    uint32_t* cost = nullptr;     // out, per tile: the sum over its warps of the largest sample count
+    uint32_t* cost = nullptr;     // out, per tile: the sum over its warps of the largest march-step count
     float* rot = nullptr;         // out: this render's camera-to-world rotation (9 floats)
 };
 struct RenderPlanIn {

@@ -183,8 +183,8 @@ __device__ __forceinline__ int brick_exit(const KParams& P, int lv, int bx, int 
 
 // One 16x8-pixel tile (128 threads; warp w covers the 8x4 pixels at
 // ((w & 1) 8, (w >> 1) 4) of the tile).  sR / sc: camera-to-world rotation
-// and centre in shared memory.  Returns the thread's evaluated samples (0
-// outside the image).
+// and centre in shared memory.  Returns the thread's march steps (jumps
+// and evaluating steps; 0 outside the image), the anchor render's tile cost.
 //
 // The march tests the grid bounds only for samples after k_safe, which a
 // conservative FP32 bound (one voxel of margin, far above the rounding of the
@@ -211,7 +211,7 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
     const uint32_t px = PX > 0 ? (uint32_t)PX : P.px;
     const uint32_t pxy = PX > 0 ? (uint32_t)(PX * PX) : P.pxy;
 
-    int nsamp = 0, hk = 0;
+    int nsamp = 0, hk = 0, steps = 0;
     unsigned int uniq = 0;   // distinct occupancy corners of this ray (DETAIL only)
     float out_d = 0.0f, out_r = 0.0f, out_g = 0.0f, out_b = 0.0f;
     if (active) {
@@ -260,6 +260,7 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
         const float irgx = rgx != 0.0f ? 1.0f / rgx : 0.0f, irgy = rgy != 0.0f ? 1.0f / rgy : 0.0f,
                     irgz = rgz != 0.0f ? 1.0f / rgz : 0.0f, ieps = 1.0f / P.eps32;
         while (k <= P.kmax) {
+            ++steps;
             const float d = __fmul_rn(kf, P.eps32);
             const float gx = __fmaf_rn(d, rgx, cgx), gy = __fmaf_rn(d, rgy, cgy), gz = __fmaf_rn(d, rgz, cgz);
             if (k > k_safe && !(gx >= -0.5f && gx < hx && gy >= -0.5f && gy < hy && gz >= -0.5f && gz < hz)) break;
@@ -410,7 +411,7 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
             atomicAdd(&stats->render_rays, (unsigned long long)rays);
         }
     }
-    return nsamp;
+    return steps;
 }
 
 // The order of an anchor render's tiles, heaviest predicted first.  A ray's
@@ -419,10 +420,10 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
 // that cannot be skipped); rendered in raster order, the heavy tiles start
 // last and their blocks run on after the other SMs have emptied.  The
 // prediction is the last anchor render's cost (per tile, the sum over its
-// warps of the warp's largest sample count) at the tile each tile's centre
-// ray falls in when turned into the last camera (rotation only), maximised
-// over its 3x3 tile neighbourhood; a ray outside the last image counts as
-// heaviest.  Tiles go into 64 cost buckets, the buckets are laid out
+// warps of the warp's largest count of march steps, jumps over empty bricks
+// included) at the tile each tile's centre ray falls in when turned into the
+// last camera (rotation only), maximised over its 3x3 tile neighbourhood; a
+// ray outside the last image counts as heaviest.  Tiles go into 64 cost buckets, the buckets are laid out
 // heaviest first; within a bucket the order is arbitrary.  The order only
 // decides when a tile is rendered, never what it renders.  One block (a
 // multiple of 32 threads); key: one word of scratch per tile.
