@@ -144,6 +144,7 @@ def measured_peaks():
 # the sources each profiled kernel is built from (a committed ncu summary
 # counts only while their hash matches)
 KERNEL_SOURCES = {"k_render": ("render.cu", "render_dev.cuh", "prism_dev.cuh"),
+                  "k_fuse_list": ("fuse.cu", "fuse_dev.cuh", "prism_dev.cuh"),
                   "k_track_gn": ("track.cu", "track_dev.cuh", "prism_dev.cuh", "linalg64.cuh")}
 
 
@@ -420,6 +421,11 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     achieved_G = G / (render_ms * 1e-3) / 1e9
     achieved_U = U / (render_ms * 1e-3) / 1e9
+    # the map update: the map-plane bytes its updates read and write
+    fuse_ms = tm["fuse_ms"] / max(tm["fuse_n"], 1)
+    fb = 2 if storage == "bf16" else 4
+    fuse_upd, fuse_col = d_st["fuse_updates"] / max(K, 1), d_st["fuse_colour_updates"] / max(K, 1)
+    fuse_bytes = fuse_upd * 2 * 2 * fb + fuse_col * 4 * 2 * fb
     # the dominant kernel by device time: the Gauss-Newton pass
     npx = w.width * w.height
     gn_ms = gn_pass_ms(tm, cfg.n_gn)
@@ -562,6 +568,17 @@ def run_ours(args, rank, world, local_rank):
                                                  "2 x 8 x 3 x %d B, per launch" % (b, b, b, b),
                             "unique_bytes_per_launch": U, "gathered_bytes_per_launch": G,
                             "samples_per_launch": samp_per, "ms_per_launch": render_ms},
+        "roofline_fuse": {"kernel": "k_fuse_cull + k_fuse_list + k_brick_bounds (the map-update phase)",
+                          "bound": "latency (dependent pixel, map and store round trips per tile; the listed "
+                                   "tiles' occupancy read for their bounds)",
+                          "achieved": fuse_bytes / (fuse_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": fuse_bytes / (fuse_ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
+                          "traffic": profiled_traffic(args.workload, "k_fuse_list"),
+                          "algorithmic_bytes": "occupancy mean and variance read and written (%d B) per updated "
+                                               "voxel + four colour planes read and written (%d B) per colour "
+                                               "update, per step" % (4 * fb, 8 * fb),
+                          "updates_per_step": fuse_upd, "colour_updates_per_step": fuse_col,
+                          "bytes_per_step": fuse_bytes, "ms_per_step": fuse_ms},
         "localisation": {"ms_per_step": loc_ms, "gauss_newton_passes": cfg.n_gn, "gauss_newton_pass_ms": gn_ms,
                          "laplace_pass_ms": tm["laplace_ms"] / max(tm["laplace_n"], 1)},
         "bf16_map": bf16,
