@@ -49,11 +49,12 @@ struct MapPlanes {
 struct RenderPlan {
     const int* order = nullptr;   // the tiles in launch order (a permutation), or null for row-major
     uint32_t* cost = nullptr;     // out, per tile: the sum over its warps of the largest march-step count
-    float* rot = nullptr;         // out: this render's camera-to-world rotation (9 floats)
+    float* rot = nullptr;         // out: this render's camera-to-world rotation and centre (12 floats)
 };
 struct RenderPlanIn {
     const uint32_t* cost;   // the last anchor render's RenderPlan::cost
-    const float* rot_last;  // and its rotation
+    const float* rot_last;  // and its rotation and centre
+    const float* depth_last;  // and its depth image (null: directions only)
     const float* c2w;       // the next anchor render's mats
     uint32_t* key;          // scratch, one word per tile
     int* order;             // out

@@ -746,7 +746,7 @@ prism_status prism_create_map(const prism_config* cfg, const prism_state* s1, vo
         uint32_t* w = (uint32_t*)h->plan_block;
         float* rot = (float*)(w + 3 * words);
         h->plan_out = RenderPlan{(const int*)(w + words), w, rot};
-        h->plan_in = RenderPlanIn{w, rot, h->dstate->c2w, w + 2 * words, (int*)(w + words)};
+        h->plan_in = RenderPlanIn{w, rot, h->a_depth, h->dstate->c2w, w + 2 * words, (int*)(w + words)};
     }
 #ifdef PRISM_CHECKED
     if (dalloc(h, &h->check, sizeof(unsigned long long)) != cudaSuccess ||

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(128, DETAIL ? 10 : 8) k_render(KParams P, cons
     if (threadIdx.x == 0) s_cost = 0u;
     if (blockIdx.x == 0) {
         if (anchor_dst && threadIdx.x < 7) anchor_dst[threadIdx.x] = anchor_src[threadIdx.x];
-        if (plan.rot && threadIdx.x < 9) plan.rot[threadIdx.x] = mats[threadIdx.x];
+        if (plan.rot && threadIdx.x < 12) plan.rot[threadIdx.x] = mats[threadIdx.x];
     }
     __syncthreads();
     const int gx = (P.W + 15) >> 4, nt = gx * ((P.H + 7) >> 3);

@@ -421,9 +421,11 @@ __device__ __forceinline__ int render_tile(const KParams& P, const float* sR, co
 // last and their blocks run on after the other SMs have emptied.  The
 // prediction is the last anchor render's cost (per tile, the sum over its
 // warps of the warp's largest count of march steps, jumps over empty bricks
-// included) at the tile each tile's centre ray falls in when turned into the
-// last camera (rotation only), maximised over its 3x3 tile neighbourhood; a
-// ray outside the last image counts as heaviest.  Tiles go into 64 cost buckets, the buckets are laid out
+// included) at the tile each tile's centre ray falls in when seen from the
+// last camera -- the ray's direction, then its point at the depth the last
+// render saw in that direction (the parallax of the centre's move) --
+// maximised over its 3x3 tile neighbourhood; a ray outside the last image
+// counts as heaviest.  Tiles go into 64 cost buckets, the buckets are laid out
 // heaviest first; within a bucket the order is arbitrary.  The order only
 // decides when a tile is rendered, never what it renders.  One block (a
 // multiple of 32 threads); key: one word of scratch per tile.
@@ -434,14 +436,18 @@ __device__ __forceinline__ void render_plan_block(const KParams& P, const Render
     const int gx = (P.W + 15) >> 4, gy = (P.H + 7) >> 3, nt = gx * gy;
     if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0u;
     if (threadIdx.x == 0) s_max = 0u;
-    // R = R_lastᵀ R_next: the next camera's ray directions in the last camera's frame
-    float R[9];
+    // R = R_lastᵀ R_next: the next camera's ray directions in the last camera's
+    // frame; dc = R_lastᵀ (c_next - c_last): the next centre there
+    float R[9], dc[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             R[3 * i + j] = in.rot_last[i] * in.c2w[j] + in.rot_last[3 + i] * in.c2w[3 + j] +
                            in.rot_last[6 + i] * in.c2w[6 + j];
+        dc[i] = in.rot_last[i] * (in.c2w[9] - in.rot_last[9]) + in.rot_last[3 + i] * (in.c2w[10] - in.rot_last[10]) +
+                in.rot_last[6 + i] * (in.c2w[11] - in.rot_last[11]);
+    }
     __syncthreads();
     uint32_t lmax = 0u;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
@@ -451,7 +457,20 @@ __device__ __forceinline__ void render_plan_block(const KParams& P, const Render
         const float ez = R[6] * dx + R[7] * dy + R[8];
         uint32_t e = kUnknown;
         if (ez > 1e-6f) {
-            const float u = P.fx32 * ex / ez + P.cx32, v = P.fy32 * ey / ez + P.cy32;
+            float u = P.fx32 * ex / ez + P.cx32, v = P.fy32 * ey / ez + P.cy32;
+            if (in.depth_last && u >= 0.0f && u < (float)P.W && v >= 0.0f && v < (float)P.H) {
+                // parallax: the ray's point at the depth the last render saw in that
+                // direction, projected into the last camera from the next centre
+                const float z0 = in.depth_last[min((int)v, P.H - 1) * P.W + min((int)u, P.W - 1)];
+                const float sz = (z0 - dc[2]) / ez;
+                if (z0 > 0.0f && sz > 0.0f) {
+                    const float px = dc[0] + sz * ex, py = dc[1] + sz * ey, pz = dc[2] + sz * ez;
+                    if (pz > 1e-6f) {
+                        u = P.fx32 * px / pz + P.cx32;
+                        v = P.fy32 * py / pz + P.cy32;
+                    }
+                }
+            }
             if (u >= 0.0f && u < (float)P.W && v >= 0.0f && v < (float)P.H) {
                 const int tx = min((int)u >> 4, gx - 1), ty = min((int)v >> 3, gy - 1);
                 const int x0 = max(tx - 1, 0), x2 = min(tx + 1, gx - 1);
