@@ -366,6 +366,14 @@ prism_status prism_set_detail_counters(prism_handle h, int32_t enabled);
 prism_status prism_get_timing(prism_handle h, prism_timing* out);   /* synchronises */
 prism_status prism_timing_reset(prism_handle h);
 
+/* The Gauss-Newton localisation's launch form.  enabled = 1 (the default):
+ * the passes after the first run as one cooperative launch (every block
+ * resident, a grid barrier between passes, each block repeating the FP64
+ * finish), where the device holds that grid at once.  enabled = 0: one
+ * launch per pass.  Both forms evaluate the same sums in the same order and
+ * give the same bits. */
+prism_status prism_set_cooperative(prism_handle h, int32_t enabled);
+
 /* Bounds-check build.  libprism_checked.so is this library compiled with
  * PRISM_CHECKED: its kernels test the data-dependent index of every gather
  * and scatter (a trilinear cell's last corner in a map plane, a brick bound,

@@ -118,6 +118,7 @@ def load() -> C.CDLL:
         "prism_get_stats": (st, [H, P(Stats)]),
         "prism_set_timing": (st, [H, C.c_int32]),
         "prism_set_detail_counters": (st, [H, C.c_int32]),
+        "prism_set_cooperative": (st, [H, C.c_int32]),
         "prism_get_timing": (st, [H, P(Timing)]),
         "prism_timing_reset": (st, [H]),
         "prism_device_bytes": (C.c_int64, [H]),

@@ -213,6 +213,7 @@ struct prism_ctx {
     std::string err;
     bool timing = false;
     bool detail = false;
+    bool coop = true;   // the cooperative localisation launch (prism_set_cooperative)
     int64_t launches = 0;
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> pool;
@@ -492,10 +493,10 @@ prism_status do_localise(prism_handle h, const float* depth, const float* rgb, b
     // the first pass also evaluates the observation's depth validity into o_mask
     // (read by the later passes and by the fuse), and clears the barrier of the
     // cooperative launch that runs the other passes (a pass per launch where
-    // the device cannot hold that launch's grid at once)
-    int it = 0;
-    for (; it < h->cfg.n_gn; ++it) {
-        if (it == 1) {
+    // the device cannot hold that launch's grid at once, or with
+    // prism_set_cooperative off)
+    for (int it = 0; it < h->cfg.n_gn; ++it) {
+        if (it == 1 && h->coop) {
             cudaError_t e = launch_track_coop(h->kp, depth, rgb, h->o_mask, h->a0, h->a1, h->dstate, h->partials,
                                               h->counter + 1, h->max_blocks, h->dstats, h->cfg.n_gn - 1, h->stream);
             if (e == cudaSuccess) {
@@ -1247,6 +1248,12 @@ prism_status prism_set_timing(prism_handle h, int32_t enabled) {
 prism_status prism_set_detail_counters(prism_handle h, int32_t enabled) {
     if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
     h->detail = enabled != 0;
+    return PRISM_OK;
+}
+
+prism_status prism_set_cooperative(prism_handle h, int32_t enabled) {
+    if (!h) return fail(nullptr, PRISM_EINVAL, "handle is NULL");
+    h->coop = enabled != 0;
     return PRISM_OK;
 }
 

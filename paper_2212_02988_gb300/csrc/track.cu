@@ -94,7 +94,10 @@ cudaError_t launch_track(const KParams& P, int mode, const float* o_depth,
                          const float* o_rgb, const uint8_t* o_mask, const float4* a0, const float4* a1,
                          DevState* dev, float* partials, unsigned int* counter, int max_blocks,
                          DevStats* stats, cudaStream_t s, bool pdl, uint8_t* mask_out) {
-    const int grid = track_launch_grid(P, mode, max_blocks);
+    // the Laplace pass takes the Gauss-Newton passes' grid, so that its sums
+    // see the pixels in the same order after either launch form of those
+    // passes (prism_set_cooperative)
+    const int grid = track_launch_grid(P, mode == TRACK_LAPLACE ? TRACK_GN : mode, max_blocks);
     if (mode == TRACK_GN && mask_out) {
         if (!pdl) {
             k_track<TRACK_GN, true><<<grid, Block<TRACK_GN>::threads, 0, s>>>(P, o_depth, o_rgb, o_mask, a0, a1, dev, partials,

@@ -356,6 +356,12 @@ class Filter:
     def set_detail_counters(self, enabled: bool = True):
         self._check(self.L.prism_set_detail_counters(self.h, int(enabled)), self.h)
 
+    def set_cooperative(self, enabled: bool = True):
+        """The localisation's launch form: one cooperative launch for the
+        Gauss-Newton passes after the first (default), or one launch per
+        pass; the same bits either way."""
+        self._check(self.L.prism_set_cooperative(self.h, int(enabled)), self.h)
+
     def timing(self) -> dict:
         t = Timing()
         self._check(self.L.prism_get_timing(self.h, C.byref(t)), self.h)
