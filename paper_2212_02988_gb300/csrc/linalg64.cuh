@@ -259,14 +259,15 @@ __device__ __forceinline__ bool pivot_ok(double d) {
     return hi >= 0 && e >= 1 && e <= 2044;
 }
 
-// 1/d for d with pivot_ok(d), by Newton-Raphson iteration for the
-// reciprocal, y' = y + y (1 - d y) (the relative error squares each step).
+// 1/d for d with pivot_ok(d): a seed y with relative error e = 1 - d y, then
+// one step of the third-order iteration y' = y (1 + e + e^2), the geometric
+// series of 1/d = y / (1 - e) cut after e^2, whose relative error is e^3.
 // The seed is the single-precision approximate reciprocal (PTX
 // rcp.approx.ftz.f32, relative error about 2^-23) of d's mantissa cut to 20
-// bits, rescaled by the exponent with integer operations: relative error
-// below 2^-19.5, then 2^-39 and, after the second step, the final rounding
-// (a result within one unit in the last place of 1/d).  Only the two steps
-// (four FMAs) use the FP64 pipe.
+// bits, rescaled by the exponent with integer operations: |e| below
+// 2^-19.5, so the step leaves 2^-58.5 (about 0.02 unit in the last place)
+// under the final rounding: a result within one unit in the last place of
+// 1/d.  Only the step's three dependent FMAs use the FP64 pipe.
 __device__ __forceinline__ double rcp64(double d) {
     const int hi = __double2hiint(d);
     const int e = (hi >> 20) & 0x7ff;
@@ -276,8 +277,8 @@ __device__ __forceinline__ double rcp64(double d) {
     const int rb = __float_as_int(r);
     const int ye = ((rb >> 23) & 0xff) - 127 + 2046 - e;                 // biased exponent of r 2^(1023 - e)
     const double y0 = __hiloint2double((ye << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
-    const double y1 = fma(y0, fma(-d, y0, 1.0), y0);
-    return fma(y1, fma(-d, y1, 1.0), y1);
+    const double er = fma(-d, y0, 1.0);
+    return fma(y0, fma(er, er, er), y0);
 }
 
 // Solves A x = b for a 6x6 symmetric positive definite A on one warp by the
@@ -285,9 +286,11 @@ __device__ __forceinline__ double rcp64(double d) {
 // triangular, D diagonal).  Lane e < 21 brings entry (i, j), e = tri6(i, j),
 // of A's lower triangle in `a`; lane 21 + i brings b_i.  Column j: the
 // pivot d_j = a_jj, l_ij = a_ij / d_j below it, and every trailing entry and
-// right-hand side row i > j takes a_im -= l_ij a_mj (b_i -= l_ij b_j: the
-// forward substitution with L rides along); then z = D^-1 y and the back
-// substitution with L^T.  Returns x_i in lane 21 + i (other lanes: junk);
+// right-hand side row i > j takes a_im -= (a_ij a_mj) / d_j (b_i -= (a_ij
+// b_j) / d_j: the forward substitution with L rides along; the product is
+// formed while the pivot's reciprocal is computed, so that one FMA follows
+// the reciprocal on the chain from pivot to pivot); then z = D^-1 y and the
+// back substitution with L^T.  Returns x_i in lane 21 + i (other lanes: junk);
 // *pd: every pivot passed pivot_ok (the same on every lane).  All 32 lanes
 // must call it.
 __device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
@@ -321,7 +324,7 @@ __device__ __forceinline__ double warp_ldlt6_solve(double a, bool* pd) {
         const int src_m = lm == 6 ? 21 + j : (lm > j ? tri6(lm, j) : 0);
         const double amj = __shfl_sync(0xffffffffu, a, src_m);
         const double lij = aij * rj;
-        const double upd = fma(-lij, amj, a);
+        const double upd = fma(-(aij * amj), rj, a);
         // the factor L_ij, kept for the back substitution; a trailing entry
         // (lm <= li) or a right-hand side (lm = 6)
         a = sel64(below && lm == j, lij, sel64(below && lm > j, upd, a));
@@ -370,7 +373,7 @@ __device__ __forceinline__ void warp_spd6_inverse(double a, bool* pd, double x[6
         const double aij = __shfl_sync(0xffffffffu, a, below ? tri6(li, j) : 0);
         const double amj = __shfl_sync(0xffffffffu, a, below && lm > j ? tri6(lm, j) : 0);
         const double lij = aij * r[j];
-        const double upd = fma(-lij, amj, a);
+        const double upd = fma(-(aij * amj), r[j], a);
         a = sel64(below && lm == j, lij, sel64(below && lm > j, upd, a));
     }
     // column c = lane of A^-1; L_ik (i > k) is in lane tri6(i, k)

@@ -215,6 +215,7 @@ __device__ __forceinline__ void track_fetch(const KParams& P, const float* sM, c
         q.ok = PRISM_IN_RANGE(P, CHK_TRACK_ANCHOR, q.iv * W + q.iu, (long long)W * P.H) &&
                PRISM_IN_RANGE(P, CHK_TRACK_ANCHOR, b00, (long long)W * P.H) &&
                PRISM_IN_RANGE(P, CHK_TRACK_ANCHOR, b00 + W + 1, (long long)W * P.H);
+        (void)b00;   // (unused where the checks compile to true)
     }
     if (q.ok) {
         const int b00 = (int)bv * W + (int)bu;

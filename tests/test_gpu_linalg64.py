@@ -2,7 +2,7 @@
 (paper_2212_02988_gb300/csrc/linalg64.cuh), compiled with nvcc into a
 temporary program:
 
-* rcp64 (Newton-Raphson reciprocal from a single-precision seed) is within
+* rcp64 (a third-order reciprocal iteration from a single-precision seed) is within
   one unit in the last place of CUDA's correctly rounded 1.0 / d over
   mantissas and exponents across its whole range;
 * warp_ldlt6_solve (square-root-free Cholesky of a 6x6 SPD system on one
