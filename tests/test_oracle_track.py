@@ -99,6 +99,81 @@ def planar_pair(O, W=40, H=30):
     return p, A, B, f(a_d), f(a_rgb), f(sB), f(o_rgb)
 
 
+PLANE_N = np.array([0.1, -0.2, -1.0]) / np.linalg.norm([0.1, -0.2, -1.0])
+
+
+def sliding_pair(O, s_world, W=40, H=30):
+    """The plane of planar_pair (n . x = -2, n = PLANE_N) seen from the
+    identity anchor and from the anchor moved by s_world (no rotation): depth
+    images by ray-plane intersection in FP64, colours from the same linear
+    field."""
+    w = synth.tiny(width=W, height=H)
+    p = O.params(w)
+    A = np.array([0, 0, 0, 1.0, 0, 0, 0])
+    nrm = PLANE_N
+    c = -2.0
+    u, v = np.meshgrid(np.arange(W, dtype=float), np.arange(H, dtype=float))
+    ray = np.stack([(u - p.cx) / p.fx, (v - p.cy) / p.fy, np.ones_like(u)], -1)
+    lin = lambda uu, vv: np.stack([0.3 + 0.004 * uu + 0.003 * vv, 0.5 - 0.002 * uu + 0.004 * vv,
+                                   0.4 + 0.003 * uu - 0.002 * vv], -1)
+    a_d = c / (ray @ nrm)
+    S = np.concatenate([s_world, [1.0, 0, 0, 0]])
+    sS = (c - nrm @ s_world) / (ray @ nrm)
+    X = s_world + sS[..., None] * ray
+    up, vp = p.fx * X[..., 0] / X[..., 2] + p.cx, p.fy * X[..., 1] / X[..., 2] + p.cy
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return p, A, S, nrm, f(a_d), f(lin(u, v)), f(sS), f(lin(up, vp))
+
+
+def test_point_to_plane_is_blind_to_sliding(oracle_mod):
+    """A planar scene and a camera that slides 10 cm along the plane (App.
+    E.3's point-to-plane term <p_hat - X, n_hat>): evaluated at the unmoved
+    pose, every kept pixel's geometric residual stays at rounding level
+    (both points lie on the plane, whichever anchor pixel X falls on) while
+    the colour residuals see the slide; a 5 mm offset along the normal gives
+    the same residual of 5 mm at every kept pixel, its sign following the
+    offset's; and the translation Jacobian of the geometric residual is the
+    unit normal (no in-plane component).  Catches a point-to-point
+    distance, a normal taken from the wrong neighbours, and a residual or
+    Jacobian off by a scale."""
+    O = oracle_mod
+    s_world = np.array([0.08, 0.06, 0.0])
+    slide = s_world - (s_world @ PLANE_N) * PLANE_N   # along the plane
+    p, A, S, nrm, a_d, a_rgb, o_d, o_rgb = sliding_pair(O, slide)
+    assert abs(slide @ nrm) < 1e-15 and np.linalg.norm(slide) > 0.09
+    # at the true pose every residual vanishes
+    true = O.residuals(p, A, a_d, a_rgb, S, o_d, o_rgb)
+    kept = true["kept"] > 0
+    assert kept.mean() > 0.6
+    assert np.abs(true["r"][kept]).max() < 1e-5
+    # at the unmoved pose: the geometry cannot see the slide, the colour can
+    slid = O.residuals(p, A, a_d, a_rgb, A, o_d, o_rgb)
+    ks = slid["kept"] > 0
+    assert ks.mean() > 0.5
+    assert np.abs(slid["r"][ks, 0]).max() < 1e-5
+    assert np.abs(slid["r"][ks, 1:]).max() > 5e-3
+    # a pose off the plane by delta along the normal: r_geo = -delta <n, n_hat> everywhere
+    for delta in (0.005, -0.005):
+        off = O.residuals(p, A, a_d, a_rgb, np.concatenate([slide + delta * nrm, S[3:]]), o_d, o_rgb)
+        ko = off["kept"] > 0
+        assert ko.mean() > 0.5
+        rg = off["r"][ko, 0]
+        np.testing.assert_allclose(np.abs(rg), abs(delta), rtol=0, atol=2e-6)
+        assert np.all(np.sign(rg) == np.sign(rg[0]))
+        if delta > 0:
+            sign_pos = np.sign(rg[0])
+        else:
+            assert np.sign(rg[0]) == -sign_pos
+    # the translation Jacobian of r_geo is the (camera-facing) unit normal,
+    # to the accuracy of a normal differenced from FP32 depths
+    Jt = true["J"][kept, 0, :3]
+    np.testing.assert_allclose(np.abs(Jt @ nrm), 1.0, rtol=0, atol=1e-5)
+    inplane = np.cross(nrm, [1.0, 0.0, 0.0])
+    inplane /= np.linalg.norm(inplane)
+    for d in (inplane, np.cross(nrm, inplane)):
+        assert np.abs(Jt @ d).max() < 1e-5
+
+
 def test_laplace_hessian_is_twice_scaled_jtj(oracle_mod):
     """At zero residual, the Hessian of S = sum (r/b)^2 (the L1 terms treated
     as squares, Sec. 4.1 / App. E.3) is exactly 2 J^T J / b^2: compare a
